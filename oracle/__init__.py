@@ -1,0 +1,175 @@
+"""CPU oracle for the dependence-volume hot path -- TEST INFRASTRUCTURE ONLY.
+
+Only the test suite, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg (and its ``--impl reference`` arm) may import this package.  The CUDA
+library never calls it and shares no code with it: the oracle has its own C++
+source (``ndf_oracle.cpp``, ``ndf_net_oracle.cpp``), its own digamma table and
+its own build.
+
+Functions and the passages they follow:
+  pearson / pearson_volume -- Sec. 3.1, Eq. 1 (FP64, two-pass, plain definition)
+  ksg_pair / ksg_volume    -- Sec. 3.2 / Sec. 6.2: the cited KSG estimator,
+                              algorithm 1, brute force (FP32 max-norm distances,
+                              k-th order statistic by nth_element, linear-scan
+                              strict counts, long-double digamma sum)
+  digamma_int              -- psi(1) = -gamma, psi(n+1) = psi(n) + 1/n
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libndf_oracle.so")
+_SOURCES = ["ndf_oracle.cpp", "ndf_net_oracle.cpp"]
+_HEADERS = ["ndf_oracle.h", "ndf_net_oracle.h"]
+_lock = threading.Lock()
+_lib = None
+
+_f32p = ctypes.POINTER(ctypes.c_float)
+_f64p = ctypes.POINTER(ctypes.c_double)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+def _existing(names):
+    return [os.path.join(_HERE, n) for n in names if os.path.exists(os.path.join(_HERE, n))]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (g++ -O2, OpenMP, no fast-math, no FMA contraction)."""
+    srcs = _existing(_SOURCES)
+    deps = srcs + _existing(_HEADERS)
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= max(
+        os.path.getmtime(p) for p in deps
+    ):
+        return _LIB_PATH
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-o", tmp] + srcs
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            lib.oracle_pearson.restype = ctypes.c_double
+            lib.oracle_pearson.argtypes = [_f32p, _f32p, ctypes.c_int64]
+            lib.oracle_pearson_volume.restype = ctypes.c_int
+            lib.oracle_pearson_volume.argtypes = [_f32p, _f32p, ctypes.c_int64, ctypes.c_int64,
+                                                  ctypes.c_int64, _i64p, ctypes.c_int64, _f64p,
+                                                  ctypes.c_int]
+            lib.oracle_digamma_int.restype = ctypes.c_double
+            lib.oracle_digamma_int.argtypes = [ctypes.c_int64]
+            lib.oracle_ksg_pair.restype = ctypes.c_double
+            lib.oracle_ksg_pair.argtypes = [_f32p, _f32p, ctypes.c_int64, ctypes.c_int, _f32p,
+                                            _i32p, _i32p]
+            lib.oracle_ksg_volume.restype = ctypes.c_int
+            lib.oracle_ksg_volume.argtypes = [_f32p, _f32p, ctypes.c_int64, ctypes.c_int64,
+                                              ctypes.c_int64, ctypes.c_int, _i64p, ctypes.c_int64,
+                                              _f64p, ctypes.c_int]
+            lib.oracle_threads.restype = ctypes.c_int
+            lib.oracle_threads.argtypes = [ctypes.c_int]
+            _lib = lib
+    return _lib
+
+
+def _f32(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data_as(_f32p)
+
+
+def threads(n: int = 0) -> int:
+    """Threads the oracle's parallel loops use for a request of ``n`` (0 = all)."""
+    return _load().oracle_threads(int(n))
+
+
+def pearson(x, y) -> float:
+    """Eq. 1 for one pair of samples (FP64)."""
+    x, px = _f32(x)
+    y, py = _f32(y)
+    if x.shape != y.shape or x.ndim != 1:
+        raise ValueError("x and y must be 1-D of equal length")
+    return _load().oracle_pearson(px, py, x.shape[0])
+
+
+def _field2d(field):
+    f = np.ascontiguousarray(field, dtype=np.float32)
+    M = f.shape[0]
+    return f.reshape(M, -1), M
+
+
+def pearson_volume(ref_field, q_field, ref_idx: int, verts=None, nthreads: int = 0) -> np.ndarray:
+    """r(reference vertex of ref_field, v of q_field) for all / selected v."""
+    rf, M = _field2d(ref_field)
+    qf, Mq = _field2d(q_field)
+    if Mq != M or rf.shape != qf.shape:
+        raise ValueError("fields differ in shape")
+    N = rf.shape[1]
+    if verts is None:
+        out = np.empty(N, dtype=np.float64)
+        vp, nv = None, 0
+    else:
+        verts = np.ascontiguousarray(verts, dtype=np.int64)
+        out = np.empty(verts.shape[0], dtype=np.float64)
+        vp, nv = verts.ctypes.data_as(_i64p), verts.shape[0]
+    rc = _load().oracle_pearson_volume(rf.ctypes.data_as(_f32p), qf.ctypes.data_as(_f32p), M, N,
+                                       int(ref_idx), vp, nv, out.ctypes.data_as(_f64p),
+                                       int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle_pearson_volume: bad arguments")
+    return out
+
+
+def digamma_int(n: int) -> float:
+    return _load().oracle_digamma_int(int(n))
+
+
+def ksg_pair(x, y, k: int):
+    """KSG algorithm 1 on one pair: returns (mi, eps[M], nx[M], ny[M])."""
+    x, px = _f32(x)
+    y, py = _f32(y)
+    if x.shape != y.shape or x.ndim != 1:
+        raise ValueError("x and y must be 1-D of equal length")
+    M = x.shape[0]
+    eps = np.empty(M, dtype=np.float32)
+    nx = np.empty(M, dtype=np.int32)
+    ny = np.empty(M, dtype=np.int32)
+    mi = _load().oracle_ksg_pair(px, py, M, int(k), eps.ctypes.data_as(_f32p),
+                                 nx.ctypes.data_as(_i32p), ny.ctypes.data_as(_i32p))
+    if np.isnan(mi):
+        raise ValueError("oracle_ksg_pair: bad arguments (need 1 <= k < M)")
+    return mi, eps, nx, ny
+
+
+def ksg_volume(ref_field, q_field, ref_idx: int, k: int, verts=None, nthreads: int = 0):
+    """KSG MI (reference vertex of ref_field, v of q_field) for all / selected v."""
+    rf, M = _field2d(ref_field)
+    qf, Mq = _field2d(q_field)
+    if Mq != M or rf.shape != qf.shape:
+        raise ValueError("fields differ in shape")
+    N = rf.shape[1]
+    if verts is None:
+        out = np.empty(N, dtype=np.float64)
+        vp, nv = None, 0
+    else:
+        verts = np.ascontiguousarray(verts, dtype=np.int64)
+        out = np.empty(verts.shape[0], dtype=np.float64)
+        vp, nv = verts.ctypes.data_as(_i64p), verts.shape[0]
+    rc = _load().oracle_ksg_volume(rf.ctypes.data_as(_f32p), qf.ctypes.data_as(_f32p), M, N,
+                                   int(ref_idx), int(k), vp, nv, out.ctypes.data_as(_f64p),
+                                   int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle_ksg_volume: bad arguments")
+    return out
