@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Dependence-volume benchmark: one reference vertex against every vertex of a
+250 x 352 x 20 grid (1.76M vertices) of a 1000-member synthetic ensemble shaped
+like the paper's CSEns data (Sec. 6.1, Table 1 workload).
+
+One step = one exact dependence volume for one reference vertex: the Pearson
+volume (Eq. 1) and the KSG mutual-information volume (k = 8), both through the
+C ABI of libndf.so, inputs resident in HBM.  ``e2e`` repeats the step through
+the same ABI from pinned host memory: ensemble upload + statistics + both
+volumes + copies of both volumes back to the host.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Under torchrun every rank computes its own reference vertices on its own copy
+of the ensemble (weak scaling, no data-path collective); rank 0 prints one JSON
+line with the max-over-ranks time.  ``--impl reference`` times the CPU oracle
+on the host cores instead (rank 0 only), on a bounded sample of vertices.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+K_NN = 8
+METRIC = "ms per 1.76M-voxel dependence volume (Pearson + KSG MI k=8, M=1000)"
+WORKLOAD = "csens-like ensemble 250x352x20 (N=1,760,000), M=1000 FP32 members, one reference per volume"
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def build_everything():
+    import oracle
+    import synth
+    from paper_2307_02203_gb300 import build
+
+    synth.build()
+    oracle.build()
+    build.build()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "sm_max_mhz": float(d.get("sm_max_mhz", 2070.0)),
+                "source": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+def make_field(recipe, pinned, nthreads):
+    import torch
+
+    import synth
+
+    shape = (recipe.M, recipe.Z, recipe.Y, recipe.X)
+    if pinned:
+        t = torch.empty(shape, dtype=torch.float32, pin_memory=True)
+        arr = t.numpy()
+        synth.generate(recipe, out=arr, nthreads=nthreads)
+        return t, arr
+    arr = synth.generate(recipe, nthreads=nthreads)
+    return None, arr
+
+
+def cpu_baseline(field, recipe, ref, seconds_target, seed):
+    """Times the oracle (all host cores) on a bounded seeded vertex sample and
+    extrapolates to ms per full volume."""
+    import oracle
+    import synth
+
+    cores = oracle.threads(0)
+    probe = synth.sample_vertices(recipe, max(2 * cores, 32), seed=seed + 1)
+    t0 = time.perf_counter()
+    oracle.ksg_volume(field, field, ref, K_NN, verts=probe)
+    oracle.pearson_volume(field, field, ref, verts=probe)
+    per_vertex = (time.perf_counter() - t0) / len(probe)
+    count = int(max(len(probe), min(recipe.N, seconds_target / max(per_vertex, 1e-9))))
+    verts = synth.sample_vertices(recipe, count, seed=seed)
+    t0 = time.perf_counter()
+    oracle.pearson_volume(field, field, ref, verts=verts)
+    tp = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.ksg_volume(field, field, ref, K_NN, verts=verts)
+    tk = time.perf_counter() - t0
+    scale = recipe.N / count
+    ms = (tp + tk) * scale * 1e3
+    return {"value": ms, "unit": "ms per volume", "cores": cores, "kind": "oracle",
+            "sample": f"Pearson + KSG at {count} seeded vertices of {recipe.N}, "
+                      f"time x {scale:.1f} (extrapolated)",
+            "pearson_ms": tp * scale * 1e3, "ksg_ms": tk * scale * 1e3}
+
+
+def run_reference(args, recipe):
+    rank = env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    _, field = make_field(recipe, pinned=False, nthreads=0)
+    rng = np.random.default_rng(20230705)
+    refs = rng.integers(0, recipe.N, size=args.steps + args.warmup)
+    per_step = max(5.0, 60.0 / max(args.steps, 1))
+    vals = []
+    info = None
+    for i in range(args.warmup + args.steps):
+        info = cpu_baseline(field, recipe, int(refs[i]), per_step if i >= args.warmup else 2.0,
+                            seed=1000 + i)
+        if i >= args.warmup:
+            vals.append(info["value"])
+    v = float(np.mean(vals))
+    line = {"metric": METRIC, "value": v, "unit": "ms", "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "k": K_NN},
+            "cpu_baseline": {"kind": "oracle", "cores": info["cores"], "sample": info["sample"],
+                             "value": v, "unit": "ms"},
+            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--small", action="store_true", help="tiny 16x16x4, M=100 workload (checks)")
+    args = ap.parse_args()
+
+    import synth
+
+    recipe = synth.TINY if args.small else synth.CSENS
+    if args.impl == "reference":
+        return run_reference(args, recipe)
+
+    import torch
+    import torch.distributed as dist
+
+    world = env_int("WORLD_SIZE", 1)
+    rank = env_int("RANK", 0)
+    local_rank = env_int("LOCAL_RANK", 0)
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local_rank)
+    build_everything()
+    from paper_2307_02203_gb300 import ndf
+
+    nthreads = max(1, (os.cpu_count() or 1) // max(1, env_int("LOCAL_WORLD_SIZE", world)))
+    field_t, field = make_field(recipe, pinned=True, nthreads=nthreads)
+    stream = torch.cuda.Stream()
+    ctx = ndf.ndf_create(local_rank, stream.cuda_stream)
+    M, Z, Y, X = field.shape
+    N = recipe.N
+    fid = ndf.ndf_load_ensemble(ctx, field_t, M, Z, Y, X)
+    rng = np.random.default_rng(20230705 + rank)
+    refs = [int(r) for r in rng.integers(0, N, size=args.warmup + args.steps)]
+    out_r = torch.empty(N, dtype=torch.float32, device="cuda")
+    out_mi = torch.empty(N, dtype=torch.float32, device="cuda")
+
+    def step(ref):
+        ndf.ndf_pearson(ctx, fid, fid, ref, out_r)
+        ndf.ndf_mi_ksg(ctx, fid, fid, ref, K_NN, out_mi)
+
+    for i in range(args.warmup):
+        step(refs[i])
+    ndf.ndf_synchronize(ctx)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    launches0 = ndf.ndf_launch_count(ctx)
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for i in range(args.steps):
+            ref = refs[args.warmup + i]
+            ev[i][0].record(stream)
+            ndf.ndf_pearson(ctx, fid, fid, ref, out_r)
+            ev[i][1].record(stream)
+            ndf.ndf_mi_ksg(ctx, fid, fid, ref, K_NN, out_mi)
+            ev[i][2].record(stream)
+        t_end.record(stream)
+        barrier()
+    launches = ndf.ndf_launch_count(ctx) - launches0
+    total_ms = t_start.elapsed_time(t_end)
+    pearson_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
+    ksg_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
+    if world > 1:
+        t = torch.tensor([total_ms, pearson_ms, ksg_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, pearson_ms, ksg_ms = [float(v) for v in t.tolist()]
+    volumes = args.steps * world
+    ms_per_volume = total_ms / volumes
+
+    # ---- end to end through the ABI with host buffers (upload + stats + both volumes + D2H)
+    host_r = torch.empty(N, dtype=torch.float32, pin_memory=True)
+    host_mi = torch.empty(N, dtype=torch.float32, pin_memory=True)
+    e2e_steps = max(1, min(args.e2e_steps, args.steps))
+    barrier()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        fid2 = ndf.ndf_load_ensemble(ctx, field_t, M, Z, Y, X)
+        ndf.ndf_pearson(ctx, fid2, fid2, refs[args.warmup + i], host_r)
+        ndf.ndf_mi_ksg(ctx, fid2, fid2, refs[args.warmup + i], K_NN, host_mi)
+        ndf.ndf_free_ensemble(ctx, fid2)
+    barrier()
+    e2e_ms = (time.perf_counter() - t0) * 1e3
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_per_volume = e2e_ms / (e2e_steps * world)
+
+    # ---- roofline of the dominant kernel (KSG: ALU-bound distance evaluations)
+    peaks = load_peaks()
+    props = torch.cuda.get_device_properties(local_rank)
+    sms = props.multi_processor_count
+    evals = float(N) * M * (M - 1)
+    achieved = evals / (ksg_ms * 1e-3) / 1e9  # Gdist/s
+    # peak: 64 ALU-pipe lanes per SM per clock, 2 ALU instructions per evaluation
+    # (the abs-max and the threshold compare), at the maximum SM clock
+    peak = sms * 64 / 2 * peaks["sm_max_mhz"] * 1e6 / 1e9
+    pearson_gbs = (4.0 * M * N + 4.0 * N + 16.0 * N) / (pearson_ms * 1e-3) / 1e9
+
+    result = None
+    if rank == 0:
+        clocks = clk.summary()
+        cpu = cpu_baseline(field, recipe, refs[args.warmup], args.cpu_seconds, seed=7) \
+            if world == 1 else None
+        result = {
+            "metric": METRIC, "value": ms_per_volume, "unit": "ms", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "M": M, "grid_xyz": [X, Y, Z], "k": K_NN,
+                       "refs_per_rank": args.steps, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (7.04 GB field, read once per volume)"},
+            "pearson_ms": pearson_ms, "ksg_ms": ksg_ms,
+            "mi_pairs_per_s": N / (ksg_ms * 1e-3),
+            "pearson_hbm_gbs": pearson_gbs,
+            "pearson_hbm_frac": pearson_gbs / peaks["hbm_gbs"],
+            "roofline": {"bound": "alu", "kernel": "ksg_volume_kernel", "achieved": achieved,
+                         "peak": peak, "unit": "Gdist/s", "frac": achieved / peak,
+                         "traffic": None, "peak_source": f"{peaks['source']} max SM clock"},
+            "e2e": {"value": e2e_per_volume, "unit": "ms",
+                    "h2d_bytes_per_step": int(field.nbytes),
+                    "d2h_bytes_per_step": int(2 * N * 4)},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(result), flush=True)
+    ndf.ndf_destroy(ctx)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

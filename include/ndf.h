@@ -1,0 +1,129 @@
+/*
+ * ndf.h -- C ABI of libndf.so, the GB300 (sm_103a) dependence-volume library.
+ *
+ * The library computes, for one selected reference vertex and every vertex of
+ * a 3-D grid, the statistical dependence across an M-member ensemble
+ * (Sec. 3: R_mu,nu(p_mu, p_nu) = rho(e^mu(p_mu), e^nu(p_nu)), one 3-D slice of
+ * the dependence field at a time), with two measures:
+ *   - Pearson's r (Sec. 3.1, Eq. 1);
+ *   - mutual information (Sec. 3.2, Eq. 2) by the Kraskov-Stoegbauer-
+ *     Grassberger k-nearest-neighbour estimator, algorithm 1 (the estimator
+ *     cited in Sec. 3.2 and timed in Sec. 6.2, Table 1).
+ *
+ * Conventions shared by every call:
+ *   - Every call returns an ndf_status; nothing throws across the ABI.  On a
+ *     failure, ndf_last_error(ctx) holds a one-line description.
+ *   - Ensemble layout: float field[M][Z][Y][X], member-major; the flat vertex
+ *     index is v = (z*Y + y)*X + x, element offset m*N + v with N = X*Y*Z.
+ *   - Pointers may be host or device memory; the library detects which with
+ *     cudaPointerGetAttributes.  Inputs are copied, never retained.  Output
+ *     buffers are owned by the caller.
+ *   - Work runs on the context's stream.  With device outputs a call returns
+ *     once the work is enqueued; with host outputs it returns after the copy
+ *     to the host has completed.  Argument errors are detected on the host
+ *     and returned before anything is enqueued.
+ *   - A context is not thread safe: use one context per host thread.
+ */
+#ifndef NDF_H
+#define NDF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ndf_ctx ndf_ctx; /* opaque; owns all device memory it allocates */
+
+typedef enum {
+    NDF_OK = 0,
+    NDF_ERR_ARG = -1,     /* invalid argument (sizes, indices, k, null pointers) */
+    NDF_ERR_OOM = -2,     /* device or host allocation failed */
+    NDF_ERR_CUDA = -3,    /* a CUDA runtime call or kernel launch failed */
+    NDF_ERR_TIMEOUT = -4, /* a bounded device-side wait gave up */
+    NDF_ERR_STATE = -5,   /* call not valid in the current state (e.g. freed field) */
+    NDF_ERR_IO = -6       /* file read/write failed */
+} ndf_status;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * to run on (e.g. PyTorch's current stream) or NULL for a context-owned
+ * non-blocking stream.  Fails with NDF_ERR_CUDA when the device is missing or
+ * is not compute capability 10.3. */
+ndf_status ndf_create(ndf_ctx** out, int device, void* cuda_stream);
+
+/* Free every device buffer of the context (fields, scratch) and the context. */
+void ndf_destroy(ndf_ctx* ctx);
+
+/* Static description of a status code. */
+const char* ndf_status_str(int status);
+
+/* Detail of the last failure on this context (context-owned string). */
+const char* ndf_last_error(const ndf_ctx* ctx);
+
+/* Switch the stream later calls run on (NULL: the context's own stream). */
+ndf_status ndf_set_stream(ndf_ctx* ctx, void* cuda_stream);
+
+/* Block until all work enqueued by this context has finished. */
+ndf_status ndf_synchronize(ndf_ctx* ctx);
+
+/* Number of CUDA kernels this context has launched so far. */
+uint64_t ndf_launch_count(const ndf_ctx* ctx);
+
+/* Flat vertex index (z*Y + y)*X + x, or -1 when a coordinate is out of range. */
+int64_t ndf_index(int64_t x, int64_t y, int64_t z, int64_t X, int64_t Y, int64_t Z);
+
+/* ---- ensembles (Sec. 3: E = {E_i}, member samples e(p) of length M) ------ */
+
+/* Copy field[M][Z][Y][X] (host or device) into context-owned device memory and
+ * compute the per-vertex statistics used by Eq. 1: the FP64 mean mu_v and
+ * 1/sqrt(S_v) with S_v = sum_m (e_m(v) - mu_v)^2 (two passes, FP64 across
+ * member blocks).  Requires M >= 2 and finite values (NDF_ERR_ARG otherwise;
+ * the check reads the copied field).  Writes the new field's id. */
+ndf_status ndf_load_ensemble(ndf_ctx* ctx, const float* field, int64_t M, int64_t Z, int64_t Y,
+                             int64_t X, int* field_id_out);
+
+/* Release a field's device memory; its id becomes invalid (NDF_ERR_STATE). */
+ndf_status ndf_free_ensemble(ndf_ctx* ctx, int field_id);
+
+/* Shape of a loaded field (any output pointer may be NULL). */
+ndf_status ndf_field_shape(const ndf_ctx* ctx, int field_id, int64_t* M, int64_t* Z, int64_t* Y,
+                           int64_t* X);
+
+/* Copy the per-vertex statistics (N doubles each, host or device; either may
+ * be NULL): mean_out = mu_v, inv_norm_out = 1/sqrt(S_v) (0 where S_v = 0). */
+ndf_status ndf_field_stats(ndf_ctx* ctx, int field_id, double* mean_out, double* inv_norm_out);
+
+/* ---- exact estimators ---------------------------------------------------- */
+
+/* Pearson volume (Sec. 3.1, Eq. 1): out[v] = r(e^ref(p_ref), e^query(v)) for
+ * all N vertices v of the query field, FP32, clamped to [-1, 1]; 0 where
+ * either sample has zero variance.  ref_field may equal query_field (the
+ * self-correlation slice S_mu(p_ref, .), Sec. 3).  Fields must have the same
+ * shape.  ref_idx is a flat vertex index in [0, N).  out: N floats. */
+ndf_status ndf_pearson(ndf_ctx* ctx, int ref_field, int query_field, int64_t ref_idx, float* out);
+
+/* KSG mutual-information volume (Sec. 3.2, Eq. 2; estimator of Sec. 6.2):
+ * out[v] = I(e^ref(p_ref); e^query(v)) in nats, FP32, for all N vertices.
+ * Algorithm 1: joint max-norm distances in FP32, eps_i = distance to the k-th
+ * nearest other member, n_x / n_y = members strictly closer than eps_i in each
+ * marginal (self excluded), I = psi(k) + psi(M) - <psi(n_x+1) + psi(n_y+1)>,
+ * the digamma sum in FP64.  Raw values, no jitter, no clamping of negative
+ * estimates.  Requires 1 <= k < M, k <= 16 and M <= 4096. */
+ndf_status ndf_mi_ksg(ndf_ctx* ctx, int ref_field, int query_field, int64_t ref_idx, int k,
+                      float* out);
+
+/* Test hook for one (reference, query) pair of the KSG path above: writes, in
+ * member order, eps[M] (k-th-neighbour distance), nx[M], ny[M] (marginal
+ * counts) and *mi (the FP64 estimate before rounding to FP32).  All four
+ * outputs are host pointers (any may be NULL).  Runs the same kernel as
+ * ndf_mi_ksg on a one-vertex range and synchronizes. */
+ndf_status ndf_ksg_debug_pair(ndf_ctx* ctx, int ref_field, int query_field, int64_t ref_idx,
+                              int64_t query_idx, int k, float* eps, int32_t* nx, int32_t* ny,
+                              double* mi);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NDF_H */

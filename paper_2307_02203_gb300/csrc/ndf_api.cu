@@ -1,0 +1,413 @@
+// C-ABI entry points of libndf.so: context, ensembles, exact estimators.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "device_common.cuh"
+#include "ndf_internal.h"
+
+namespace ndf {
+
+cudaError_t DevBuf::reserve(size_t need) {
+    if (need <= bytes && ptr) return cudaSuccess;
+    release();
+    size_t n = need < 256 ? 256 : need;
+    cudaError_t e = cudaMalloc(&ptr, n);
+    if (e != cudaSuccess) {
+        ptr = nullptr;
+        bytes = 0;
+        return e;
+    }
+    bytes = n;
+    return cudaSuccess;
+}
+
+void DevBuf::release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+}
+
+PtrKind pointer_kind(const void* p) {
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return PTR_HOST;
+    }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? PTR_DEVICE
+                                                                                : PTR_HOST;
+}
+
+ndf_status fail(ndf_ctx* ctx, ndf_status st, const char* fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        ctx->last_error = buf;
+    }
+    return st;
+}
+
+ndf_status cuda_fail(ndf_ctx* ctx, cudaError_t e, const char* what) {
+    ndf_status st = (e == cudaErrorMemoryAllocation) ? NDF_ERR_OOM : NDF_ERR_CUDA;
+    return fail(ctx, st, "%s: %s", what, cudaGetErrorString(e));
+}
+
+ndf_status check_pair(ndf_ctx* ctx, int ref_field, int query_field, int64_t ref_idx,
+                      const Field** rf, const Field** qf) {
+    int nf = (int)ctx->fields.size();
+    if (ref_field < 0 || ref_field >= nf || query_field < 0 || query_field >= nf)
+        return fail(ctx, NDF_ERR_ARG, "field id out of range");
+    const Field& a = ctx->fields[ref_field];
+    const Field& b = ctx->fields[query_field];
+    if (!a.live || !b.live) return fail(ctx, NDF_ERR_STATE, "field has been freed");
+    if (a.M != b.M || a.Z != b.Z || a.Y != b.Y || a.X != b.X)
+        return fail(ctx, NDF_ERR_ARG, "reference and query fields differ in shape");
+    if (ref_idx < 0 || ref_idx >= a.N)
+        return fail(ctx, NDF_ERR_ARG, "ref_idx %lld out of [0, %lld)", (long long)ref_idx,
+                    (long long)a.N);
+    *rf = &a;
+    *qf = &b;
+    return NDF_OK;
+}
+
+ndf_status resolve_out(ndf_ctx* ctx, void* out, size_t bytes, void** dev_out, bool* is_host) {
+    if (!out) return fail(ctx, NDF_ERR_ARG, "null output pointer");
+    if (pointer_kind(out) == PTR_DEVICE) {
+        *dev_out = out;
+        *is_host = false;
+        return NDF_OK;
+    }
+    cudaError_t e = ctx->out_tmp.reserve(bytes);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "output staging allocation");
+    *dev_out = ctx->out_tmp.ptr;
+    *is_host = true;
+    return NDF_OK;
+}
+
+// Reads and clears the device status word; call only after the stream has drained.
+ndf_status check_device_status(ndf_ctx* ctx) {
+    unsigned st = 0;
+    unsigned* d = ctx->flag.as<unsigned>() + 1;
+    cudaError_t e = cudaMemcpy(&st, d, sizeof st, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "device status read");
+    if (st == 0) return NDF_OK;
+    cudaMemset(d, 0, sizeof st);
+    if (st & kDevTimeout) return fail(ctx, NDF_ERR_TIMEOUT, "a bounded device wait gave up");
+    return fail(ctx, NDF_ERR_CUDA, "device reported status 0x%x", st);
+}
+
+ndf_status finish_out(ndf_ctx* ctx, void* out, const void* dev_out, size_t bytes, bool is_host) {
+    if (!is_host) return NDF_OK;
+    cudaError_t e = cudaMemcpyAsync(out, dev_out, bytes, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy of the result to the host");
+    return check_device_status(ctx);
+}
+
+// psi(n) at positive integers for the device table.  Shift n up to x >= 20 with
+// psi(x) = psi(x + 1) - 1/x, then the asymptotic series
+//   psi(x) ~ ln x - 1/(2x) - sum_j B_2j / (2j x^2j)
+// (Abramowitz & Stegun 6.3.18) through the x^-12 term; truncation < 1e-17.
+double digamma_int_host(int64_t n) {
+    double x = (double)n, shift = 0.0;
+    while (x < 20.0) {
+        shift += 1.0 / x;
+        x += 1.0;
+    }
+    double r = 1.0 / x, r2 = r * r;
+    double series = r2 * (1.0 / 12 - r2 * (1.0 / 120 - r2 * (1.0 / 252 - r2 * (1.0 / 240 -
+                    r2 * (1.0 / 132 - r2 * (691.0 / 32760))))));
+    return log(x) - 0.5 * r - series - shift;
+}
+
+ndf_status ensure_psi_table(ndf_ctx* ctx, int64_t n_max) {
+    if (ctx->psi_n > n_max) return NDF_OK;
+    int64_t n = n_max + 1;
+    std::vector<double> h((size_t)n, 0.0);
+    for (int64_t i = 1; i < n; ++i) h[(size_t)i] = digamma_int_host(i);
+    cudaError_t e = ctx->psi.reserve(sizeof(double) * (size_t)n);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->psi.ptr, h.data(), sizeof(double) * (size_t)n,
+                            cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "digamma table upload");
+    ctx->psi_n = n;
+    return NDF_OK;
+}
+
+}  // namespace ndf
+
+using namespace ndf;
+
+extern "C" {
+
+const char* ndf_status_str(int status) {
+    switch (status) {
+        case NDF_OK: return "ok";
+        case NDF_ERR_ARG: return "invalid argument";
+        case NDF_ERR_OOM: return "out of memory";
+        case NDF_ERR_CUDA: return "CUDA error";
+        case NDF_ERR_TIMEOUT: return "device wait timed out";
+        case NDF_ERR_STATE: return "invalid state";
+        case NDF_ERR_IO: return "I/O error";
+        default: return "unknown status";
+    }
+}
+
+ndf_status ndf_create(ndf_ctx** out, int device, void* cuda_stream) {
+    if (!out) return NDF_ERR_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return NDF_ERR_CUDA;
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return NDF_ERR_CUDA;
+    if (prop.major != 10 || prop.minor != 3) return NDF_ERR_CUDA;  // built for sm_103a only
+    if (cudaSetDevice(device) != cudaSuccess) return NDF_ERR_CUDA;
+    ndf_ctx* c = new (std::nothrow) ndf_ctx();
+    if (!c) return NDF_ERR_OOM;
+    c->device = device;
+    c->sm_count = prop.multiProcessorCount;
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return NDF_ERR_CUDA;
+        }
+        c->stream = c->own_stream;
+    }
+    if (c->flag.reserve(256) != cudaSuccess || cudaMemset(c->flag.ptr, 0, 256) != cudaSuccess) {
+        ndf_destroy(c);
+        return NDF_ERR_OOM;
+    }
+    *out = c;
+    return NDF_OK;
+}
+
+void ndf_destroy(ndf_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (auto& f : ctx->fields) {
+        if (f.data) cudaFree(f.data);
+        if (f.mean) cudaFree(f.mean);
+        if (f.inv_norm) cudaFree(f.inv_norm);
+    }
+    ctx->stage_x.release();
+    ctx->stage_perm.release();
+    ctx->out_tmp.release();
+    ctx->psi.release();
+    ctx->dbg.release();
+    ctx->flag.release();
+    if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+    delete ctx;
+}
+
+const char* ndf_last_error(const ndf_ctx* ctx) {
+    return ctx ? ctx->last_error.c_str() : "null context";
+}
+
+ndf_status ndf_set_stream(ndf_ctx* ctx, void* cuda_stream) {
+    if (!ctx) return NDF_ERR_ARG;
+    if (cuda_stream) {
+        ctx->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (!ctx->own_stream &&
+            cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(ctx, NDF_ERR_CUDA, "stream creation failed");
+        ctx->stream = ctx->own_stream;
+    }
+    return NDF_OK;
+}
+
+ndf_status ndf_synchronize(ndf_ctx* ctx) {
+    if (!ctx) return NDF_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
+    return check_device_status(ctx);
+}
+
+uint64_t ndf_launch_count(const ndf_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int64_t ndf_index(int64_t x, int64_t y, int64_t z, int64_t X, int64_t Y, int64_t Z) {
+    if (x < 0 || y < 0 || z < 0 || x >= X || y >= Y || z >= Z) return -1;
+    return (z * Y + y) * X + x;
+}
+
+ndf_status ndf_load_ensemble(ndf_ctx* ctx, const float* field, int64_t M, int64_t Z, int64_t Y,
+                             int64_t X, int* field_id_out) {
+    if (!ctx) return NDF_ERR_ARG;
+    if (!field || !field_id_out) return fail(ctx, NDF_ERR_ARG, "null pointer");
+    if (M < 2 || Z < 1 || Y < 1 || X < 1)
+        return fail(ctx, NDF_ERR_ARG, "need M >= 2 and a non-empty grid");
+    int64_t N = Z * Y * X;
+    if (N / X / Y != Z || M > (int64_t(1) << 40) / N)
+        return fail(ctx, NDF_ERR_ARG, "field too large");
+    cudaSetDevice(ctx->device);
+    Field f;
+    f.M = M; f.Z = Z; f.Y = Y; f.X = X; f.N = N;
+    size_t bytes = sizeof(float) * (size_t)M * (size_t)N;
+    cudaError_t e = cudaMalloc(&f.data, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&f.mean, sizeof(double) * (size_t)N);
+    if (e == cudaSuccess) e = cudaMalloc(&f.inv_norm, sizeof(double) * (size_t)N);
+    if (e != cudaSuccess) {
+        if (f.data) cudaFree(f.data);
+        if (f.mean) cudaFree(f.mean);
+        if (f.inv_norm) cudaFree(f.inv_norm);
+        return cuda_fail(ctx, e, "field allocation");
+    }
+    cudaMemcpyKind kind = pointer_kind(field) == PTR_DEVICE ? cudaMemcpyDeviceToDevice
+                                                            : cudaMemcpyHostToDevice;
+    int* d_flag = ctx->flag.as<int>();
+    e = cudaMemcpyAsync(f.data, field, bytes, kind, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_flag, 0, sizeof(int), ctx->stream);
+    if (e == cudaSuccess) e = launch_field_stats(ctx, f, d_flag);
+    int nonfinite = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&nonfinite, d_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess || nonfinite) {
+        cudaFree(f.data);
+        cudaFree(f.mean);
+        cudaFree(f.inv_norm);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "ensemble upload / statistics");
+        return fail(ctx, NDF_ERR_ARG, "field contains non-finite values");
+    }
+    f.live = true;
+    ctx->fields.push_back(f);
+    *field_id_out = (int)ctx->fields.size() - 1;
+    return NDF_OK;
+}
+
+ndf_status ndf_free_ensemble(ndf_ctx* ctx, int field_id) {
+    if (!ctx) return NDF_ERR_ARG;
+    if (field_id < 0 || field_id >= (int)ctx->fields.size())
+        return fail(ctx, NDF_ERR_ARG, "field id out of range");
+    Field& f = ctx->fields[field_id];
+    if (!f.live) return fail(ctx, NDF_ERR_STATE, "field already freed");
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(f.data);
+    cudaFree(f.mean);
+    cudaFree(f.inv_norm);
+    f.data = nullptr;
+    f.mean = f.inv_norm = nullptr;
+    f.live = false;
+    return NDF_OK;
+}
+
+ndf_status ndf_field_shape(const ndf_ctx* ctx, int field_id, int64_t* M, int64_t* Z, int64_t* Y,
+                           int64_t* X) {
+    if (!ctx || field_id < 0 || field_id >= (int)ctx->fields.size()) return NDF_ERR_ARG;
+    const Field& f = ctx->fields[field_id];
+    if (!f.live) return NDF_ERR_STATE;
+    if (M) *M = f.M;
+    if (Z) *Z = f.Z;
+    if (Y) *Y = f.Y;
+    if (X) *X = f.X;
+    return NDF_OK;
+}
+
+ndf_status ndf_field_stats(ndf_ctx* ctx, int field_id, double* mean_out, double* inv_norm_out) {
+    if (!ctx) return NDF_ERR_ARG;
+    if (field_id < 0 || field_id >= (int)ctx->fields.size())
+        return fail(ctx, NDF_ERR_ARG, "field id out of range");
+    const Field& f = ctx->fields[field_id];
+    if (!f.live) return fail(ctx, NDF_ERR_STATE, "field has been freed");
+    size_t bytes = sizeof(double) * (size_t)f.N;
+    cudaError_t e = cudaSuccess;
+    if (mean_out) e = cudaMemcpyAsync(mean_out, f.mean, bytes, cudaMemcpyDefault, ctx->stream);
+    if (e == cudaSuccess && inv_norm_out)
+        e = cudaMemcpyAsync(inv_norm_out, f.inv_norm, bytes, cudaMemcpyDefault, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "statistics copy");
+    return NDF_OK;
+}
+
+ndf_status ndf_pearson(ndf_ctx* ctx, int ref_field, int query_field, int64_t ref_idx, float* out) {
+    if (!ctx) return NDF_ERR_ARG;
+    const Field *rf, *qf;
+    ndf_status st = check_pair(ctx, ref_field, query_field, ref_idx, &rf, &qf);
+    if (st != NDF_OK) return st;
+    cudaSetDevice(ctx->device);
+    size_t bytes = sizeof(float) * (size_t)qf->N;
+    void* dev_out;
+    bool is_host;
+    if ((st = resolve_out(ctx, out, bytes, &dev_out, &is_host)) != NDF_OK) return st;
+    cudaError_t e = launch_pearson(ctx, *rf, *qf, ref_idx, (float*)dev_out);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "pearson launch");
+    return finish_out(ctx, out, dev_out, bytes, is_host);
+}
+
+static ndf_status check_ksg_args(ndf_ctx* ctx, const Field* rf, int k) {
+    if (k < 1 || k >= rf->M) return fail(ctx, NDF_ERR_ARG, "need 1 <= k < M (k=%d)", k);
+    if (k > kKsgMaxK) return fail(ctx, NDF_ERR_ARG, "k=%d above the supported %d", k, kKsgMaxK);
+    if (rf->M > kKsgMaxM)
+        return fail(ctx, NDF_ERR_ARG, "M=%lld above the supported %d", (long long)rf->M, kKsgMaxM);
+    return NDF_OK;
+}
+
+ndf_status ndf_mi_ksg(ndf_ctx* ctx, int ref_field, int query_field, int64_t ref_idx, int k,
+                      float* out) {
+    if (!ctx) return NDF_ERR_ARG;
+    const Field *rf, *qf;
+    ndf_status st = check_pair(ctx, ref_field, query_field, ref_idx, &rf, &qf);
+    if (st != NDF_OK) return st;
+    if ((st = check_ksg_args(ctx, rf, k)) != NDF_OK) return st;
+    cudaSetDevice(ctx->device);
+    if ((st = ensure_psi_table(ctx, rf->M + 1)) != NDF_OK) return st;
+    size_t bytes = sizeof(float) * (size_t)qf->N;
+    void* dev_out;
+    bool is_host;
+    if ((st = resolve_out(ctx, out, bytes, &dev_out, &is_host)) != NDF_OK) return st;
+    cudaError_t e = launch_ksg(ctx, *rf, *qf, ref_idx, k, 0, qf->N, (float*)dev_out, nullptr,
+                               nullptr, nullptr, nullptr);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "ksg launch");
+    return finish_out(ctx, out, dev_out, bytes, is_host);
+}
+
+ndf_status ndf_ksg_debug_pair(ndf_ctx* ctx, int ref_field, int query_field, int64_t ref_idx,
+                              int64_t query_idx, int k, float* eps, int32_t* nx, int32_t* ny,
+                              double* mi) {
+    if (!ctx) return NDF_ERR_ARG;
+    const Field *rf, *qf;
+    ndf_status st = check_pair(ctx, ref_field, query_field, ref_idx, &rf, &qf);
+    if (st != NDF_OK) return st;
+    if (query_idx < 0 || query_idx >= qf->N) return fail(ctx, NDF_ERR_ARG, "query_idx out of range");
+    if ((st = check_ksg_args(ctx, rf, k)) != NDF_OK) return st;
+    cudaSetDevice(ctx->device);
+    if ((st = ensure_psi_table(ctx, rf->M + 1)) != NDF_OK) return st;
+    int64_t M = rf->M;
+    // layout of the debug block: mi (double) | out (float) | eps[M] | nx[M] | ny[M]
+    size_t need = 16 + sizeof(float) * (size_t)M * 3 + 64;
+    cudaError_t e = ctx->dbg.reserve(need);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "debug buffer");
+    char* base = ctx->dbg.as<char>();
+    double* d_mi = (double*)base;
+    float* d_out = (float*)(base + 8);
+    float* d_eps = (float*)(base + 16);
+    int32_t* d_nx = (int32_t*)(d_eps + M);
+    int32_t* d_ny = d_nx + M;
+    e = launch_ksg(ctx, *rf, *qf, ref_idx, k, query_idx, query_idx + 1, d_out, d_mi,
+                   d_eps, d_nx, d_ny);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "ksg debug launch");
+    std::vector<char> h(need);
+    e = cudaMemcpyAsync(h.data(), base, need, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "ksg debug copy");
+    const char* hb = h.data();
+    if (mi) memcpy(mi, hb, sizeof(double));
+    if (eps) memcpy(eps, hb + 16, sizeof(float) * (size_t)M);
+    if (nx) memcpy(nx, hb + 16 + 4 * M, sizeof(int32_t) * (size_t)M);
+    if (ny) memcpy(ny, hb + 16 + 8 * M, sizeof(int32_t) * (size_t)M);
+    return NDF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,85 @@
+// Internal declarations shared by the CUDA translation units of libndf.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "ndf.h"
+
+namespace ndf {
+
+// A device allocation owned by the context; grows on demand, never shrinks.
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    cudaError_t reserve(size_t need);
+    void release();
+    template <class T>
+    T* as() const { return static_cast<T*>(ptr); }
+};
+
+struct Field {
+    bool live = false;
+    int64_t M = 0, Z = 0, Y = 0, X = 0, N = 0;
+    float* data = nullptr;     // [M][N]
+    double* mean = nullptr;    // [N]
+    double* inv_norm = nullptr;// [N] 1/sqrt(sum (e - mean)^2), 0 when the sum is 0
+};
+
+}  // namespace ndf
+
+struct ndf_ctx {
+    int device = 0;
+    int sm_count = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;
+    std::vector<ndf::Field> fields;
+    std::string last_error;
+    uint64_t launches = 0;
+    // scratch
+    ndf::DevBuf stage_x;     // reference column: centred values (Pearson) / sorted values (KSG)
+    ndf::DevBuf stage_perm;  // KSG: member index of each sorted position
+    ndf::DevBuf out_tmp;     // device output staging when the caller passes host memory
+    ndf::DevBuf psi;         // digamma table psi(0..psi_n-1), FP64
+    int64_t psi_n = 0;
+    ndf::DevBuf dbg;         // KSG debug outputs
+    ndf::DevBuf flag;        // small device status words
+};
+
+namespace ndf {
+
+enum PtrKind { PTR_HOST = 0, PTR_DEVICE = 1 };
+PtrKind pointer_kind(const void* p);
+
+ndf_status fail(ndf_ctx* ctx, ndf_status st, const char* fmt, ...);
+ndf_status cuda_fail(ndf_ctx* ctx, cudaError_t e, const char* what);
+
+// Validates field ids, shapes and the reference index; on success returns the fields.
+ndf_status check_pair(ndf_ctx* ctx, int ref_field, int query_field, int64_t ref_idx,
+                      const Field** rf, const Field** qf);
+
+// Resolves an output pointer: device pointers are used directly, host pointers
+// get a context-owned device staging buffer of `bytes`.
+ndf_status resolve_out(ndf_ctx* ctx, void* out, size_t bytes, void** dev_out, bool* is_host);
+ndf_status check_device_status(ndf_ctx* ctx);
+ndf_status finish_out(ndf_ctx* ctx, void* out, const void* dev_out, size_t bytes, bool is_host);
+
+// Digamma psi(n) for n = 0..n_max (entry 0 unused), FP64, on the device.
+ndf_status ensure_psi_table(ndf_ctx* ctx, int64_t n_max);
+double digamma_int_host(int64_t n);
+
+// kernels (launch wrappers; each returns the launch error)
+cudaError_t launch_field_stats(ndf_ctx* ctx, const Field& f, int* d_nonfinite);
+cudaError_t launch_pearson(ndf_ctx* ctx, const Field& rf, const Field& qf, int64_t ref_idx,
+                           float* out);
+cudaError_t launch_ksg(ndf_ctx* ctx, const Field& rf, const Field& qf, int64_t ref_idx, int k,
+                       int64_t v_begin, int64_t v_end, float* out, double* dbg_mi, float* dbg_eps,
+                       int32_t* dbg_nx, int32_t* dbg_ny);
+
+constexpr int kKsgMaxM = 4096;
+constexpr int kKsgMaxK = 16;
+
+}  // namespace ndf

@@ -1,0 +1,166 @@
+"""Thin ctypes binding of libndf.so: the C-ABI calls under the same names.
+
+Argument marshalling only -- every step of the computation runs in the
+library's CUDA kernels.  Arrays may be torch tensors (host or CUDA), numpy
+arrays or raw integer addresses; the library itself detects host vs device
+memory.  A non-zero status raises :class:`NdfError` carrying the library's
+last-error string.  There is no CPU fallback: if ``libndf.so`` has not been
+built, importing this module raises ``ImportError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libndf.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with `python -m paper_2307_02203_gb300.build` "
+        "(the library has no CPU fallback)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+NDF_OK, NDF_ERR_ARG, NDF_ERR_OOM, NDF_ERR_CUDA = 0, -1, -2, -3
+NDF_ERR_TIMEOUT, NDF_ERR_STATE, NDF_ERR_IO = -4, -5, -6
+NDF_PREC_FP32, NDF_PREC_BF16X3, NDF_PREC_TF32 = 0, 1, 2
+NDF_MEASURE_PEARSON, NDF_MEASURE_MI_KSG = 0, 1
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+
+
+class NdfError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        self.status = status
+        super().__init__(f"{where}: {_lib.ndf_status_str(status).decode()} ({status}): {detail}")
+
+
+def _sig(name, res, args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+_sig("ndf_status_str", ctypes.c_char_p, [ctypes.c_int])
+_sig("ndf_last_error", ctypes.c_char_p, [_vp])
+_sig("ndf_create", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _vp])
+_sig("ndf_destroy", None, [_vp])
+_sig("ndf_set_stream", ctypes.c_int, [_vp, _vp])
+_sig("ndf_synchronize", ctypes.c_int, [_vp])
+_sig("ndf_launch_count", ctypes.c_uint64, [_vp])
+_sig("ndf_index", _i64, [_i64, _i64, _i64, _i64, _i64, _i64])
+_sig("ndf_load_ensemble", ctypes.c_int, [_vp, _vp, _i64, _i64, _i64, _i64,
+                                         ctypes.POINTER(ctypes.c_int)])
+_sig("ndf_free_ensemble", ctypes.c_int, [_vp, ctypes.c_int])
+_sig("ndf_field_shape", ctypes.c_int, [_vp, ctypes.c_int] + [ctypes.POINTER(_i64)] * 4)
+_sig("ndf_field_stats", ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp])
+_sig("ndf_pearson", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, _vp])
+_sig("ndf_mi_ksg", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, ctypes.c_int, _vp])
+_sig("ndf_ksg_debug_pair", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, _i64,
+                                          ctypes.c_int, _vp, _vp, _vp, _vp])
+
+
+def _addr(x):
+    """Address of a torch tensor / numpy array / int / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):  # torch.Tensor
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):  # numpy
+        if not x.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)!r}")
+
+
+def _check(ctx, st, where):
+    if st != NDF_OK:
+        detail = _lib.ndf_last_error(ctx).decode() if ctx else ""
+        raise NdfError(st, where, detail)
+
+
+def ndf_status_str(status: int) -> str:
+    return _lib.ndf_status_str(status).decode()
+
+
+def ndf_last_error(ctx) -> str:
+    return _lib.ndf_last_error(ctx).decode()
+
+
+def ndf_create(device: int = 0, cuda_stream=None):
+    """Returns an opaque context handle; ``cuda_stream`` is a raw cudaStream_t (int) or None."""
+    h = _vp()
+    st = _lib.ndf_create(ctypes.byref(h), int(device), cuda_stream)
+    if st != NDF_OK:
+        raise NdfError(st, "ndf_create", "no usable sm_103 device" if st == NDF_ERR_CUDA else "")
+    return h
+
+
+def ndf_destroy(ctx) -> None:
+    _lib.ndf_destroy(ctx)
+
+
+def ndf_set_stream(ctx, cuda_stream=None) -> None:
+    _check(ctx, _lib.ndf_set_stream(ctx, cuda_stream), "ndf_set_stream")
+
+
+def ndf_synchronize(ctx) -> None:
+    _check(ctx, _lib.ndf_synchronize(ctx), "ndf_synchronize")
+
+
+def ndf_launch_count(ctx) -> int:
+    return int(_lib.ndf_launch_count(ctx))
+
+
+def ndf_index(x, y, z, X, Y, Z) -> int:
+    return int(_lib.ndf_index(x, y, z, X, Y, Z))
+
+
+def ndf_load_ensemble(ctx, field, M, Z, Y, X) -> int:
+    fid = ctypes.c_int(-1)
+    _check(ctx, _lib.ndf_load_ensemble(ctx, _addr(field), M, Z, Y, X, ctypes.byref(fid)),
+           "ndf_load_ensemble")
+    return fid.value
+
+
+def ndf_free_ensemble(ctx, field_id: int) -> None:
+    _check(ctx, _lib.ndf_free_ensemble(ctx, field_id), "ndf_free_ensemble")
+
+
+def ndf_field_shape(ctx, field_id: int):
+    v = [_i64() for _ in range(4)]
+    _check(ctx, _lib.ndf_field_shape(ctx, field_id, *[ctypes.byref(t) for t in v]),
+           "ndf_field_shape")
+    return tuple(t.value for t in v)  # (M, Z, Y, X)
+
+
+def ndf_field_stats(ctx, field_id: int, mean_out, inv_norm_out) -> None:
+    _check(ctx, _lib.ndf_field_stats(ctx, field_id, _addr(mean_out), _addr(inv_norm_out)),
+           "ndf_field_stats")
+
+
+def ndf_pearson(ctx, ref_field: int, query_field: int, ref_idx: int, out) -> None:
+    _check(ctx, _lib.ndf_pearson(ctx, ref_field, query_field, ref_idx, _addr(out)), "ndf_pearson")
+
+
+def ndf_mi_ksg(ctx, ref_field: int, query_field: int, ref_idx: int, k: int, out) -> None:
+    _check(ctx, _lib.ndf_mi_ksg(ctx, ref_field, query_field, ref_idx, k, _addr(out)),
+           "ndf_mi_ksg")
+
+
+def ndf_ksg_debug_pair(ctx, ref_field, query_field, ref_idx, query_idx, k, eps, nx, ny, mi) -> None:
+    _check(ctx, _lib.ndf_ksg_debug_pair(ctx, ref_field, query_field, ref_idx, query_idx, k,
+                                        _addr(eps), _addr(nx), _addr(ny), _addr(mi)),
+           "ndf_ksg_debug_pair")
+
+
+def exported_symbols():
+    """Every ndf_* function name this binding declares."""
+    return sorted(n for n in globals() if n.startswith("ndf_") and callable(globals()[n]))

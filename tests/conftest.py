@@ -29,3 +29,25 @@ def tiny_ref():
 
     x, y, z = synth.TINY_REF
     return synth.vertex_index(x, y, z, synth.TINY)
+
+
+@pytest.fixture(scope="session")
+def ndf_mod():
+    """The ctypes binding over a freshly built libndf.so (GPU tests only)."""
+    from paper_2307_02203_gb300 import build
+
+    build.build()
+    from paper_2307_02203_gb300 import ndf
+
+    return ndf
+
+
+@pytest.fixture(scope="session")
+def ctx(ndf_mod):
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.init()
+    c = ndf_mod.ndf_create(0, None)
+    yield c
+    ndf_mod.ndf_destroy(c)

@@ -1,0 +1,238 @@
+"""GPU parity of the exact estimators against the CPU oracle (same seeded bytes).
+
+Bars (element by element):
+  Pearson            |r_gpu - r_oracle(FP64)| <= 1e-5
+  KSG eps, nx, ny    bit-exact (FP32 max-norm distances are computed identically)
+  KSG MI             |mi_gpu - mi_oracle| <= 1e-6 |mi_oracle| + 1e-9
+                     (the FP32 volume adds at most 2^-24 relative rounding)
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+PEARSON_TOL = 1e-5
+
+
+def mi_close(gpu, ref):
+    gpu = np.asarray(gpu, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    bad = np.abs(gpu - ref) > 1e-6 * np.abs(ref) + 1e-9
+    return not bad.any(), np.flatnonzero(bad)[:10]
+
+
+def load(ndf, ctx, field):
+    f = np.ascontiguousarray(field, dtype=np.float32)
+    M, Z, Y, X = f.shape
+    return ndf.ndf_load_ensemble(ctx, f, M, Z, Y, X)
+
+
+def rand_field(shape, seed, kind="normal"):
+    rng = np.random.default_rng(seed)
+    f = rng.normal(size=shape)
+    if kind == "ties":
+        f = np.round(f * 2.0) / 2.0
+    return f.astype(np.float32)
+
+
+# ---------------------------------------------------------------- statistics (load)
+def test_load_statistics(ndf_mod, ctx, tiny_field):
+    fid = load(ndf_mod, ctx, tiny_field)
+    M = tiny_field.shape[0]
+    N = tiny_field[0].size
+    mean = np.empty(N)
+    inv = np.empty(N)
+    ndf_mod.ndf_field_stats(ctx, fid, mean, inv)
+    f64 = tiny_field.reshape(M, N).astype(np.float64)
+    mu = f64.mean(axis=0)
+    S = ((f64 - mu) ** 2).sum(axis=0)
+    np.testing.assert_allclose(mean, mu, rtol=0, atol=1e-5 * np.abs(f64).max())
+    np.testing.assert_allclose(inv, 1.0 / np.sqrt(S), rtol=1e-5)
+    assert ndf_mod.ndf_field_shape(ctx, fid) == tiny_field.shape
+    ndf_mod.ndf_free_ensemble(ctx, fid)
+
+
+def test_load_from_device_memory(ndf_mod, ctx, tiny_field, tiny_ref):
+    t = torch.from_numpy(tiny_field).cuda()
+    fid = ndf_mod.ndf_load_ensemble(ctx, t, *tiny_field.shape)
+    out = np.empty(tiny_field[0].size, dtype=np.float32)
+    ndf_mod.ndf_pearson(ctx, fid, fid, tiny_ref, out)
+    ref = oracle.pearson_volume(tiny_field, tiny_field, tiny_ref)
+    assert np.abs(out - ref).max() <= PEARSON_TOL
+    ndf_mod.ndf_free_ensemble(ctx, fid)
+
+
+# ---------------------------------------------------------------- Pearson (Eq. 1)
+def test_pearson_tiny_host_and_device_outputs(ndf_mod, ctx, tiny_field, tiny_ref):
+    fid = load(ndf_mod, ctx, tiny_field)
+    N = tiny_field[0].size
+    ref = oracle.pearson_volume(tiny_field, tiny_field, tiny_ref)
+    host = np.empty(N, dtype=np.float32)
+    ndf_mod.ndf_pearson(ctx, fid, fid, tiny_ref, host)
+    dev = torch.empty(N, dtype=torch.float32, device="cuda")
+    ndf_mod.ndf_pearson(ctx, fid, fid, tiny_ref, dev)
+    ndf_mod.ndf_synchronize(ctx)
+    assert np.abs(host - ref).max() <= PEARSON_TOL
+    np.testing.assert_array_equal(dev.cpu().numpy(), host)
+    assert host[tiny_ref] == pytest.approx(1.0, abs=1e-6)
+    ndf_mod.ndf_free_ensemble(ctx, fid)
+
+
+@pytest.mark.parametrize("shape", [(1000, 4, 10, 25),   # N % 4 == 0: vector path, many CTAs
+                                   (37, 3, 5, 7),        # N odd: scalar path, ragged tail
+                                   (2, 1, 1, 3),         # smallest M
+                                   (2500, 2, 4, 9),      # more members than one staged chunk
+                                   (64, 1, 1, 1)])       # a single vertex
+def test_pearson_shapes(ndf_mod, ctx, shape):
+    f = rand_field(shape, seed=sum(shape))
+    f[:, 0, 0, 0] += 3.0 * f[:, -1, -1, -1]  # some real dependence
+    fid = load(ndf_mod, ctx, f)
+    N = f[0].size
+    for r in sorted({0, N // 2, N - 1}):
+        out = np.empty(N, dtype=np.float32)
+        ndf_mod.ndf_pearson(ctx, fid, fid, r, out)
+        ref = oracle.pearson_volume(f, f, r)
+        assert np.abs(out - ref).max() <= PEARSON_TOL, (shape, r)
+    ndf_mod.ndf_free_ensemble(ctx, fid)
+
+
+def test_pearson_cross_field_and_degenerate(ndf_mod, ctx):
+    shape = (200, 2, 6, 10)
+    a = rand_field(shape, 11)
+    b = (0.6 * a + 0.8 * rand_field(shape, 12)).astype(np.float32)
+    b[:, 1, 2, 3] = 7.0  # constant query column: r = 0
+    fa, fb = load(ndf_mod, ctx, a), load(ndf_mod, ctx, b)
+    out = np.empty(a[0].size, dtype=np.float32)
+    ndf_mod.ndf_pearson(ctx, fa, fb, 17, out)
+    ref = oracle.pearson_volume(a, b, 17)
+    assert np.abs(out - ref).max() <= PEARSON_TOL
+    assert out[(1 * 6 + 2) * 10 + 3] == 0.0
+    ndf_mod.ndf_free_ensemble(ctx, fa)
+    ndf_mod.ndf_free_ensemble(ctx, fb)
+
+
+# ---------------------------------------------------------------- KSG algorithm 1
+def ksg_debug(ndf, ctx, fa, fb, r, v, k, M):
+    eps = np.empty(M, dtype=np.float32)
+    nx = np.empty(M, dtype=np.int32)
+    ny = np.empty(M, dtype=np.int32)
+    mi = np.empty(1, dtype=np.float64)
+    ndf.ndf_ksg_debug_pair(ctx, fa, fb, r, v, k, eps, nx, ny, mi)
+    return mi[0], eps, nx, ny
+
+
+def check_pairs_bit_exact(ndf, ctx, fa, fb, a, b, r, verts, k):
+    M = a.shape[0]
+    a2 = a.reshape(M, -1)
+    b2 = b.reshape(M, -1)
+    for v in verts:
+        g = ksg_debug(ndf, ctx, fa, fb, r, int(v), k, M)
+        o = oracle.ksg_pair(a2[:, r], b2[:, v], k)
+        np.testing.assert_array_equal(g[1], o[1], err_msg=f"eps v={v}")
+        np.testing.assert_array_equal(g[2], o[2], err_msg=f"nx v={v}")
+        np.testing.assert_array_equal(g[3], o[3], err_msg=f"ny v={v}")
+        assert abs(g[0] - o[0]) <= 1e-6 * abs(o[0]) + 1e-9, (v, g[0], o[0])
+
+
+def test_ksg_tiny_every_pair_bit_exact(ndf_mod, ctx, tiny_field, tiny_ref):
+    fid = load(ndf_mod, ctx, tiny_field)
+    N = tiny_field[0].size
+    check_pairs_bit_exact(ndf_mod, ctx, fid, fid, tiny_field, tiny_field, tiny_ref, range(N), 4)
+    ndf_mod.ndf_free_ensemble(ctx, fid)
+
+
+def test_ksg_tiny_volume(ndf_mod, ctx, tiny_field, tiny_ref):
+    fid = load(ndf_mod, ctx, tiny_field)
+    N = tiny_field[0].size
+    out = np.empty(N, dtype=np.float32)
+    ndf_mod.ndf_mi_ksg(ctx, fid, fid, tiny_ref, 4, out)
+    ref = oracle.ksg_volume(tiny_field, tiny_field, tiny_ref, 4)
+    ok, where = mi_close(out, ref)
+    assert ok, where
+    dev = torch.empty(N, dtype=torch.float32, device="cuda")
+    ndf_mod.ndf_mi_ksg(ctx, fid, fid, tiny_ref, 4, dev)
+    ndf_mod.ndf_synchronize(ctx)
+    np.testing.assert_array_equal(dev.cpu().numpy(), out)  # deterministic
+    ndf_mod.ndf_free_ensemble(ctx, fid)
+
+
+@pytest.mark.parametrize("shape,k,kind", [
+    ((1000, 2, 8, 25), 8, "normal"),   # paper-scale M, several tiles + ragged tail
+    ((1000, 1, 3, 7), 8, "ties"),      # heavy ties: eps = 0 and equal distances
+    ((2500, 1, 2, 9), 8, "normal"),    # M > 2048: threads own two point blocks
+    ((2, 1, 2, 2), 1, "normal"),       # smallest M
+    ((17, 1, 3, 3), 16, "normal"),     # k = M - 1 = 16 (largest supported k)
+    ((100, 2, 3, 5), 3, "ties"),
+    ((333, 1, 1, 13), 5, "normal"),    # M not a multiple of 4
+])
+def test_ksg_shapes(ndf_mod, ctx, shape, k, kind):
+    f = rand_field(shape, seed=shape[0] + k, kind=kind)
+    f[:, 0, 0, 0] = f[:, -1, -1, -1] ** 2 + 0.1 * f[:, 0, 0, 0]
+    fid = load(ndf_mod, ctx, f)
+    N = f[0].size
+    r = N - 1
+    out = np.empty(N, dtype=np.float32)
+    ndf_mod.ndf_mi_ksg(ctx, fid, fid, r, k, out)
+    ref = oracle.ksg_volume(f, f, r, k)
+    ok, where = mi_close(out, ref)
+    assert ok, (where, out[where], ref[where])
+    check_pairs_bit_exact(ndf_mod, ctx, fid, fid, f, f, r, sorted({0, 1, N // 2, N - 1}), k)
+    ndf_mod.ndf_free_ensemble(ctx, fid)
+
+
+def test_ksg_cross_field(ndf_mod, ctx):
+    shape = (300, 2, 4, 6)
+    a = rand_field(shape, 21)
+    b = (np.tanh(a) + 0.5 * rand_field(shape, 22)).astype(np.float32)
+    fa, fb = load(ndf_mod, ctx, a), load(ndf_mod, ctx, b)
+    N = a[0].size
+    out = np.empty(N, dtype=np.float32)
+    ndf_mod.ndf_mi_ksg(ctx, fa, fb, 5, 8, out)
+    ok, where = mi_close(out, oracle.ksg_volume(a, b, 5, 8))
+    assert ok, where
+    check_pairs_bit_exact(ndf_mod, ctx, fa, fb, a, b, 5, [0, 5, N - 1], 8)
+    ndf_mod.ndf_free_ensemble(ctx, fa)
+    ndf_mod.ndf_free_ensemble(ctx, fb)
+
+
+# ---------------------------------------------------------------- argument errors
+def test_argument_errors(ndf_mod, ctx, tiny_field, tiny_ref):
+    ndf = ndf_mod
+    fid = load(ndf, ctx, tiny_field)
+    N = tiny_field[0].size
+    out = np.empty(N, dtype=np.float32)
+    cases = [
+        lambda: ndf.ndf_mi_ksg(ctx, fid, fid, tiny_ref, 0, out),
+        lambda: ndf.ndf_mi_ksg(ctx, fid, fid, tiny_ref, 100, out),
+        lambda: ndf.ndf_mi_ksg(ctx, fid, fid, tiny_ref, 17, out),
+        lambda: ndf.ndf_pearson(ctx, fid, fid, N, out),
+        lambda: ndf.ndf_pearson(ctx, fid, fid, -1, out),
+        lambda: ndf.ndf_pearson(ctx, fid, 99, 0, out),
+        lambda: ndf.ndf_pearson(ctx, fid, fid, 0, None),
+    ]
+    for c in cases:
+        with pytest.raises(ndf.NdfError) as ei:
+            c()
+        assert ei.value.status == ndf.NDF_ERR_ARG
+    other = load(ndf, ctx, tiny_field[:, :2])
+    with pytest.raises(ndf.NdfError) as ei:
+        ndf.ndf_pearson(ctx, fid, other, 0, out)
+    assert ei.value.status == ndf.NDF_ERR_ARG
+    bad = tiny_field.copy()
+    bad[3, 0, 0, 0] = np.nan
+    with pytest.raises(ndf.NdfError) as ei:
+        load(ndf, ctx, bad)
+    assert ei.value.status == ndf.NDF_ERR_ARG
+    with pytest.raises(ndf.NdfError) as ei:
+        ndf.ndf_load_ensemble(ctx, tiny_field, 1, 4, 16, 16)
+    assert ei.value.status == ndf.NDF_ERR_ARG
+    ndf.ndf_free_ensemble(ctx, other)
+    with pytest.raises(ndf.NdfError) as ei:
+        ndf.ndf_pearson(ctx, other, other, 0, out)
+    assert ei.value.status == ndf.NDF_ERR_STATE
+    ndf.ndf_free_ensemble(ctx, fid)
+    assert ndf.ndf_launch_count(ctx) > 0
