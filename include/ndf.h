@@ -123,6 +123,39 @@ ndf_status ndf_ksg_debug_pair(ndf_ctx* ctx, int ref_field, int query_field, int6
                               int64_t query_idx, int k, float* eps, int32_t* nx, int32_t* ny,
                               double* mi);
 
+/* ---- allocation-free variant --------------------------------------------- */
+
+/* Largest member count ndf_pearson_noalloc accepts. */
+#define NDF_NOALLOC_MAX_M 16384
+
+/* Pearson volume that allocates no memory at all (no cudaMalloc, no cudaFree,
+ * no allocating library call), for callers that cannot allocate device memory:
+ * applications whose own allocator or pool owns the device budget, or whose
+ * frame loop cannot absorb the device-wide synchronisation an allocation may
+ * cause.  The paper has no counterpart; it is an addition of this library.
+ *
+ * Same result as ndf_pearson (Eq. 1 for every vertex, FP32, clamped, 0 for
+ * zero variance) but without a context or a loaded ensemble: ref_field and
+ * query_field are caller-owned DEVICE buffers float[M][N] (member-major, may be
+ * the same buffer), out is a caller-owned DEVICE buffer of N floats, and the
+ * work is enqueued on cuda_stream (NULL = legacy default stream); the call
+ * returns without synchronising.  The query statistics are formed in the same
+ * pass, so nothing needs to be loaded first.
+ *
+ * Scratch: a fixed 64 KB file-scope device array (NDF_NOALLOC_MAX_M floats and
+ * two doubles) that every GPU loading the library holds until the process
+ * exits.  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call before
+ * any stream capture.  All calls share the array and each rewrites what it
+ * reads, so calls that overlap on the GPU (other streams, other threads) race:
+ * serialise them.
+ *
+ * Errors: NDF_ERR_ARG for a null or non-device pointer, M < 2,
+ * M > NDF_NOALLOC_MAX_M, N < 1 or ref_idx outside [0, N); NDF_ERR_CUDA when
+ * the set-up or a launch fails.  There is no context, so no error string. */
+ndf_status ndf_pearson_noalloc(const float* ref_field, const float* query_field, int64_t M,
+                               int64_t N, int64_t ref_idx, float* out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

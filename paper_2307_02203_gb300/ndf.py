@@ -59,6 +59,7 @@ _sig("ndf_field_shape", ctypes.c_int, [_vp, ctypes.c_int] + [ctypes.POINTER(_i64
 _sig("ndf_field_stats", ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp])
 _sig("ndf_pearson", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, _vp])
 _sig("ndf_mi_ksg", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, ctypes.c_int, _vp])
+_sig("ndf_pearson_noalloc", ctypes.c_int, [_vp, _vp, _i64, _i64, _i64, _vp, _vp])
 _sig("ndf_ksg_debug_pair", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, _i64,
                                           ctypes.c_int, _vp, _vp, _vp, _vp])
 
@@ -159,6 +160,14 @@ def ndf_ksg_debug_pair(ctx, ref_field, query_field, ref_idx, query_idx, k, eps, 
     _check(ctx, _lib.ndf_ksg_debug_pair(ctx, ref_field, query_field, ref_idx, query_idx, k,
                                         _addr(eps), _addr(nx), _addr(ny), _addr(mi)),
            "ndf_ksg_debug_pair")
+
+
+def ndf_pearson_noalloc(ref_field, query_field, M, N, ref_idx, out, cuda_stream=None) -> None:
+    """Allocation-free Pearson volume: device buffers only, enqueued on cuda_stream."""
+    st = _lib.ndf_pearson_noalloc(_addr(ref_field), _addr(query_field), M, N, ref_idx,
+                                  _addr(out), cuda_stream)
+    if st != NDF_OK:
+        raise NdfError(st, "ndf_pearson_noalloc", "see include/ndf.h for the argument limits")
 
 
 def exported_symbols():
