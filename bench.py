@@ -33,7 +33,11 @@ if ROOT not in sys.path:
 
 K_NN = 8
 METRIC = "ms per 1.76M-voxel dependence volume (Pearson + KSG MI k=8, M=1000)"
-WORKLOAD = "csens-like ensemble 250x352x20 (N=1,760,000), M=1000 FP32 members, one reference per volume"
+
+
+def workload_name(recipe):
+    return (f"csens-like ensemble {recipe.X}x{recipe.Y}x{recipe.Z} (N={recipe.N:,}), "
+            f"M={recipe.M} FP32 members, one reference per volume")
 
 
 def env_int(name, default):
@@ -161,6 +165,49 @@ def cpu_baseline(field, recipe, ref, seconds_target, seed):
             "pearson_ms": tp * scale * 1e3, "ksg_ms": tk * scale * 1e3}
 
 
+def measure_pearson_batch(ndf, ctx, fid, field, recipe, stream, rank, R=64, reps=3):
+    """Times ndf_pearson_batch for R references per precision (the standardised
+    copies are built by an untimed first call) and states the error of each
+    precision against the FP64 oracle on a seeded vertex sample."""
+    import torch
+
+    import oracle
+    import synth
+
+    N, M = recipe.N, recipe.M
+    rng = np.random.default_rng(4242 + rank)
+    refs = [int(r) for r in rng.integers(0, N, size=R)]
+    out = torch.empty((R, N), dtype=torch.float32, device="cuda")
+    verts = synth.sample_vertices(recipe, 512, seed=99)
+    want = np.stack([oracle.pearson_volume(field, field, r, verts=verts) for r in refs])
+    res = {"refs": R}
+    for name, code in (("tf32", ndf.NDF_PREC_TF32), ("bf16x3", ndf.NDF_PREC_BF16X3),
+                       ("fp32", ndf.NDF_PREC_FP32)):
+        ndf.ndf_pearson_batch(ctx, fid, fid, refs, code, out)  # builds the copy, warms up
+        ndf.ndf_synchronize(ctx)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(reps):
+            ndf.ndf_pearson_batch(ctx, fid, fid, refs, code, out)
+        ev1.record(stream)
+        ndf.ndf_synchronize(ctx)
+        ms = ev0.elapsed_time(ev1) / reps
+        got = out[:, torch.from_numpy(verts).cuda()].cpu().numpy().astype(np.float64)
+        err = np.abs(got - want)
+        kp = (M + 63) // 64 * 64
+        zbytes = {"tf32": 4, "bf16x3": 4, "fp32": None}[name]
+        entry = {"ms": ms, "ms_per_volume": ms / R, "max_abs_err_vs_fp64": float(err.max()),
+                 "mean_abs_err_vs_fp64": float(err.mean())}
+        if zbytes:
+            gb = (N * kp * zbytes + R * N * 4) / (ms * 1e-3) / 1e9
+            entry["hbm_gbs"] = gb
+            entry["flops_tflops"] = 2.0 * R * N * kp * (3 if name == "bf16x3" else 1) / (
+                ms * 1e-3) / 1e12
+        res[name] = entry
+    return res
+
+
 def run_reference(args, recipe):
     rank = env_int("RANK", 0)
     if rank != 0:
@@ -180,7 +227,7 @@ def run_reference(args, recipe):
     line = {"metric": METRIC, "value": v, "unit": "ms", "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "k": K_NN},
+            "data": "synthetic", "config": {"workload": workload_name(recipe), "k": K_NN},
             "cpu_baseline": {"kind": "oracle", "cores": info["cores"], "sample": info["sample"],
                              "value": v, "unit": "ms"},
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -196,12 +243,19 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--small", action="store_true", help="tiny 16x16x4, M=100 workload (checks)")
+    ap.add_argument("--batch", type=int, default=1, help="also time 64-reference Pearson GEMMs")
+    ap.add_argument("--workload", choices=["csens", "csens-slab", "tiny"], default="csens",
+                    help="csens: 250x352x20, M=1000 (the benchmark); csens-slab: one vertical "
+                         "level of it (profiling); tiny: 16x16x4, M=100 (checks)")
     args = ap.parse_args()
 
     import synth
 
-    recipe = synth.TINY if args.small else synth.CSENS
+    global METRIC
+    recipe = {"csens": synth.CSENS, "tiny": synth.TINY,
+              "csens-slab": synth.scaled(synth.CSENS, Z=1)}[args.workload]
+    if args.workload != "csens":
+        METRIC = f"ms per {recipe.N}-voxel dependence volume (Pearson + KSG MI k=8, M={recipe.M})"
     if args.impl == "reference":
         return run_reference(args, recipe)
 
@@ -269,6 +323,9 @@ def main():
     volumes = args.steps * world
     ms_per_volume = total_ms / volumes
 
+    # ---- batched multi-reference Pearson (64 references per call) per precision
+    batch = measure_pearson_batch(ndf, ctx, fid, field, recipe, stream, rank) if args.batch else None
+
     # ---- end to end through the ABI with host buffers (upload + stats + both volumes + D2H)
     host_r = torch.empty(N, dtype=torch.float32, pin_memory=True)
     host_mi = torch.empty(N, dtype=torch.float32, pin_memory=True)
@@ -309,7 +366,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "M": M, "grid_xyz": [X, Y, Z], "k": K_NN,
+            "config": {"workload": workload_name(recipe), "M": M, "grid_xyz": [X, Y, Z], "k": K_NN,
                        "refs_per_rank": args.steps, "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (7.04 GB field, read once per volume)"},
             "pearson_ms": pearson_ms, "ksg_ms": ksg_ms,
@@ -323,6 +380,7 @@ def main():
                     "h2d_bytes_per_step": int(field.nbytes),
                     "d2h_bytes_per_step": int(2 * N * 4)},
             "gpu_launches": int(launches),
+            "pearson_batch64": batch,
             "clocks": clocks,
             "cpu_baseline": cpu,
         }

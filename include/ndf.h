@@ -35,6 +35,13 @@ extern "C" {
 
 typedef struct ndf_ctx ndf_ctx; /* opaque; owns all device memory it allocates */
 
+/* Arithmetic of the batched Pearson volumes. */
+typedef enum {
+    NDF_PREC_FP32 = 0,   /* exact FP32 CUDA-core volumes, one per reference */
+    NDF_PREC_BF16X3 = 1, /* tensor cores, z = hi + lo in BF16, 3 products, FP32 accumulate */
+    NDF_PREC_TF32 = 2    /* tensor cores, z rounded to TF32, FP32 accumulate */
+} ndf_precision;
+
 typedef enum {
     NDF_OK = 0,
     NDF_ERR_ARG = -1,     /* invalid argument (sizes, indices, k, null pointers) */
@@ -103,6 +110,18 @@ ndf_status ndf_field_stats(ndf_ctx* ctx, int field_id, double* mean_out, double*
  * self-correlation slice S_mu(p_ref, .), Sec. 3).  Fields must have the same
  * shape.  ref_idx is a flat vertex index in [0, N).  out: N floats. */
 ndf_status ndf_pearson(ndf_ctx* ctx, int ref_field, int query_field, int64_t ref_idx, float* out);
+
+/* R Pearson volumes in one call (Sec. 3.1, Eq. 1; the slices R(p_ref_i, .) of
+ * Sec. 3 for R reference vertices): out[i*N + v] = r(ref_idx[i], v), FP32,
+ * clamped to [-1, 1].  ref_idx: R host indices in [0, N).  out: R*N floats,
+ * host or device.  With NDF_PREC_TF32 / NDF_PREC_BF16X3 the volumes are one
+ * GEMM of standardised data, z = (e - mu) / sqrt(S), on the tensor cores
+ * (chunks of 256 references); the standardised copy of each field is built on
+ * the first such call and kept with the field (4 bytes per member and vertex,
+ * members padded to a multiple of 64).  NDF_PREC_FP32 runs the exact
+ * single-reference kernel R times. */
+ndf_status ndf_pearson_batch(ndf_ctx* ctx, int ref_field, int query_field, const int64_t* ref_idx,
+                             int R, ndf_precision prec, float* out);
 
 /* KSG mutual-information volume (Sec. 3.2, Eq. 2; estimator of Sec. 6.2):
  * out[v] = I(e^ref(p_ref); e^query(v)) in nats, FP32, for all N vertices.

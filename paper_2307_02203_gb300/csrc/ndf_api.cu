@@ -23,6 +23,16 @@ cudaError_t DevBuf::reserve(size_t need) {
     return cudaSuccess;
 }
 
+void Field::free_all() {
+    void* ps[] = {data, mean, inv_norm, z_tf32, z_hi, z_lo};
+    for (void* q : ps)
+        if (q) cudaFree(q);
+    data = nullptr;
+    mean = inv_norm = nullptr;
+    z_tf32 = z_hi = z_lo = nullptr;
+    live = false;
+}
+
 void DevBuf::release() {
     if (ptr) cudaFree(ptr);
     ptr = nullptr;
@@ -196,17 +206,15 @@ void ndf_destroy(ndf_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-    for (auto& f : ctx->fields) {
-        if (f.data) cudaFree(f.data);
-        if (f.mean) cudaFree(f.mean);
-        if (f.inv_norm) cudaFree(f.inv_norm);
-    }
+    for (auto& f : ctx->fields) f.free_all();
     ctx->stage_x.release();
     ctx->stage_perm.release();
     ctx->out_tmp.release();
     ctx->psi.release();
     ctx->dbg.release();
     ctx->flag.release();
+    ctx->zr.release();
+    ctx->refidx.release();
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     delete ctx;
 }
@@ -294,12 +302,7 @@ ndf_status ndf_free_ensemble(ndf_ctx* ctx, int field_id) {
     Field& f = ctx->fields[field_id];
     if (!f.live) return fail(ctx, NDF_ERR_STATE, "field already freed");
     cudaStreamSynchronize(ctx->stream);
-    cudaFree(f.data);
-    cudaFree(f.mean);
-    cudaFree(f.inv_norm);
-    f.data = nullptr;
-    f.mean = f.inv_norm = nullptr;
-    f.live = false;
+    f.free_all();
     return NDF_OK;
 }
 

@@ -27,6 +27,13 @@ struct Field {
     float* data = nullptr;     // [M][N]
     double* mean = nullptr;    // [N]
     double* inv_norm = nullptr;// [N] 1/sqrt(sum (e - mean)^2), 0 when the sum is 0
+    // standardised vertex-major copies for the tensor-core batched Pearson
+    // (built on first use): z[v][m] = (e_m(v) - mean_v) * inv_norm_v, m < Kp
+    int Kp = 0;
+    void* z_tf32 = nullptr;    // float [N][Kp], TF32-rounded
+    void* z_hi = nullptr;      // bf16 [N][Kp]
+    void* z_lo = nullptr;      // bf16 [N][Kp]
+    void free_all();
 };
 
 }  // namespace ndf
@@ -47,6 +54,8 @@ struct ndf_ctx {
     int64_t psi_n = 0;
     ndf::DevBuf dbg;         // KSG debug outputs
     ndf::DevBuf flag;        // small device status words
+    ndf::DevBuf zr;          // batched Pearson: standardised reference rows
+    ndf::DevBuf refidx;      // batched calls: reference indices on the device
 };
 
 namespace ndf {

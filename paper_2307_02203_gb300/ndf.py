@@ -59,6 +59,8 @@ _sig("ndf_field_shape", ctypes.c_int, [_vp, ctypes.c_int] + [ctypes.POINTER(_i64
 _sig("ndf_field_stats", ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp])
 _sig("ndf_pearson", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, _vp])
 _sig("ndf_mi_ksg", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, ctypes.c_int, _vp])
+_sig("ndf_pearson_batch", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int,
+                                         ctypes.c_int, _vp])
 _sig("ndf_pearson_noalloc", ctypes.c_int, [_vp, _vp, _i64, _i64, _i64, _vp, _vp])
 _sig("ndf_ksg_debug_pair", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, _i64,
                                           ctypes.c_int, _vp, _vp, _vp, _vp])
@@ -149,6 +151,16 @@ def ndf_field_stats(ctx, field_id: int, mean_out, inv_norm_out) -> None:
 
 def ndf_pearson(ctx, ref_field: int, query_field: int, ref_idx: int, out) -> None:
     _check(ctx, _lib.ndf_pearson(ctx, ref_field, query_field, ref_idx, _addr(out)), "ndf_pearson")
+
+
+def ndf_pearson_batch(ctx, ref_field: int, query_field: int, ref_idx, prec: int, out) -> None:
+    """ref_idx: sequence of flat vertex indices (host); out: [R][N] floats."""
+    import numpy as _np
+
+    refs = _np.ascontiguousarray(_np.asarray(ref_idx, dtype=_np.int64))
+    _check(ctx, _lib.ndf_pearson_batch(ctx, ref_field, query_field, refs.ctypes.data,
+                                       int(refs.shape[0]), int(prec), _addr(out)),
+           "ndf_pearson_batch")
 
 
 def ndf_mi_ksg(ctx, ref_field: int, query_field: int, ref_idx: int, k: int, out) -> None:
