@@ -13,6 +13,8 @@ Functions and the passages they follow:
                               k-th order statistic by nth_element, linear-scan
                               strict counts, long-double digamma sum)
   digamma_int              -- psi(1) = -gamma, psi(n+1) = psi(n) + 1/n
+  ndf_*, adam_step         -- Sec. 4: dense-grid NDF forward, L1 loss (Eq. 3), hand-written
+                              backward, Adam update, all FP64
 """
 from __future__ import annotations
 
@@ -173,3 +175,90 @@ def ksg_volume(ref_field, q_field, ref_idx: int, k: int, verts=None, nthreads: i
     if rc != 0:
         raise ValueError("oracle_ksg_volume: bad arguments")
     return out
+
+
+# ---------------------------------------------------------------- neural dependence field
+class NetShape(ctypes.Structure):
+    """Shape of the dense-grid NDF (see ndf_net_oracle.h)."""
+
+    _fields_ = [("levels", ctypes.c_int), ("res", ctypes.c_int * 8), ("feat", ctypes.c_int),
+                ("hidden", ctypes.c_int), ("measure", ctypes.c_int)]
+
+
+def net_shape(res, feat, hidden, measure):
+    s = NetShape()
+    s.levels = len(res)
+    for i, r in enumerate(res):
+        s.res[i] = int(r)
+    s.feat = int(feat)
+    s.hidden = int(hidden)
+    s.measure = int(measure)
+    return s
+
+
+def _net_lib():
+    lib = _load()
+    if not hasattr(lib, "_net_ready"):
+        sp = ctypes.POINTER(NetShape)
+        lib.oracle_ndf_param_count.restype = ctypes.c_int64
+        lib.oracle_ndf_param_count.argtypes = [sp]
+        lib.oracle_ndf_encode.restype = None
+        lib.oracle_ndf_encode.argtypes = [sp, _f64p, _f64p, _f64p]
+        lib.oracle_ndf_forward.restype = None
+        lib.oracle_ndf_forward.argtypes = [sp, _f64p, ctypes.c_int64, _f64p, _f64p, _f64p]
+        lib.oracle_ndf_loss_grad.restype = ctypes.c_double
+        lib.oracle_ndf_loss_grad.argtypes = [sp, _f64p, ctypes.c_int64, _f64p, _f64p, _f64p,
+                                             _f64p]
+        lib.oracle_adam_step.restype = None
+        lib.oracle_adam_step.argtypes = [ctypes.c_int64, _f64p, _f64p, _f64p, _f64p,
+                                         ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double]
+        lib._net_ready = True
+    return lib
+
+
+def _d(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_f64p)
+
+
+def ndf_param_count(shape) -> int:
+    return int(_net_lib().oracle_ndf_param_count(ctypes.byref(shape)))
+
+
+def ndf_encode(shape, params, p):
+    params, pp = _d(params)
+    p, ppos = _d(p)
+    out = np.empty(shape.levels * shape.feat)
+    _net_lib().oracle_ndf_encode(ctypes.byref(shape), pp, ppos, out.ctypes.data_as(_f64p))
+    return out
+
+
+def ndf_forward(shape, params, pr, pq):
+    params, pp = _d(params)
+    pr, a = _d(pr)
+    pq, b = _d(pq)
+    B = pr.shape[0]
+    y = np.empty(B)
+    _net_lib().oracle_ndf_forward(ctypes.byref(shape), pp, B, a, b, y.ctypes.data_as(_f64p))
+    return y
+
+
+def ndf_loss_grad(shape, params, pr, pq, target, want_grad=True):
+    params, pp = _d(params)
+    pr, a = _d(pr)
+    pq, b = _d(pq)
+    target, t = _d(target)
+    grad = np.empty(params.shape[0]) if want_grad else None
+    loss = _net_lib().oracle_ndf_loss_grad(ctypes.byref(shape), pp, pr.shape[0], a, b, t,
+                                           grad.ctypes.data_as(_f64p) if want_grad else None)
+    return loss, grad
+
+
+def adam_step(params, grad, m, v, t, lr=3e-4, beta1=0.9, beta2=0.999, eps=1e-8):
+    """In place on float64 arrays (params, m, v); returns nothing."""
+    for arr in (params, grad, m, v):
+        assert arr.dtype == np.float64 and arr.flags.c_contiguous
+    _net_lib().oracle_adam_step(params.shape[0], params.ctypes.data_as(_f64p),
+                                grad.ctypes.data_as(_f64p), m.ctypes.data_as(_f64p),
+                                v.ctypes.data_as(_f64p), int(t), lr, beta1, beta2, eps)
