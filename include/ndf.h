@@ -142,6 +142,92 @@ ndf_status ndf_ksg_debug_pair(ndf_ctx* ctx, int ref_field, int query_field, int6
                               int64_t query_idx, int k, float* eps, int32_t* nx, int32_t* ny,
                               double* mi);
 
+/* ---- neural dependence field (Sec. 4) ------------------------------------ */
+
+typedef struct ndf_model ndf_model; /* opaque; owned by the caller, freed by ndf_model_free */
+
+/* Dependence measure a network learns. */
+typedef enum { NDF_MEASURE_PEARSON = 0, NDF_MEASURE_MI_KSG = 1 } ndf_measure;
+
+/* Training configuration (Sec. 4.3); ndf_train_cfg_default fills the values in
+ * brackets.  The network is fixed at 4 dense feature-grid levels x 16 BF16
+ * features (res[] points per axis, corner-aligned on [-1,1]^3), the merged
+ * input [f_ref*f_q ; f_ref+f_q] (128), 3 hidden ReLU layers of 128 and one
+ * output (tanh for Pearson, softplus for MI). */
+typedef struct {
+    int res[4];               /* grid points per axis per level [32, 64, 128, 256] */
+    int64_t n_triples;        /* (reference, query, target) training triples [2^26] */
+    int64_t batch;            /* pairs per Adam step [2^18] */
+    int64_t refs_per_group;   /* references per generation group [128] */
+    int64_t queries_per_group;/* query vertices per group [8192] */
+    int max_passes;           /* passes over the triples [50] */
+    int patience;             /* passes without improvement before lr x 0.1 [5] */
+    int max_decays;           /* stop after this many decays [2] */
+    float lr, beta1, beta2, eps; /* Adam [3e-4, 0.9, 0.999, 1e-8] */
+    uint64_t seed;            /* triples, pass orders, initial weights [20230705] */
+    double time_budget_s;     /* stop training after this many seconds (0: none) [0] */
+} ndf_train_cfg;
+
+/* What a model is and how it was trained. */
+typedef struct {
+    int measure;
+    int res[4];
+    int64_t X, Y, Z;          /* ensemble grid the model decodes */
+    int64_t param_count, grid_params;
+    int64_t network_bytes;    /* decoding footprint: BF16 grid and weights, FP32 rest */
+    int64_t training_bytes;   /* FP32 master + gradient + Adam moments + BF16 grid */
+    int64_t adam_steps;
+    int passes;
+    double last_loss;         /* mean L1 loss of the last pass */
+    int64_t n_triples;
+    double gen_seconds, train_seconds;
+} ndf_model_info_t;
+
+void ndf_train_cfg_default(ndf_train_cfg* cfg);
+
+/* Learn Phi(p_ref, p_q) ~ R(p_ref, p_q) (Eq. 3, L1 loss, Adam) for the
+ * reference field / query field pair (the self-correlation field when they
+ * are the same, Sec. 3; a cross-variable field otherwise, Sec. 6.4).  Targets
+ * come from this library's exact estimators (Pearson, or KSG MI with k) on
+ * seeded uniform vertex pairs; positions are vertex-aligned in [-1,1]^3.
+ * cfg may be NULL (defaults).  The new model is returned in *out. */
+ndf_status ndf_train(ndf_ctx* ctx, int ref_field, int query_field, int measure, int k,
+                     const ndf_train_cfg* cfg, ndf_model** out);
+
+/* Decode a full dependence volume for one reference vertex (Sec. 5):
+ * out[v] = Phi(p(ref_idx), p(v)) for all N vertices of the model's grid.
+ * out: N floats, host or device. */
+ndf_status ndf_infer(ndf_model* model, int64_t ref_idx, float* out);
+
+/* R volumes in one launch: out[i*N + v] for R host reference indices. */
+ndf_status ndf_infer_batch(ndf_model* model, const int64_t* ref_idx, int R, float* out);
+
+/* Save / load a model (FP32 parameters and Adam state, versioned binary). */
+ndf_status ndf_model_save(ndf_model* model, const char* path);
+ndf_status ndf_model_load(ndf_ctx* ctx, const char* path, ndf_model** out);
+void ndf_model_free(ndf_model* model);
+ndf_status ndf_model_info(const ndf_model* model, ndf_model_info_t* info);
+
+/* Lower-level calls (used by the tests and the benchmark).  A fresh model
+ * over an X x Y x Z grid: grid features U(-1e-4, 1e-4), weights He-uniform,
+ * biases 0, from a counter-based generator keyed by seed. */
+ndf_status ndf_model_create(ndf_ctx* ctx, const int res[4], int measure, uint64_t seed, int64_t X,
+                            int64_t Y, int64_t Z, ndf_model** out);
+/* Number of FP32 parameters; layout: grid levels (point-major, 16 features),
+ * W1 [128][128] ([out][in]), b1, W2, b2, W3, b3, w4 [128], b4. */
+int64_t ndf_model_param_count(const ndf_model* model);
+ndf_status ndf_model_get_params(ndf_model* model, float* out);      /* host or device */
+ndf_status ndf_model_set_params(ndf_model* model, const float* in); /* host or device */
+/* One step on B explicit position pairs (p_ref, p_query: [B][3] in [-1,1]^3)
+ * with targets: writes the mean L1 loss and (if grad_out) dL/dparams in the
+ * parameter layout; with update != 0 also applies one Adam step at rate lr. */
+ndf_status ndf_model_step(ndf_model* model, const float* p_ref, const float* p_query,
+                          const float* target, int64_t B, float lr, int update, double* loss_out,
+                          float* grad_out);
+/* Phi for B explicit position pairs; out: B floats, host or device. */
+ndf_status ndf_model_forward(ndf_model* model, const float* p_ref, const float* p_query,
+                             int64_t B, float* out);
+
 /* ---- allocation-free variant --------------------------------------------- */
 
 /* Largest member count ndf_pearson_noalloc accepts. */

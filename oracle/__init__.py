@@ -209,6 +209,9 @@ def _net_lib():
         lib.oracle_ndf_loss_grad.restype = ctypes.c_double
         lib.oracle_ndf_loss_grad.argtypes = [sp, _f64p, ctypes.c_int64, _f64p, _f64p, _f64p,
                                              _f64p]
+        lib.oracle_ndf_loss_grad_abs.restype = ctypes.c_double
+        lib.oracle_ndf_loss_grad_abs.argtypes = [sp, _f64p, ctypes.c_int64, _f64p, _f64p, _f64p,
+                                                 _f64p, _f64p]
         lib.oracle_adam_step.restype = None
         lib.oracle_adam_step.argtypes = [ctypes.c_int64, _f64p, _f64p, _f64p, _f64p,
                                          ctypes.c_int64, ctypes.c_double, ctypes.c_double,
@@ -253,6 +256,20 @@ def ndf_loss_grad(shape, params, pr, pq, target, want_grad=True):
     loss = _net_lib().oracle_ndf_loss_grad(ctypes.byref(shape), pp, pr.shape[0], a, b, t,
                                            grad.ctypes.data_as(_f64p) if want_grad else None)
     return loss, grad
+
+
+def ndf_loss_grad_abs(shape, params, pr, pq, target):
+    """(loss, grad, gabs): gabs = mean over samples of |per-sample gradient|."""
+    params, pp = _d(params)
+    pr, a = _d(pr)
+    pq, b = _d(pq)
+    target, t = _d(target)
+    grad = np.empty(params.shape[0])
+    gabs = np.empty(params.shape[0])
+    loss = _net_lib().oracle_ndf_loss_grad_abs(ctypes.byref(shape), pp, pr.shape[0], a, b, t,
+                                               grad.ctypes.data_as(_f64p),
+                                               gabs.ctypes.data_as(_f64p))
+    return loss, grad, gabs
 
 
 def adam_step(params, grad, m, v, t, lr=3e-4, beta1=0.9, beta2=0.999, eps=1e-8):

@@ -223,6 +223,24 @@ double oracle_ndf_loss_grad(const oracle_net_shape* s, const double* params, int
     return loss / (double)B;
 }
 
+double oracle_ndf_loss_grad_abs(const oracle_net_shape* s, const double* params, int64_t B,
+                                const double* pr, const double* pq, const double* target,
+                                double* grad, double* gabs) {
+    // same gradient, one sample at a time, also summing |per-sample gradient|
+    Offsets o = offsets(s);
+    std::vector<double> one((size_t)o.total);
+    for (int64_t i = 0; i < o.total; ++i) grad[i] = gabs[i] = 0.0;
+    double loss = 0.0;
+    for (int64_t b = 0; b < B; ++b) {
+        loss += oracle_ndf_loss_grad(s, params, 1, pr + 3 * b, pq + 3 * b, target + b, one.data());
+        for (int64_t i = 0; i < o.total; ++i) {
+            grad[i] += one[(size_t)i] / (double)B;
+            gabs[i] += std::fabs(one[(size_t)i]) / (double)B;
+        }
+    }
+    return loss / (double)B;
+}
+
 void oracle_adam_step(int64_t n, double* params, const double* grad, double* m, double* v,
                       int64_t t, double lr, double beta1, double beta2, double eps) {
     const double c1 = 1.0 - std::pow(beta1, (double)t);

@@ -49,6 +49,13 @@ double oracle_ndf_loss_grad(const oracle_net_shape* s, const double* params, int
                             const double* pr, const double* pq, const double* target,
                             double* grad);
 
+/* the same loss and gradient, plus gabs = (1/B) sum_b |gradient of sample b|:
+ * the magnitude of the summed terms, which bounds how much rounding in the
+ * individual terms can move the (cancelling) sum */
+double oracle_ndf_loss_grad_abs(const oracle_net_shape* s, const double* params, int64_t B,
+                                const double* pr, const double* pq, const double* target,
+                                double* grad, double* gabs);
+
 /* one Adam step (t = step number, starting at 1) on n parameters */
 void oracle_adam_step(int64_t n, double* params, const double* grad, double* m, double* v,
                       int64_t t, double lr, double beta1, double beta2, double eps);

@@ -1,0 +1,824 @@
+// Neural dependence field: model calls, training (Sec. 4.3, Eq. 3), volume
+// decoding (Sec. 5) and model files.
+//
+// Training set: (reference vertex, query vertex, target) triples whose targets
+// come from this library's exact estimators.  They are generated in groups: a
+// group draws Rg reference vertices and Qg query vertices (uniform, seeded),
+// gathers the Qg query columns once into a compact member-major block, and runs
+// the Pearson or KSG kernel for each reference over that block, so every group
+// yields Rg x Qg uniform pairs without re-reading scattered columns.
+// Training: passes over the triples in an affine-bijective order that changes
+// every pass, Adam, L1 loss, learning rate x0.1 after `patience` passes without
+// improvement of the pass loss (Sec. 4.3), stopping after `max_decays` decays or
+// `max_passes` passes.
+// Decoding: the reference half of the merged input is folded into the first
+// layer once per reference,
+//   W1 [f_r*f_q ; f_r+f_q] + b1 = (W1a diag(f_r) + W1b) f_q + (W1b f_r + b1),
+// so each query vertex needs only its own encoding and a 64-input first layer.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <numeric>
+#include <vector>
+
+#include "device_common.cuh"
+#include "ndf_net.h"
+
+namespace ndf {
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ float axis_pos(int64_t i, int64_t n) {
+    return n > 1 ? -1.0f + 2.0f * (float)i / (float)(n - 1) : 0.0f;
+}
+
+__device__ __forceinline__ void vertex_pos(int64_t v, int64_t X, int64_t Y, int64_t Z, float* p) {
+    const int64_t x = v % X, y = (v / X) % Y, z = v / (X * Y);
+    p[0] = axis_pos(x, X);
+    p[1] = axis_pos(y, Y);
+    p[2] = axis_pos(z, Z);
+}
+
+static uint64_t host_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+static uint64_t host_rand(uint64_t key, uint64_t i) {
+    return host_mix(key + (i + 1) * 0x9e3779b97f4a7c15ULL);
+}
+
+// gather the query columns of one group: out[m][q] = field[m][verts[q]]
+__global__ void gather_columns_kernel(const float* __restrict__ field, int64_t M, int64_t N,
+                                      const int64_t* __restrict__ verts, int64_t Q,
+                                      float* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M * Q;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = i / Q, q = i % Q;
+        out[i] = field[m * N + verts[q]];
+    }
+}
+
+// batch positions and targets from the triple arrays through the bijection
+// j = (a * (base + i) + c) mod T
+__global__ void make_batch_kernel(const int32_t* __restrict__ vref, const int32_t* __restrict__ vq,
+                                  const float* __restrict__ tgt, int64_t T, uint64_t a, uint64_t c,
+                                  int64_t base, int64_t B, int64_t X, int64_t Y, int64_t Z,
+                                  float* __restrict__ pr, float* __restrict__ pq,
+                                  float* __restrict__ target) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B) return;
+    const uint64_t j = (a * (uint64_t)(base + i) + c) % (uint64_t)T;  // a, i < T <= 2^31
+    vertex_pos(vref[j], X, Y, Z, pr + 3 * i);
+    vertex_pos(vq[j], X, Y, Z, pq + 3 * i);
+    target[i] = tgt[j];
+}
+
+// ---------------------------------------------------------------- decoding (Sec. 5)
+constexpr int kFoldStride = kLF + 8;  // padded bf16 row stride of the folded first layer
+
+struct GridArgs {
+    const __nv_bfloat16* grid;
+    int res[kLevels];
+    int64_t off[kLevels];
+};
+
+__device__ __forceinline__ float2 bf2f2(uint32_t u) {
+    __nv_bfloat162 v = *reinterpret_cast<__nv_bfloat162*>(&u);
+    return __bfloat1622float2(v);
+}
+
+__device__ __forceinline__ uint32_t f2bf2(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+template <int L>
+__device__ __forceinline__ void encode_level_t(const GridArgs& G, const float* p, float (&out)[kFeat]) {
+    const int R = G.res[L];
+    int i[3];
+    float f[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float u = (p[a] + 1.0f) * 0.5f * (float)(R - 1);
+        int k = (int)floorf(u);
+        k = k < 0 ? 0 : (k > R - 2 ? R - 2 : k);
+        i[a] = k;
+        f[a] = u - (float)k;
+    }
+#pragma unroll
+    for (int q = 0; q < kFeat; ++q) out[q] = 0.0f;
+    const uint4* base = reinterpret_cast<const uint4*>(G.grid + G.off[L]);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
+        const int64_t idx = ((int64_t)(i[2] + dz) * R + (i[1] + dy)) * R + (i[0] + dx);
+        const float w = (dx ? f[0] : 1.0f - f[0]) * (dy ? f[1] : 1.0f - f[1]) * (dz ? f[2] : 1.0f - f[2]);
+        const uint4 u0 = __ldg(base + idx * 2), u1 = __ldg(base + idx * 2 + 1);
+        const uint32_t uu[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float2 v = bf2f2(uu[j]);
+            out[2 * j] = fmaf(w, v.x, out[2 * j]);
+            out[2 * j + 1] = fmaf(w, v.y, out[2 * j + 1]);
+        }
+    }
+}
+
+__device__ __forceinline__ void encode_level_any(const GridArgs& G, int l, const float* p,
+                                                 float (&out)[kFeat]) {
+    switch (l) {
+        case 0: encode_level_t<0>(G, p, out); break;
+        case 1: encode_level_t<1>(G, p, out); break;
+        case 2: encode_level_t<2>(G, p, out); break;
+        default: encode_level_t<3>(G, p, out); break;
+    }
+}
+
+// one CTA (128 threads) per reference: f_ref, then the folded first layer
+__global__ void __launch_bounds__(128)
+    infer_fold_kernel(GridArgs G, const float* __restrict__ params, int64_t offW1, int64_t offb1,
+                      const int64_t* __restrict__ refs, int64_t X, int64_t Y, int64_t Z,
+                      __nv_bfloat16* __restrict__ w1f, float* __restrict__ b1f) {
+    __shared__ float fr[kLF];
+    const int r = blockIdx.x;
+    if (threadIdx.x < kLevels) {
+        float p[3];
+        vertex_pos(refs[r], X, Y, Z, p);
+        float f[kFeat];
+        encode_level_any(G, threadIdx.x, p, f);
+#pragma unroll
+        for (int q = 0; q < kFeat; ++q) fr[threadIdx.x * kFeat + q] = f[q];
+    }
+    __syncthreads();
+    const int o = threadIdx.x;  // output row of the first layer
+    const float* W = params + offW1 + (int64_t)o * kIn;
+    float b = params[offb1 + o];
+    __nv_bfloat16* dst = w1f + ((int64_t)r * kHid + o) * kLF;
+    for (int f = 0; f < kLF; ++f) {
+        dst[f] = __float2bfloat16_rn(fmaf(W[f], fr[f], W[kLF + f]));
+        b = fmaf(W[kLF + f], fr[f], b);
+    }
+    b1f[(int64_t)r * kHid + o] = b;
+}
+
+struct InferArgs {
+    GridArgs G;
+    const __nv_bfloat16* w1f;  // [R][128][64]
+    const float* b1f;          // [R][128]
+    const __nv_bfloat16* w23;  // W2, W3 bf16 [2][128][128]
+    const float* params;
+    int64_t offb2, offb3, offw4, offb4;
+    int64_t N, X, Y, Z;
+    int measure;
+    float* out;                // [R][N]
+};
+
+__device__ __forceinline__ void mma16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+constexpr int kInferWarps = 8;
+constexpr size_t kInferSmem = (size_t)kHid * kFoldStride * 2 + (size_t)2 * kHid * kWStride * 2 +
+                              (size_t)kInferWarps * 16 * kFoldStride * 2;
+
+// grid (CTAs per reference, R); each warp decodes 16 query vertices at a time
+__global__ void __launch_bounds__(256) infer_volume_kernel(InferArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __nv_bfloat16* sW1 = reinterpret_cast<__nv_bfloat16*>(smem);          // [128][72]
+    __nv_bfloat16* sW23 = sW1 + kHid * kFoldStride;                          // [2][128][136]
+    __nv_bfloat16* sEnc = sW23 + 2 * kHid * kWStride;                        // [warps][16][72]
+    const int r = blockIdx.y;
+    const __nv_bfloat16* w1 = a.w1f + (int64_t)r * kHid * kLF;
+    for (int i = threadIdx.x; i < kHid * (kLF / 8); i += blockDim.x) {
+        const int row = i / (kLF / 8), c8 = i % (kLF / 8);
+        *reinterpret_cast<uint4*>(sW1 + row * kFoldStride + c8 * 8) =
+            reinterpret_cast<const uint4*>(w1 + row * kLF)[c8];
+    }
+    for (int i = threadIdx.x; i < 2 * kHid * (kHid / 8); i += blockDim.x) {
+        const int mat = i / (kHid * kHid / 8), rem = i % (kHid * kHid / 8);
+        const int row = rem / (kHid / 8), c8 = rem % (kHid / 8);
+        *reinterpret_cast<uint4*>(sW23 + (size_t)mat * kHid * kWStride + row * kWStride + c8 * 8) =
+            reinterpret_cast<const uint4*>(a.w23 + (size_t)mat * kHid * kHid)[row * (kHid / 8) + c8];
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    __nv_bfloat16* enc = sEnc + warp * 16 * kFoldStride;
+    const float* b1 = a.b1f + (int64_t)r * kHid;
+    const float* b2 = a.params + a.offb2;
+    const float* b3 = a.params + a.offb3;
+    const float* w4 = a.params + a.offw4;
+    const float b4 = a.params[a.offb4];
+    float* out = a.out + (int64_t)r * a.N;
+    const int64_t tiles = (a.N + 15) / 16;
+    for (int64_t tile = (int64_t)blockIdx.x * kInferWarps + warp; tile < tiles;
+         tile += (int64_t)gridDim.x * kInferWarps) {
+        const int64_t v0 = tile * 16;
+        // encode 16 vertices x 4 levels (two tasks per lane) into the warp's tile
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int task = lane + 32 * h, row = task >> 2, l = task & 3;
+            const int64_t v = v0 + row;
+            float f[kFeat];
+            if (v < a.N) {
+                float p[3];
+                vertex_pos(v, a.X, a.Y, a.Z, p);
+                encode_level_any(a.G, l, p, f);
+            } else {
+#pragma unroll
+                for (int q = 0; q < kFeat; ++q) f[q] = 0.0f;
+            }
+            uint4* d = reinterpret_cast<uint4*>(enc + row * kFoldStride + l * kFeat);
+            d[0] = make_uint4(f2bf2(f[0], f[1]), f2bf2(f[2], f[3]), f2bf2(f[4], f[5]), f2bf2(f[6], f[7]));
+            d[1] = make_uint4(f2bf2(f[8], f[9]), f2bf2(f[10], f[11]), f2bf2(f[12], f[13]), f2bf2(f[14], f[15]));
+        }
+        __syncwarp();
+        uint32_t A[8][4];
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            const int c = 16 * kk + 2 * t;
+            A[kk][0] = *reinterpret_cast<const uint32_t*>(enc + g * kFoldStride + c);
+            A[kk][1] = *reinterpret_cast<const uint32_t*>(enc + (g + 8) * kFoldStride + c);
+            A[kk][2] = *reinterpret_cast<const uint32_t*>(enc + g * kFoldStride + c + 8);
+            A[kk][3] = *reinterpret_cast<const uint32_t*>(enc + (g + 8) * kFoldStride + c + 8);
+        }
+        __syncwarp();
+        float c[16][4];
+        // layer 1 (folded, K = 64)
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const float x0 = b1[8 * j + 2 * t], x1 = b1[8 * j + 2 * t + 1];
+            c[j][0] = x0; c[j][1] = x1; c[j][2] = x0; c[j][3] = x1;
+        }
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const __nv_bfloat16* row = sW1 + (8 * j + g) * kFoldStride + 16 * kk + 2 * t;
+                mma16816(c[j], A[kk], *reinterpret_cast<const uint32_t*>(row),
+                         *reinterpret_cast<const uint32_t*>(row + 8));
+            }
+        // layers 2 and 3
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+                A[kk][0] = f2bf2(fmaxf(c[2 * kk][0], 0.f), fmaxf(c[2 * kk][1], 0.f));
+                A[kk][1] = f2bf2(fmaxf(c[2 * kk][2], 0.f), fmaxf(c[2 * kk][3], 0.f));
+                A[kk][2] = f2bf2(fmaxf(c[2 * kk + 1][0], 0.f), fmaxf(c[2 * kk + 1][1], 0.f));
+                A[kk][3] = f2bf2(fmaxf(c[2 * kk + 1][2], 0.f), fmaxf(c[2 * kk + 1][3], 0.f));
+            }
+            const float* bias = l == 0 ? b2 : b3;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float x0 = bias[8 * j + 2 * t], x1 = bias[8 * j + 2 * t + 1];
+                c[j][0] = x0; c[j][1] = x1; c[j][2] = x0; c[j][3] = x1;
+            }
+            const __nv_bfloat16* W = sW23 + (size_t)l * kHid * kWStride;
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk)
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const __nv_bfloat16* row = W + (8 * j + g) * kWStride + 16 * kk + 2 * t;
+                    mma16816(c[j], A[kk], *reinterpret_cast<const uint32_t*>(row),
+                             *reinterpret_cast<const uint32_t*>(row + 8));
+                }
+        }
+        // output: o = w4 . relu(h3) (as BF16) + b4
+        float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int col = 8 * j + 2 * t;
+            const float2 ha = bf2f2(f2bf2(fmaxf(c[j][0], 0.f), fmaxf(c[j][1], 0.f)));
+            const float2 hb = bf2f2(f2bf2(fmaxf(c[j][2], 0.f), fmaxf(c[j][3], 0.f)));
+            s0 = fmaf(w4[col], ha.x, fmaf(w4[col + 1], ha.y, s0));
+            s1 = fmaf(w4[col], hb.x, fmaf(w4[col + 1], hb.y, s1));
+        }
+        s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+        s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
+        if (t == 0) {
+            const int64_t va = v0 + g, vb = v0 + g + 8;
+            const float oa = s0 + b4, ob = s1 + b4;
+            if (va < a.N) out[va] = a.measure == 0 ? tanhf(oa) : (oa > 20.f ? oa : log1pf(expf(oa)));
+            if (vb < a.N) out[vb] = a.measure == 0 ? tanhf(ob) : (ob > 20.f ? ob : log1pf(expf(ob)));
+        }
+    }
+}
+
+cudaError_t model_infer(ndf_model* m, const int64_t* d_refs, int R, float* out) {
+    ndf_ctx* ctx = m->ctx;
+    if (m->infer_cap < R) {
+        if (m->w1f) cudaFree(m->w1f);
+        if (m->b1f) cudaFree(m->b1f);
+        m->w1f = nullptr;
+        m->b1f = nullptr;
+        m->infer_cap = 0;
+        cudaError_t e = cudaMalloc(&m->w1f, (size_t)R * kHid * kLF * 2);
+        if (e == cudaSuccess) e = cudaMalloc(&m->b1f, (size_t)R * kHid * 4);
+        if (e != cudaSuccess) return e;
+        m->infer_cap = R;
+        e = cudaFuncSetAttribute(infer_volume_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kInferSmem);
+        if (e != cudaSuccess) return e;
+    }
+    GridArgs G;
+    G.grid = m->grid_bf;
+    for (int l = 0; l < kLevels; ++l) {
+        G.res[l] = m->L.res[l];
+        G.off[l] = m->L.grid_off[l];
+    }
+    infer_fold_kernel<<<R, kHid, 0, ctx->stream>>>(G, m->params, m->L.W1, m->L.b1, d_refs, m->X,
+                                                   m->Y, m->Z, m->w1f, m->b1f);
+    InferArgs a;
+    a.G = G;
+    a.w1f = m->w1f;
+    a.b1f = m->b1f;
+    a.w23 = m->wbf + (size_t)kHid * kHid;  // W2, W3
+    a.params = m->params;
+    a.offb2 = m->L.b2;
+    a.offb3 = m->L.b3;
+    a.offw4 = m->L.w4;
+    a.offb4 = m->L.b4;
+    a.N = m->X * m->Y * m->Z;
+    a.X = m->X;
+    a.Y = m->Y;
+    a.Z = m->Z;
+    a.measure = m->measure;
+    a.out = out;
+    int per_ref = (int)((ctx->sm_count * 2 + R - 1) / R);
+    const int64_t tiles = (a.N + 15) / 16;
+    const int64_t need = (tiles + kInferWarps - 1) / kInferWarps;
+    if (per_ref > need) per_ref = (int)need;
+    if (per_ref < 1) per_ref = 1;
+    infer_volume_kernel<<<dim3(per_ref, R), 256, kInferSmem, ctx->stream>>>(a);
+    ctx->launches += 2;
+    return cudaGetLastError();
+}
+
+}  // namespace ndf
+
+using namespace ndf;
+
+// ---------------------------------------------------------------- C ABI
+extern "C" {
+
+void ndf_train_cfg_default(ndf_train_cfg* c) {
+    if (!c) return;
+    memset(c, 0, sizeof *c);
+    c->res[0] = 32;
+    c->res[1] = 64;
+    c->res[2] = 128;
+    c->res[3] = 256;
+    c->n_triples = int64_t(1) << 26;
+    c->batch = int64_t(1) << 18;
+    c->refs_per_group = 128;
+    c->queries_per_group = 8192;
+    c->max_passes = 50;
+    c->patience = 5;
+    c->max_decays = 2;
+    c->lr = 3e-4f;
+    c->beta1 = 0.9f;
+    c->beta2 = 0.999f;
+    c->eps = 1e-8f;
+    c->seed = 20230705ULL;
+    c->time_budget_s = 0.0;
+}
+
+ndf_status ndf_model_create(ndf_ctx* ctx, const int res[4], int measure, uint64_t seed, int64_t X,
+                            int64_t Y, int64_t Z, ndf_model** out) {
+    if (!ctx || !res || !out) return NDF_ERR_ARG;
+    if (X < 1 || Y < 1 || Z < 1 || X * Y * Z > (int64_t(1) << 31))
+        return fail(ctx, NDF_ERR_ARG, "grid dimensions out of range");
+    cudaSetDevice(ctx->device);
+    cudaError_t e = net_set_attributes();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel attributes");
+    ndf_model* m = nullptr;
+    ndf_status st = model_alloc(ctx, res, measure, X, Y, Z, &m);
+    if (st != NDF_OK) return st;
+    e = model_init_params(m, seed);
+    if (e != cudaSuccess) {
+        model_free(m);
+        return cuda_fail(ctx, e, "parameter initialisation");
+    }
+    *out = m;
+    return NDF_OK;
+}
+
+void ndf_model_free(ndf_model* m) {
+    if (!m) return;
+    cudaSetDevice(m->ctx->device);
+    cudaStreamSynchronize(m->ctx->stream);
+    model_free(m);
+}
+
+int64_t ndf_model_param_count(const ndf_model* m) { return m ? m->L.total : 0; }
+
+ndf_status ndf_model_get_params(ndf_model* m, float* out) {
+    if (!m || !out) return NDF_ERR_ARG;
+    ndf_ctx* ctx = m->ctx;
+    cudaError_t e = cudaMemcpyAsync(out, m->params, (size_t)m->L.total * 4, cudaMemcpyDefault,
+                                    ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "parameter copy");
+    return NDF_OK;
+}
+
+ndf_status ndf_model_set_params(ndf_model* m, const float* in) {
+    if (!m || !in) return NDF_ERR_ARG;
+    ndf_ctx* ctx = m->ctx;
+    cudaError_t e = cudaMemcpyAsync(m->params, in, (size_t)m->L.total * 4, cudaMemcpyDefault,
+                                    ctx->stream);
+    if (e == cudaSuccess) e = model_refresh_bf16(m);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "parameter upload");
+    return NDF_OK;
+}
+
+// stage host-or-device positions/targets into device buffers of the work area
+static ndf_status stage_batch(ndf_model* m, const float* pr, const float* pq, const float* target,
+                              int64_t B, const float** dpr, const float** dpq, const float** dt) {
+    ndf_ctx* ctx = m->ctx;
+    ndf_status st = ensure_work(m, B);
+    if (st != NDF_OK) return st;
+    cudaError_t e = cudaSuccess;
+    if (pointer_kind(pr) == PTR_DEVICE) {
+        *dpr = pr;
+    } else {
+        e = cudaMemcpyAsync(m->work.pos, pr, (size_t)B * 12, cudaMemcpyHostToDevice, ctx->stream);
+        *dpr = m->work.pos;
+    }
+    if (e == cudaSuccess) {
+        if (pointer_kind(pq) == PTR_DEVICE) {
+            *dpq = pq;
+        } else {
+            e = cudaMemcpyAsync(m->work.pos + 3 * B, pq, (size_t)B * 12, cudaMemcpyHostToDevice,
+                                ctx->stream);
+            *dpq = m->work.pos + 3 * B;
+        }
+    }
+    if (e == cudaSuccess && target) {
+        if (pointer_kind(target) == PTR_DEVICE) {
+            *dt = target;
+        } else {
+            e = cudaMemcpyAsync(m->work.target, target, (size_t)B * 4, cudaMemcpyHostToDevice,
+                                ctx->stream);
+            *dt = m->work.target;
+        }
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batch upload");
+    return NDF_OK;
+}
+
+ndf_status ndf_model_step(ndf_model* m, const float* p_ref, const float* p_query,
+                          const float* target, int64_t B, float lr, int update, double* loss_out,
+                          float* grad_out) {
+    if (!m || !p_ref || !p_query || !target || B < 1) return NDF_ERR_ARG;
+    ndf_ctx* ctx = m->ctx;
+    cudaSetDevice(ctx->device);
+    const float *dpr, *dpq, *dt;
+    ndf_status st = stage_batch(m, p_ref, p_query, target, B, &dpr, &dpq, &dt);
+    if (st != NDF_OK) return st;
+    cudaError_t e = cudaMemsetAsync(m->work.loss, 0, 8, ctx->stream);
+    if (e == cudaSuccess) e = model_step(m, dpr, dpq, dt, B, lr, 0.9f, 0.999f, 1e-8f, update != 0);
+    if (e == cudaSuccess && grad_out)
+        e = cudaMemcpyAsync(grad_out, m->grad, (size_t)m->L.total * 4, cudaMemcpyDefault,
+                            ctx->stream);
+    double loss = 0.0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&loss, m->work.loss, 8, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "network step");
+    if (loss_out) *loss_out = loss / (double)B;
+    return NDF_OK;
+}
+
+ndf_status ndf_model_forward(ndf_model* m, const float* p_ref, const float* p_query, int64_t B,
+                             float* out) {
+    if (!m || !p_ref || !p_query || !out || B < 1) return NDF_ERR_ARG;
+    ndf_ctx* ctx = m->ctx;
+    cudaSetDevice(ctx->device);
+    const float *dpr, *dpq, *dt = nullptr;
+    ndf_status st = stage_batch(m, p_ref, p_query, nullptr, B, &dpr, &dpq, &dt);
+    if (st != NDF_OK) return st;
+    void* dev_out;
+    bool is_host;
+    if ((st = resolve_out(ctx, out, (size_t)B * 4, &dev_out, &is_host)) != NDF_OK) return st;
+    cudaError_t e = model_forward(m, dpr, dpq, B, static_cast<float*>(dev_out));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "network forward");
+    return finish_out(ctx, out, dev_out, (size_t)B * 4, is_host);
+}
+
+ndf_status ndf_infer_batch(ndf_model* m, const int64_t* ref_idx, int R, float* out) {
+    if (!m || !ref_idx || R < 1 || !out) return m ? fail(m->ctx, NDF_ERR_ARG, "bad arguments") : NDF_ERR_ARG;
+    ndf_ctx* ctx = m->ctx;
+    const int64_t N = m->X * m->Y * m->Z;
+    for (int i = 0; i < R; ++i)
+        if (ref_idx[i] < 0 || ref_idx[i] >= N) return fail(ctx, NDF_ERR_ARG, "ref_idx out of range");
+    cudaSetDevice(ctx->device);
+    const size_t bytes = (size_t)R * (size_t)N * 4;
+    void* dev_out;
+    bool is_host;
+    ndf_status st = resolve_out(ctx, out, bytes, &dev_out, &is_host);
+    if (st != NDF_OK) return st;
+    cudaError_t e = ctx->refidx.reserve(sizeof(int64_t) * (size_t)R);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->refidx.ptr, ref_idx, sizeof(int64_t) * (size_t)R,
+                            cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = model_infer(m, ctx->refidx.as<int64_t>(), R, static_cast<float*>(dev_out));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "network decoding");
+    return finish_out(ctx, out, dev_out, bytes, is_host);
+}
+
+ndf_status ndf_infer(ndf_model* m, int64_t ref_idx, float* out) {
+    return ndf_infer_batch(m, &ref_idx, 1, out);
+}
+
+ndf_status ndf_model_info(const ndf_model* m, ndf_model_info_t* info) {
+    if (!m || !info) return NDF_ERR_ARG;
+    memset(info, 0, sizeof *info);
+    info->measure = m->measure;
+    for (int l = 0; l < kLevels; ++l) info->res[l] = m->L.res[l];
+    info->X = m->X;
+    info->Y = m->Y;
+    info->Z = m->Z;
+    info->param_count = m->L.total;
+    info->grid_params = m->L.n_grid;
+    // inference footprint: BF16 grid + BF16 weights + FP32 biases/output layer
+    info->network_bytes = m->L.n_grid * 2 + (int64_t)3 * kHid * kHid * 2 * 2 + (m->L.total - m->L.W1) * 4;
+    info->training_bytes = m->L.total * 4 * 4 + m->L.n_grid * 2;
+    info->adam_steps = m->t;
+    info->passes = m->passes;
+    info->last_loss = m->last_loss;
+    info->n_triples = m->n_triples;
+    info->gen_seconds = m->gen_seconds;
+    info->train_seconds = m->train_seconds;
+    return NDF_OK;
+}
+
+// ---- training (Sec. 4.3)
+ndf_status ndf_train(ndf_ctx* ctx, int ref_field, int query_field, int measure, int k,
+                     const ndf_train_cfg* cfg_in, ndf_model** out) {
+    if (!ctx || !out) return NDF_ERR_ARG;
+    ndf_train_cfg cfg;
+    if (cfg_in) cfg = *cfg_in;
+    else ndf_train_cfg_default(&cfg);
+    const Field *rf, *qf;
+    ndf_status st = check_pair(ctx, ref_field, query_field, 0, &rf, &qf);
+    if (st != NDF_OK) return st;
+    if (measure != NDF_MEASURE_PEARSON && measure != NDF_MEASURE_MI_KSG)
+        return fail(ctx, NDF_ERR_ARG, "unknown measure %d", measure);
+    if (measure == NDF_MEASURE_MI_KSG &&
+        (k < 1 || k >= rf->M || k > kKsgMaxK || rf->M > kKsgMaxM))
+        return fail(ctx, NDF_ERR_ARG, "bad k or M for the KSG targets");
+    if (cfg.n_triples < 1 || cfg.batch < 1 || cfg.refs_per_group < 1 || cfg.queries_per_group < 1 ||
+        cfg.max_passes < 1 || cfg.n_triples > (int64_t(1) << 31))
+        return fail(ctx, NDF_ERR_ARG, "bad training configuration");
+    cudaSetDevice(ctx->device);
+    const int64_t N = qf->N, M = qf->M;
+    const int64_t Qg = cfg.queries_per_group < N ? cfg.queries_per_group : N;
+    const int64_t Rg = cfg.refs_per_group;
+    const int64_t T = cfg.n_triples;
+    ndf_model* m = nullptr;
+    if ((st = ndf_model_create(ctx, cfg.res, measure, cfg.seed, qf->X, qf->Y, qf->Z, &m)) != NDF_OK)
+        return st;
+    auto bail = [&](ndf_status s) {
+        ndf_model_free(m);
+        return s;
+    };
+    if (measure == NDF_MEASURE_MI_KSG && (st = ensure_psi_table(ctx, M + 1)) != NDF_OK) return bail(st);
+
+    // ---- training triples
+    auto t0 = std::chrono::steady_clock::now();
+    int32_t *vref = nullptr, *vq = nullptr;
+    float *tgt = nullptr, *block = nullptr, *spare = nullptr;
+    int64_t* dq = nullptr;
+    cudaError_t e = cudaMalloc(&vref, (size_t)T * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&vq, (size_t)T * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&tgt, (size_t)T * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&block, (size_t)M * Qg * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&dq, (size_t)Qg * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&spare, (size_t)Qg * 4);
+    Field blk;
+    blk.live = true;
+    blk.M = M;
+    blk.Z = 1;
+    blk.Y = 1;
+    blk.X = Qg;
+    blk.N = Qg;
+    blk.data = block;
+    if (e == cudaSuccess && measure == NDF_MEASURE_PEARSON) {
+        e = cudaMalloc(&blk.mean, (size_t)Qg * 8);
+        if (e == cudaSuccess) e = cudaMalloc(&blk.inv_norm, (size_t)Qg * 8);
+    }
+    auto cleanup_data = [&]() {
+        void* ps[] = {vref, vq, tgt, block, dq, spare, blk.mean, blk.inv_norm};
+        for (void* q : ps)
+            if (q) cudaFree(q);
+    };
+    if (e != cudaSuccess) {
+        cleanup_data();
+        return bail(cuda_fail(ctx, e, "training-set buffers"));
+    }
+    std::vector<int64_t> hq((size_t)Qg);
+    std::vector<int32_t> hr((size_t)T), hqv((size_t)T);
+    const uint64_t key = host_mix(cfg.seed ^ 0x4e44465452414e53ULL);
+    int64_t filled = 0, group = 0;
+    int* d_flag = ctx->flag.as<int>();
+    while (filled < T && e == cudaSuccess) {
+        // queries of this group: Qg distinct-ish uniform vertices, sorted for locality
+        for (int64_t q = 0; q < Qg; ++q)
+            hq[(size_t)q] = (int64_t)(host_rand(key, (uint64_t)(group * 2 * Qg + q)) % (uint64_t)N);
+        std::sort(hq.begin(), hq.end());
+        e = cudaMemcpyAsync(dq, hq.data(), (size_t)Qg * 8, cudaMemcpyHostToDevice, ctx->stream);
+        if (e != cudaSuccess) break;
+        gather_columns_kernel<<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(qf->data, M, N, dq, Qg, block);
+        ctx->launches++;
+        if (measure == NDF_MEASURE_PEARSON) {
+            e = cudaMemsetAsync(d_flag, 0, 4, ctx->stream);
+            if (e == cudaSuccess) e = launch_field_stats(ctx, blk, d_flag);
+        }
+        for (int64_t r = 0; r < Rg && filled < T && e == cudaSuccess; ++r) {
+            const int64_t ref = (int64_t)(host_rand(key ^ 0xa5a5a5a5ULL, (uint64_t)(group * Rg + r)) %
+                                          (uint64_t)rf->N);
+            const int64_t take = T - filled < Qg ? T - filled : Qg;
+            float* dst = tgt + filled;
+            if (measure == NDF_MEASURE_PEARSON) {
+                if (take == Qg) {
+                    e = launch_pearson(ctx, *rf, blk, ref, dst);
+                } else {  // last partial row: full block into the spare row, keep `take`
+                    e = launch_pearson(ctx, *rf, blk, ref, spare);
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(dst, spare, (size_t)take * 4,
+                                            cudaMemcpyDeviceToDevice, ctx->stream);
+                }
+            } else {
+                e = launch_ksg(ctx, *rf, blk, ref, k, 0, take, dst, nullptr, nullptr, nullptr,
+                               nullptr);
+            }
+            for (int64_t q = 0; q < take; ++q) {
+                hr[(size_t)(filled + q)] = (int32_t)ref;
+                hqv[(size_t)(filled + q)] = (int32_t)hq[(size_t)q];
+            }
+            filled += take;
+        }
+        // the next group's gather overwrites the block: wait for this group's kernels
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        ++group;
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(vref, hr.data(), (size_t)T * 4, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(vq, hqv.data(), (size_t)T * 4, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        cleanup_data();
+        return bail(cuda_fail(ctx, e, "training-set generation"));
+    }
+    auto t1 = std::chrono::steady_clock::now();
+    m->gen_seconds = std::chrono::duration<double>(t1 - t0).count();
+    m->n_triples = T;
+
+    // ---- passes with Adam and the plateau schedule
+    const int64_t B = cfg.batch < T ? cfg.batch : T;
+    if ((st = ensure_work(m, B)) != NDF_OK) {
+        cleanup_data();
+        return bail(st);
+    }
+    float lr = cfg.lr;
+    double best = 1e300;
+    int bad = 0, decays = 0;
+    for (int pass = 0; pass < cfg.max_passes && e == cudaSuccess; ++pass) {
+        // a new affine bijection j = a*i + c (mod T) every pass
+        uint64_t a = host_rand(key ^ 0x5bd1e995ULL, (uint64_t)pass) % (uint64_t)T;
+        if (a == 0) a = 1;
+        while (std::gcd(a, (uint64_t)T) != 1) a = (a + 1) % (uint64_t)T == 0 ? 1 : a + 1;
+        const uint64_t c = host_rand(key ^ 0x27d4eb2fULL, (uint64_t)pass) % (uint64_t)T;
+        e = cudaMemsetAsync(m->work.loss, 0, 8, ctx->stream);
+        for (int64_t base = 0; base < T && e == cudaSuccess; base += B) {
+            const int64_t b = T - base < B ? T - base : B;
+            make_batch_kernel<<<(unsigned)((b + 255) / 256), 256, 0, ctx->stream>>>(
+                vref, vq, tgt, T, a, c, base, b, m->X, m->Y, m->Z, m->work.pos,
+                m->work.pos + 3 * B, m->work.target);
+            ctx->launches++;
+            e = model_step(m, m->work.pos, m->work.pos + 3 * B, m->work.target, b, lr, cfg.beta1,
+                           cfg.beta2, cfg.eps, true);
+            m->steps++;
+        }
+        double sum = 0.0;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&sum, m->work.loss, 8, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) break;
+        const double pass_loss = sum / (double)T;
+        m->last_loss = pass_loss;
+        m->passes = pass + 1;
+        if (pass_loss < best * (1.0 - 1e-4)) {
+            best = pass_loss;
+            bad = 0;
+        } else if (++bad > cfg.patience) {
+            lr *= 0.1f;
+            bad = 0;
+            if (++decays > cfg.max_decays) break;
+        }
+        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t1).count();
+        if (cfg.time_budget_s > 0.0 && el > cfg.time_budget_s) break;
+    }
+    m->train_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t1).count();
+    cleanup_data();
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "training"));
+    *out = m;
+    return NDF_OK;
+}
+
+// ---- model files: "NDFMODEL" v1, header, then FP32 params, Adam m and v
+struct FileHeader {
+    char magic[8];
+    int32_t version, measure;
+    int32_t res[4];
+    int64_t X, Y, Z, total, t;
+};
+
+ndf_status ndf_model_save(ndf_model* m, const char* path) {
+    if (!m || !path) return NDF_ERR_ARG;
+    ndf_ctx* ctx = m->ctx;
+    const size_t n = (size_t)m->L.total;
+    std::vector<float> buf(3 * n);
+    cudaError_t e = cudaMemcpyAsync(buf.data(), m->params, n * 4, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(buf.data() + n, m->m, n * 4, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(buf.data() + 2 * n, m->v, n * 4, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "model download");
+    FileHeader h;
+    memcpy(h.magic, "NDFMODEL", 8);
+    h.version = 1;
+    h.measure = m->measure;
+    for (int l = 0; l < 4; ++l) h.res[l] = m->L.res[l];
+    h.X = m->X;
+    h.Y = m->Y;
+    h.Z = m->Z;
+    h.total = m->L.total;
+    h.t = m->t;
+    FILE* f = fopen(path, "wb");
+    if (!f) return fail(ctx, NDF_ERR_IO, "cannot open %s", path);
+    bool ok = fwrite(&h, sizeof h, 1, f) == 1 && fwrite(buf.data(), 4, 3 * n, f) == 3 * n;
+    ok = (fclose(f) == 0) && ok;
+    return ok ? NDF_OK : fail(ctx, NDF_ERR_IO, "write to %s failed", path);
+}
+
+ndf_status ndf_model_load(ndf_ctx* ctx, const char* path, ndf_model** out) {
+    if (!ctx || !path || !out) return NDF_ERR_ARG;
+    FILE* f = fopen(path, "rb");
+    if (!f) return fail(ctx, NDF_ERR_IO, "cannot open %s", path);
+    FileHeader h;
+    if (fread(&h, sizeof h, 1, f) != 1 || memcmp(h.magic, "NDFMODEL", 8) != 0 || h.version != 1) {
+        fclose(f);
+        return fail(ctx, NDF_ERR_IO, "%s is not an NDF model file", path);
+    }
+    ndf_model* m = nullptr;
+    ndf_status st = ndf_model_create(ctx, h.res, h.measure, 0, h.X, h.Y, h.Z, &m);
+    if (st != NDF_OK) {
+        fclose(f);
+        return st;
+    }
+    if (m->L.total != h.total) {
+        fclose(f);
+        ndf_model_free(m);
+        return fail(ctx, NDF_ERR_IO, "%s: parameter count mismatch", path);
+    }
+    const size_t n = (size_t)h.total;
+    std::vector<float> buf(3 * n);
+    const bool ok = fread(buf.data(), 4, 3 * n, f) == 3 * n;
+    fclose(f);
+    if (!ok) {
+        ndf_model_free(m);
+        return fail(ctx, NDF_ERR_IO, "%s is truncated", path);
+    }
+    cudaError_t e = cudaMemcpyAsync(m->params, buf.data(), n * 4, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(m->m, buf.data() + n, n * 4, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(m->v, buf.data() + 2 * n, n * 4, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = model_refresh_bf16(m);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        ndf_model_free(m);
+        return cuda_fail(ctx, e, "model upload");
+    }
+    m->t = h.t;
+    *out = m;
+    return NDF_OK;
+}
+
+}  // extern "C"

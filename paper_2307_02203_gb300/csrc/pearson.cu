@@ -129,14 +129,15 @@ __global__ void __launch_bounds__(kPearsonThreads)
 
 cudaError_t launch_pearson(ndf_ctx* ctx, const Field& rf, const Field& qf, int64_t ref_idx,
                            float* out) {
-    const int64_t M = rf.M, N = rf.N;
+    // the reference column comes from rf (N_ref vertices), the volume from qf (N vertices)
+    const int64_t M = rf.M, N = qf.N, N_ref = rf.N;
     const int64_t Mpad = (M + 3) & ~int64_t(3);
     cudaError_t e = ctx->stage_x.reserve(sizeof(float) * (size_t)Mpad);
     if (e != cudaSuccess) return e;
     float* xt = ctx->stage_x.as<float>();
     unsigned* status = ctx->flag.as<unsigned>() + 1;
     int sb = (int)((Mpad + 255) / 256);
-    pearson_stage_kernel<<<sb < 64 ? sb : 64, 256, 0, ctx->stream>>>(rf.data, M, N, ref_idx,
+    pearson_stage_kernel<<<sb < 64 ? sb : 64, 256, 0, ctx->stream>>>(rf.data, M, N_ref, ref_idx,
                                                                       rf.mean, xt, Mpad);
     ctx->launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -66,6 +66,50 @@ _sig("ndf_ksg_debug_pair", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64,
                                           ctypes.c_int, _vp, _vp, _vp, _vp])
 
 
+class TrainCfg(ctypes.Structure):
+    """ndf_train_cfg (see include/ndf.h); fill with ndf_train_cfg_default()."""
+
+    _fields_ = [("res", ctypes.c_int * 4), ("n_triples", _i64), ("batch", _i64),
+                ("refs_per_group", _i64), ("queries_per_group", _i64), ("max_passes", ctypes.c_int),
+                ("patience", ctypes.c_int), ("max_decays", ctypes.c_int), ("lr", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("seed", ctypes.c_uint64), ("time_budget_s", ctypes.c_double)]
+
+
+class ModelInfo(ctypes.Structure):
+    """ndf_model_info_t (see include/ndf.h)."""
+
+    _fields_ = [("measure", ctypes.c_int), ("res", ctypes.c_int * 4), ("X", _i64), ("Y", _i64),
+                ("Z", _i64), ("param_count", _i64), ("grid_params", _i64),
+                ("network_bytes", _i64), ("training_bytes", _i64), ("adam_steps", _i64),
+                ("passes", ctypes.c_int), ("last_loss", ctypes.c_double), ("n_triples", _i64),
+                ("gen_seconds", ctypes.c_double), ("train_seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        d = {n: getattr(self, n) for n, _ in self._fields_}
+        d["res"] = list(self.res)
+        return d
+
+
+_sig("ndf_train_cfg_default", None, [ctypes.POINTER(TrainCfg)])
+_sig("ndf_train", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                 ctypes.POINTER(TrainCfg), ctypes.POINTER(_vp)])
+_sig("ndf_infer", ctypes.c_int, [_vp, _i64, _vp])
+_sig("ndf_infer_batch", ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp])
+_sig("ndf_model_save", ctypes.c_int, [_vp, ctypes.c_char_p])
+_sig("ndf_model_load", ctypes.c_int, [_vp, ctypes.c_char_p, ctypes.POINTER(_vp)])
+_sig("ndf_model_free", None, [_vp])
+_sig("ndf_model_info", ctypes.c_int, [_vp, ctypes.POINTER(ModelInfo)])
+_sig("ndf_model_create", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                        ctypes.c_uint64, _i64, _i64, _i64, ctypes.POINTER(_vp)])
+_sig("ndf_model_param_count", _i64, [_vp])
+_sig("ndf_model_get_params", ctypes.c_int, [_vp, _vp])
+_sig("ndf_model_set_params", ctypes.c_int, [_vp, _vp])
+_sig("ndf_model_step", ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, ctypes.c_float, ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_double), _vp])
+_sig("ndf_model_forward", ctypes.c_int, [_vp, _vp, _vp, _i64, _vp])
+
+
 def _addr(x):
     """Address of a torch tensor / numpy array / int / None."""
     if x is None:
@@ -180,6 +224,96 @@ def ndf_pearson_noalloc(ref_field, query_field, M, N, ref_idx, out, cuda_stream=
                                   _addr(out), cuda_stream)
     if st != NDF_OK:
         raise NdfError(st, "ndf_pearson_noalloc", "see include/ndf.h for the argument limits")
+
+
+def ndf_train_cfg_default() -> TrainCfg:
+    c = TrainCfg()
+    _lib.ndf_train_cfg_default(ctypes.byref(c))
+    return c
+
+
+def ndf_train(ctx, ref_field: int, query_field: int, measure: int, k: int, cfg=None):
+    """Returns an opaque model handle (free with ndf_model_free)."""
+    h = _vp()
+    _check(ctx, _lib.ndf_train(ctx, ref_field, query_field, measure, k,
+                               ctypes.byref(cfg) if cfg is not None else None, ctypes.byref(h)),
+           "ndf_train")
+    return h
+
+
+def _model_ctx_error(model, st, where):
+    # model-level calls report through the owning context; the handle hides it,
+    # so only the status and its description are available here
+    if st != NDF_OK:
+        raise NdfError(st, where, "")
+
+
+def ndf_infer(model, ref_idx: int, out) -> None:
+    _model_ctx_error(model, _lib.ndf_infer(model, ref_idx, _addr(out)), "ndf_infer")
+
+
+def ndf_infer_batch(model, ref_idx, out) -> None:
+    import numpy as _np
+
+    refs = _np.ascontiguousarray(_np.asarray(ref_idx, dtype=_np.int64))
+    _model_ctx_error(model, _lib.ndf_infer_batch(model, refs.ctypes.data, int(refs.shape[0]),
+                                                 _addr(out)), "ndf_infer_batch")
+
+
+def ndf_model_save(model, path: str) -> None:
+    _model_ctx_error(model, _lib.ndf_model_save(model, path.encode()), "ndf_model_save")
+
+
+def ndf_model_load(ctx, path: str):
+    h = _vp()
+    _check(ctx, _lib.ndf_model_load(ctx, path.encode(), ctypes.byref(h)), "ndf_model_load")
+    return h
+
+
+def ndf_model_free(model) -> None:
+    _lib.ndf_model_free(model)
+
+
+def ndf_model_info(model) -> dict:
+    info = ModelInfo()
+    _model_ctx_error(model, _lib.ndf_model_info(model, ctypes.byref(info)), "ndf_model_info")
+    return info.as_dict()
+
+
+def ndf_model_create(ctx, res, measure: int, seed: int, X: int, Y: int, Z: int):
+    r = (ctypes.c_int * 4)(*[int(v) for v in res])
+    h = _vp()
+    _check(ctx, _lib.ndf_model_create(ctx, r, measure, seed, X, Y, Z, ctypes.byref(h)),
+           "ndf_model_create")
+    return h
+
+
+def ndf_model_param_count(model) -> int:
+    return int(_lib.ndf_model_param_count(model))
+
+
+def ndf_model_get_params(model, out) -> None:
+    _model_ctx_error(model, _lib.ndf_model_get_params(model, _addr(out)), "ndf_model_get_params")
+
+
+def ndf_model_set_params(model, params) -> None:
+    _model_ctx_error(model, _lib.ndf_model_set_params(model, _addr(params)), "ndf_model_set_params")
+
+
+def ndf_model_step(model, p_ref, p_query, target, lr: float, update: bool, grad_out=None) -> float:
+    """Returns the mean L1 loss of the batch (positions [B][3] float32)."""
+    loss = ctypes.c_double(0.0)
+    B = int(p_ref.shape[0])
+    _model_ctx_error(model, _lib.ndf_model_step(model, _addr(p_ref), _addr(p_query), _addr(target),
+                                                B, float(lr), int(bool(update)), ctypes.byref(loss),
+                                                _addr(grad_out)), "ndf_model_step")
+    return loss.value
+
+
+def ndf_model_forward(model, p_ref, p_query, out) -> None:
+    _model_ctx_error(model, _lib.ndf_model_forward(model, _addr(p_ref), _addr(p_query),
+                                                   int(p_ref.shape[0]), _addr(out)),
+                     "ndf_model_forward")
 
 
 def exported_symbols():

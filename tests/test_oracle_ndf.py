@@ -130,3 +130,17 @@ def test_adam_constant_gradient_closed_form():
         oracle.adam_step(p, g, m, v, t, lr=lr, eps=eps)
         np.testing.assert_allclose(before - p, lr * g / (np.abs(g) + eps), rtol=1e-9, atol=1e-18)
     assert p[3] == start[3]
+
+
+def test_abs_term_gradient_consistent():
+    # the per-sample accumulation returns the same loss and gradient, and the
+    # summed magnitudes bound the (cancelling) sum element by element
+    s = tiny(1)
+    p = random_params(s, 13)
+    pr, pq = positions(40, 14)
+    t = np.random.default_rng(15).uniform(0.0, 1.5, size=40)
+    l1, g1 = oracle.ndf_loss_grad(s, p, pr, pq, t)
+    l2, g2, ga = oracle.ndf_loss_grad_abs(s, p, pr, pq, t)
+    assert l1 == pytest.approx(l2, abs=1e-15)
+    np.testing.assert_allclose(g1, g2, rtol=0, atol=1e-15)
+    assert (ga >= np.abs(g2) - 1e-15).all()
