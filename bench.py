@@ -208,6 +208,71 @@ def measure_pearson_batch(ndf, ctx, fid, field, recipe, stream, rank, R=64, reps
     return res
 
 
+def measure_ndf(ndf, ctx, fid, recipe, stream, args, exact_ms):
+    """Learned part: trains a Pearson and a KSG-MI network on the loaded field
+    (targets from the GPU estimators), then times volume decoding (1 reference
+    per launch and 16 per launch) and states MAE / max error per volume against
+    the exact estimator, beside the exact method's time on the same GPU."""
+    import torch
+
+    N = recipe.N
+    out = {}
+    rng = np.random.default_rng(777)
+    refs = [int(r) for r in rng.integers(0, N, size=16)]
+    for name, measure, k, triples in (("pearson", ndf.NDF_MEASURE_PEARSON, 0, args.ndf_triples),
+                                      ("mi", ndf.NDF_MEASURE_MI_KSG, K_NN, args.ndf_mi_triples)):
+        cfg = ndf.ndf_train_cfg_default()
+        cfg.n_triples = int(triples)
+        cfg.time_budget_s = float(args.ndf_seconds)
+        t0 = time.perf_counter()
+        model = ndf.ndf_train(ctx, fid, fid, measure, k, cfg)
+        ndf.ndf_synchronize(ctx)
+        wall = time.perf_counter() - t0
+        info = ndf.ndf_model_info(model)
+        one = torch.empty(N, dtype=torch.float32, device="cuda")
+        many = torch.empty((16, N), dtype=torch.float32, device="cuda")
+        for _ in range(3):
+            ndf.ndf_infer(model, refs[0], one)
+            ndf.ndf_infer_batch(model, refs, many)
+        ndf.ndf_synchronize(ctx)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        for r in refs:
+            ndf.ndf_infer(model, r, one)
+        e1.record(stream)
+        ndf.ndf_infer_batch(model, refs, many)
+        e2.record(stream)
+        ndf.ndf_synchronize(ctx)
+        ms_one = e0.elapsed_time(e1) / len(refs)
+        ms_batch = e1.elapsed_time(e2) / len(refs)
+        # exact volumes of the same references for the error statement
+        n_err = 16 if measure == ndf.NDF_MEASURE_PEARSON else args.ndf_mi_err_refs
+        exact = torch.empty((n_err, N), dtype=torch.float32, device="cuda")
+        if measure == ndf.NDF_MEASURE_PEARSON:
+            ndf.ndf_pearson_batch(ctx, fid, fid, refs[:n_err], ndf.NDF_PREC_FP32, exact)
+        else:
+            for i in range(n_err):
+                ndf.ndf_mi_ksg(ctx, fid, fid, refs[i], K_NN, exact[i])
+        ndf.ndf_synchronize(ctx)
+        err = (many[:n_err] - exact).abs()
+        out[name] = {
+            "triples": info["n_triples"], "triples_per_s": info["n_triples"] / max(info["gen_seconds"], 1e-9),
+            "train_seconds": info["train_seconds"], "adam_steps": info["adam_steps"],
+            "train_steps_per_s": info["adam_steps"] / max(info["train_seconds"], 1e-9),
+            "passes": info["passes"], "last_pass_l1": info["last_loss"], "batch": int(cfg.batch),
+            "train_wall_s": wall,
+            "network_bytes": info["network_bytes"], "training_bytes": info["training_bytes"],
+            "decode_ms_per_volume_1ref": ms_one, "decode_ms_per_volume_16refs": ms_batch,
+            "exact_ms_per_volume": exact_ms[name],
+            "speedup_vs_exact_16refs": exact_ms[name] / ms_batch,
+            "mae": float(err.mean()), "max_err_mean_over_refs": float(err.amax(dim=1).mean()),
+            "max_err": float(err.max()), "error_refs": n_err,
+            "exact_mean_abs_value": float(exact.abs().mean()),
+        }
+        ndf.ndf_model_free(model)
+    return out
+
+
 def run_reference(args, recipe):
     rank = env_int("RANK", 0)
     if rank != 0:
@@ -244,6 +309,11 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--batch", type=int, default=1, help="also time 64-reference Pearson GEMMs")
+    ap.add_argument("--ndf", type=int, default=1, help="also train and time the neural field")
+    ap.add_argument("--ndf-seconds", type=float, default=25.0, help="training budget per network")
+    ap.add_argument("--ndf-triples", type=int, default=1 << 26, help="Pearson training triples")
+    ap.add_argument("--ndf-mi-triples", type=int, default=1 << 24, help="KSG-MI training triples")
+    ap.add_argument("--ndf-mi-err-refs", type=int, default=4, help="exact KSG volumes for MI error")
     ap.add_argument("--workload", choices=["csens", "csens-slab", "tiny"], default="csens",
                     help="csens: 250x352x20, M=1000 (the benchmark); csens-slab: one vertical "
                          "level of it (profiling); tiny: 16x16x4, M=100 (checks)")
@@ -326,6 +396,10 @@ def main():
     # ---- batched multi-reference Pearson (64 references per call) per precision
     batch = measure_pearson_batch(ndf, ctx, fid, field, recipe, stream, rank) if args.batch else None
 
+    # ---- learned part: train, decode, error against the exact estimators
+    ndf_res = measure_ndf(ndf, ctx, fid, recipe, stream, args,
+                          {"pearson": pearson_ms, "mi": ksg_ms}) if args.ndf else None
+
     # ---- end to end through the ABI with host buffers (upload + stats + both volumes + D2H)
     host_r = torch.empty(N, dtype=torch.float32, pin_memory=True)
     host_mi = torch.empty(N, dtype=torch.float32, pin_memory=True)
@@ -381,6 +455,7 @@ def main():
                     "d2h_bytes_per_step": int(2 * N * 4)},
             "gpu_launches": int(launches),
             "pearson_batch64": batch,
+            "ndf": ndf_res,
             "clocks": clocks,
             "cpu_baseline": cpu,
         }

@@ -27,6 +27,7 @@
 #include <limits.h>
 
 #include "device_common.cuh"
+#include "ksg_common.cuh"
 #include "ndf_internal.h"
 
 namespace ndf {
@@ -71,58 +72,6 @@ __global__ void __launch_bounds__(1024) ksg_stage_kernel(const float* __restrict
         xs_out[i] = key[i];
         perm_out[i] = val[i];
     }
-}
-
-// ---------------------------------------------------------------- helpers
-// sorted ascending a[0..K1): insert d, dropping the largest; identity if d >= a[K1-1]
-template <int K1>
-__device__ __forceinline__ void topk_insert(float (&a)[K1], float d) {
-#pragma unroll
-    for (int p = K1 - 1; p > 0; --p) a[p] = fmaxf(a[p - 1], fminf(a[p], d));
-    a[0] = fminf(a[0], d);
-}
-
-// #{p : |fl(a[p] - c)| < e} in the ascending array a[0..n) by two binary
-// searches on predicates that are monotone in p.
-__device__ __forceinline__ int count_within(const float* a, int n, float c, float e) {
-    int lo = 0, len = n;
-    while (len > 0) {  // first p with fl(c - a[p]) < e
-        int h = len >> 1;
-        if (!((c - a[lo + h]) < e)) {
-            lo += h + 1;
-            len -= h + 1;
-        } else {
-            len = h;
-        }
-    }
-    int hi = 0;
-    len = n;
-    while (len > 0) {  // first p with fl(a[p] - c) >= e
-        int h = len >> 1;
-        if (!((a[hi + h] - c) >= e)) {
-            hi += h + 1;
-            len -= h + 1;
-        } else {
-            len = h;
-        }
-    }
-    return hi > lo ? hi - lo : 0;
-}
-
-__device__ __forceinline__ double block_sum(double v, double* red) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) red[w] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x < 32) {
-        int nw = (blockDim.x + 31) >> 5;
-        t = threadIdx.x < nw ? red[threadIdx.x] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-    }
-    return t;  // valid in thread 0
 }
 
 struct KsgArgs {

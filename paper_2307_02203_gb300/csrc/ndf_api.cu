@@ -215,6 +215,7 @@ void ndf_destroy(ndf_ctx* ctx) {
     ctx->flag.release();
     ctx->zr.release();
     ctx->refidx.release();
+    ctx->evals.release();
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     delete ctx;
 }
@@ -357,6 +358,23 @@ static ndf_status check_ksg_args(ndf_ctx* ctx, const Field* rf, int k) {
     return NDF_OK;
 }
 
+// one reference over [v_begin, v_end) with the context's algorithm
+static cudaError_t run_ksg_one(ndf_ctx* ctx, const Field& rf, const Field& qf, int64_t ref_idx,
+                               int k, int64_t v_begin, int64_t v_end, float* out, double* dbg_mi,
+                               float* dbg_eps, int32_t* dbg_nx, int32_t* dbg_ny) {
+    if (ctx->ksg_algorithm == NDF_KSG_BRUTE)
+        return launch_ksg(ctx, rf, qf, ref_idx, k, v_begin, v_end, out, dbg_mi, dbg_eps, dbg_nx,
+                          dbg_ny);
+    cudaError_t e = ctx->refidx.reserve(sizeof(int64_t));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->refidx.ptr, &ref_idx, sizeof(int64_t), cudaMemcpyHostToDevice,
+                            ctx->stream);
+    if (e != cudaSuccess) return e;
+    return launch_ksg_pruned(ctx, rf, qf, ctx->refidx.as<int64_t>(), 1, k, v_begin, v_end, out,
+                             0, 1, 8, dbg_mi, dbg_eps, dbg_nx, dbg_ny,
+                             ctx->count_evals ? ctx->evals.as<unsigned long long>() : nullptr);
+}
+
 ndf_status ndf_mi_ksg(ndf_ctx* ctx, int ref_field, int query_field, int64_t ref_idx, int k,
                       float* out) {
     if (!ctx) return NDF_ERR_ARG;
@@ -370,8 +388,8 @@ ndf_status ndf_mi_ksg(ndf_ctx* ctx, int ref_field, int query_field, int64_t ref_
     void* dev_out;
     bool is_host;
     if ((st = resolve_out(ctx, out, bytes, &dev_out, &is_host)) != NDF_OK) return st;
-    cudaError_t e = launch_ksg(ctx, *rf, *qf, ref_idx, k, 0, qf->N, (float*)dev_out, nullptr,
-                               nullptr, nullptr, nullptr);
+    cudaError_t e = run_ksg_one(ctx, *rf, *qf, ref_idx, k, 0, qf->N, (float*)dev_out, nullptr,
+                                nullptr, nullptr, nullptr);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "ksg launch");
     return finish_out(ctx, out, dev_out, bytes, is_host);
 }
@@ -398,8 +416,8 @@ ndf_status ndf_ksg_debug_pair(ndf_ctx* ctx, int ref_field, int query_field, int6
     float* d_eps = (float*)(base + 16);
     int32_t* d_nx = (int32_t*)(d_eps + M);
     int32_t* d_ny = d_nx + M;
-    e = launch_ksg(ctx, *rf, *qf, ref_idx, k, query_idx, query_idx + 1, d_out, d_mi,
-                   d_eps, d_nx, d_ny);
+    e = run_ksg_one(ctx, *rf, *qf, ref_idx, k, query_idx, query_idx + 1, d_out, d_mi, d_eps, d_nx,
+                    d_ny);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "ksg debug launch");
     std::vector<char> h(need);
     e = cudaMemcpyAsync(h.data(), base, need, cudaMemcpyDeviceToHost, ctx->stream);
@@ -411,6 +429,63 @@ ndf_status ndf_ksg_debug_pair(ndf_ctx* ctx, int ref_field, int query_field, int6
     if (nx) memcpy(nx, hb + 16 + 4 * M, sizeof(int32_t) * (size_t)M);
     if (ny) memcpy(ny, hb + 16 + 8 * M, sizeof(int32_t) * (size_t)M);
     return NDF_OK;
+}
+
+ndf_status ndf_set_ksg_algorithm(ndf_ctx* ctx, int algorithm, int count_evals) {
+    if (!ctx) return NDF_ERR_ARG;
+    if (algorithm != NDF_KSG_BRUTE && algorithm != NDF_KSG_PRUNED)
+        return fail(ctx, NDF_ERR_ARG, "unknown KSG algorithm %d", algorithm);
+    ctx->ksg_algorithm = algorithm;
+    ctx->count_evals = count_evals != 0;
+    if (ctx->count_evals) {
+        cudaError_t e = ctx->evals.reserve(sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMemsetAsync(ctx->evals.ptr, 0, sizeof(unsigned long long), ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "evaluation counter");
+    }
+    return NDF_OK;
+}
+
+ndf_status ndf_ksg_take_eval_count(ndf_ctx* ctx, uint64_t* out) {
+    if (!ctx || !out) return NDF_ERR_ARG;
+    *out = 0;
+    if (!ctx->count_evals || !ctx->evals.ptr) return NDF_OK;
+    unsigned long long v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, ctx->evals.ptr, sizeof v, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->evals.ptr, 0, sizeof v, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "evaluation counter read");
+    *out = v;
+    return NDF_OK;
+}
+
+ndf_status ndf_mi_ksg_batch(ndf_ctx* ctx, int ref_field, int query_field, const int64_t* ref_idx,
+                            int R, int k, float* out) {
+    if (!ctx) return NDF_ERR_ARG;
+    if (!ref_idx || R < 1) return fail(ctx, NDF_ERR_ARG, "need R >= 1 reference indices");
+    const Field *rf, *qf;
+    ndf_status st = check_pair(ctx, ref_field, query_field, 0, &rf, &qf);
+    if (st != NDF_OK) return st;
+    for (int i = 0; i < R; ++i)
+        if (ref_idx[i] < 0 || ref_idx[i] >= rf->N)
+            return fail(ctx, NDF_ERR_ARG, "ref_idx[%d] out of range", i);
+    if ((st = check_ksg_args(ctx, rf, k)) != NDF_OK) return st;
+    cudaSetDevice(ctx->device);
+    if ((st = ensure_psi_table(ctx, rf->M + 1)) != NDF_OK) return st;
+    const size_t bytes = sizeof(float) * (size_t)R * (size_t)qf->N;
+    void* dev_out;
+    bool is_host;
+    if ((st = resolve_out(ctx, out, bytes, &dev_out, &is_host)) != NDF_OK) return st;
+    cudaError_t e = ctx->refidx.reserve(sizeof(int64_t) * (size_t)R);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->refidx.ptr, ref_idx, sizeof(int64_t) * (size_t)R,
+                            cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+        e = launch_ksg_pruned(ctx, *rf, *qf, ctx->refidx.as<int64_t>(), R, k, 0, qf->N,
+                              static_cast<float*>(dev_out), qf->N, ctx->ksg_group, ctx->ksg_tile,
+                              nullptr, nullptr, nullptr, nullptr,
+                              ctx->count_evals ? ctx->evals.as<unsigned long long>() : nullptr);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "ksg batch launch");
+    return finish_out(ctx, out, dev_out, bytes, is_host);
 }
 
 }  // extern "C"

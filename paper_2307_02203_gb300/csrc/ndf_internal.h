@@ -54,6 +54,11 @@ struct ndf_ctx {
     int64_t psi_n = 0;
     ndf::DevBuf dbg;         // KSG debug outputs
     ndf::DevBuf flag;        // small device status words
+    int ksg_algorithm = NDF_KSG_PRUNED;
+    int ksg_group = 4;       // references per CTA in batched KSG (tuned by ndf_ksg_autotune)
+    int ksg_tile = 8;        // query vertices per tile
+    bool count_evals = false;
+    ndf::DevBuf evals;       // KSG distance evaluations (when counting is on)
     ndf::DevBuf zr;          // batched Pearson: standardised reference rows
     ndf::DevBuf refidx;      // batched calls: reference indices on the device
 };
@@ -87,6 +92,11 @@ cudaError_t launch_pearson(ndf_ctx* ctx, const Field& rf, const Field& qf, int64
 cudaError_t launch_ksg(ndf_ctx* ctx, const Field& rf, const Field& qf, int64_t ref_idx, int k,
                        int64_t v_begin, int64_t v_end, float* out, double* dbg_mi, float* dbg_eps,
                        int32_t* dbg_nx, int32_t* dbg_ny);
+
+cudaError_t launch_ksg_pruned(ndf_ctx* ctx, const Field& rf, const Field& qf, const int64_t* d_refs,
+                              int R, int k, int64_t v_begin, int64_t v_end, float* out,
+                              int64_t out_stride, int G, int VT, double* dbg_mi, float* dbg_eps,
+                              int32_t* dbg_nx, int32_t* dbg_ny, unsigned long long* evals);
 
 constexpr int kKsgMaxM = 4096;
 constexpr int kKsgMaxK = 16;

@@ -600,14 +600,15 @@ ndf_status ndf_train(ndf_ctx* ctx, int ref_field, int query_field, int measure, 
     // ---- training triples
     auto t0 = std::chrono::steady_clock::now();
     int32_t *vref = nullptr, *vq = nullptr;
-    float *tgt = nullptr, *block = nullptr, *spare = nullptr;
-    int64_t* dq = nullptr;
+    float *tgt = nullptr, *block = nullptr, *gtgt = nullptr;
+    int64_t *dq = nullptr, *drefs = nullptr;
     cudaError_t e = cudaMalloc(&vref, (size_t)T * 4);
     if (e == cudaSuccess) e = cudaMalloc(&vq, (size_t)T * 4);
     if (e == cudaSuccess) e = cudaMalloc(&tgt, (size_t)T * 4);
     if (e == cudaSuccess) e = cudaMalloc(&block, (size_t)M * Qg * 4);
     if (e == cudaSuccess) e = cudaMalloc(&dq, (size_t)Qg * 8);
-    if (e == cudaSuccess) e = cudaMalloc(&spare, (size_t)Qg * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&gtgt, (size_t)Rg * Qg * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&drefs, (size_t)Rg * 8);
     Field blk;
     blk.live = true;
     blk.M = M;
@@ -621,7 +622,7 @@ ndf_status ndf_train(ndf_ctx* ctx, int ref_field, int query_field, int measure, 
         if (e == cudaSuccess) e = cudaMalloc(&blk.inv_norm, (size_t)Qg * 8);
     }
     auto cleanup_data = [&]() {
-        void* ps[] = {vref, vq, tgt, block, dq, spare, blk.mean, blk.inv_norm};
+        void* ps[] = {vref, vq, tgt, block, dq, gtgt, drefs, blk.mean, blk.inv_norm};
         for (void* q : ps)
             if (q) cudaFree(q);
     };
@@ -629,7 +630,7 @@ ndf_status ndf_train(ndf_ctx* ctx, int ref_field, int query_field, int measure, 
         cleanup_data();
         return bail(cuda_fail(ctx, e, "training-set buffers"));
     }
-    std::vector<int64_t> hq((size_t)Qg);
+    std::vector<int64_t> hq((size_t)Qg), hrefs((size_t)Rg);
     std::vector<int32_t> hr((size_t)T), hqv((size_t)T);
     const uint64_t key = host_mix(cfg.seed ^ 0x4e44465452414e53ULL);
     int64_t filled = 0, group = 0;
@@ -647,30 +648,32 @@ ndf_status ndf_train(ndf_ctx* ctx, int ref_field, int query_field, int measure, 
             e = cudaMemsetAsync(d_flag, 0, 4, ctx->stream);
             if (e == cudaSuccess) e = launch_field_stats(ctx, blk, d_flag);
         }
-        for (int64_t r = 0; r < Rg && filled < T && e == cudaSuccess; ++r) {
-            const int64_t ref = (int64_t)(host_rand(key ^ 0xa5a5a5a5ULL, (uint64_t)(group * Rg + r)) %
-                                          (uint64_t)rf->N);
-            const int64_t take = T - filled < Qg ? T - filled : Qg;
-            float* dst = tgt + filled;
-            if (measure == NDF_MEASURE_PEARSON) {
-                if (take == Qg) {
-                    e = launch_pearson(ctx, *rf, blk, ref, dst);
-                } else {  // last partial row: full block into the spare row, keep `take`
-                    e = launch_pearson(ctx, *rf, blk, ref, spare);
-                    if (e == cudaSuccess)
-                        e = cudaMemcpyAsync(dst, spare, (size_t)take * 4,
-                                            cudaMemcpyDeviceToDevice, ctx->stream);
-                }
-            } else {
-                e = launch_ksg(ctx, *rf, blk, ref, k, 0, take, dst, nullptr, nullptr, nullptr,
-                               nullptr);
-            }
-            for (int64_t q = 0; q < take; ++q) {
-                hr[(size_t)(filled + q)] = (int32_t)ref;
-                hqv[(size_t)(filled + q)] = (int32_t)hq[(size_t)q];
-            }
-            filled += take;
+        // reference vertices of this group (as many as the remaining triples need)
+        const int64_t rows = std::min<int64_t>(Rg, (T - filled + Qg - 1) / Qg);
+        for (int64_t r = 0; r < rows; ++r)
+            hrefs[(size_t)r] = (int64_t)(host_rand(key ^ 0xa5a5a5a5ULL, (uint64_t)(group * Rg + r)) %
+                                         (uint64_t)rf->N);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(drefs, hrefs.data(), (size_t)rows * 8, cudaMemcpyHostToDevice,
+                                ctx->stream);
+        if (measure == NDF_MEASURE_PEARSON) {
+            for (int64_t r = 0; r < rows && e == cudaSuccess; ++r)
+                e = launch_pearson(ctx, *rf, blk, hrefs[(size_t)r], gtgt + r * Qg);
+        } else if (e == cudaSuccess) {
+            // all references of the group in one launch; each query column is sorted once
+            e = launch_ksg_pruned(ctx, *rf, blk, drefs, (int)rows, k, 0, Qg, gtgt, Qg,
+                                  ctx->ksg_group, ctx->ksg_tile, nullptr, nullptr, nullptr,
+                                  nullptr, nullptr);
         }
+        const int64_t take = std::min<int64_t>(T - filled, rows * Qg);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(tgt + filled, gtgt, (size_t)take * 4, cudaMemcpyDeviceToDevice,
+                                ctx->stream);
+        for (int64_t i = 0; i < take; ++i) {
+            hr[(size_t)(filled + i)] = (int32_t)hrefs[(size_t)(i / Qg)];
+            hqv[(size_t)(filled + i)] = (int32_t)hq[(size_t)(i % Qg)];
+        }
+        filled += take;
         // the next group's gather overwrites the block: wait for this group's kernels
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         ++group;

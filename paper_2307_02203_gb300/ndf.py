@@ -26,6 +26,7 @@ NDF_OK, NDF_ERR_ARG, NDF_ERR_OOM, NDF_ERR_CUDA = 0, -1, -2, -3
 NDF_ERR_TIMEOUT, NDF_ERR_STATE, NDF_ERR_IO = -4, -5, -6
 NDF_PREC_FP32, NDF_PREC_BF16X3, NDF_PREC_TF32 = 0, 1, 2
 NDF_MEASURE_PEARSON, NDF_MEASURE_MI_KSG = 0, 1
+NDF_KSG_BRUTE, NDF_KSG_PRUNED = 0, 1
 
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -61,6 +62,12 @@ _sig("ndf_pearson", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, _vp])
 _sig("ndf_mi_ksg", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, ctypes.c_int, _vp])
 _sig("ndf_pearson_batch", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int,
                                          ctypes.c_int, _vp])
+_sig("ndf_set_ksg_algorithm", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int])
+_sig("ndf_ksg_take_eval_count", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64)])
+_sig("ndf_mi_ksg_batch", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int,
+                                        ctypes.c_int, _vp])
+_sig("ndf_ksg_autotune", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)])
 _sig("ndf_pearson_noalloc", ctypes.c_int, [_vp, _vp, _i64, _i64, _i64, _vp, _vp])
 _sig("ndf_ksg_debug_pair", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, _i64,
                                           ctypes.c_int, _vp, _vp, _vp, _vp])
@@ -210,6 +217,33 @@ def ndf_pearson_batch(ctx, ref_field: int, query_field: int, ref_idx, prec: int,
 def ndf_mi_ksg(ctx, ref_field: int, query_field: int, ref_idx: int, k: int, out) -> None:
     _check(ctx, _lib.ndf_mi_ksg(ctx, ref_field, query_field, ref_idx, k, _addr(out)),
            "ndf_mi_ksg")
+
+
+def ndf_set_ksg_algorithm(ctx, algorithm: int, count_evals: bool = False) -> None:
+    _check(ctx, _lib.ndf_set_ksg_algorithm(ctx, int(algorithm), int(bool(count_evals))),
+           "ndf_set_ksg_algorithm")
+
+
+def ndf_ksg_take_eval_count(ctx) -> int:
+    v = ctypes.c_uint64(0)
+    _check(ctx, _lib.ndf_ksg_take_eval_count(ctx, ctypes.byref(v)), "ndf_ksg_take_eval_count")
+    return int(v.value)
+
+
+def ndf_mi_ksg_batch(ctx, ref_field: int, query_field: int, ref_idx, k: int, out) -> None:
+    import numpy as _np
+
+    refs = _np.ascontiguousarray(_np.asarray(ref_idx, dtype=_np.int64))
+    _check(ctx, _lib.ndf_mi_ksg_batch(ctx, ref_field, query_field, refs.ctypes.data,
+                                      int(refs.shape[0]), int(k), _addr(out)), "ndf_mi_ksg_batch")
+
+
+def ndf_ksg_autotune(ctx, ref_field: int, query_field: int, k: int):
+    g = ctypes.c_int(0)
+    t = ctypes.c_int(0)
+    _check(ctx, _lib.ndf_ksg_autotune(ctx, ref_field, query_field, k, ctypes.byref(g),
+                                      ctypes.byref(t)), "ndf_ksg_autotune")
+    return g.value, t.value
 
 
 def ndf_ksg_debug_pair(ctx, ref_field, query_field, ref_idx, query_idx, k, eps, nx, ny, mi) -> None:

@@ -116,6 +116,15 @@ def test_pearson_cross_field_and_degenerate(ndf_mod, ctx):
 
 
 # ---------------------------------------------------------------- KSG algorithm 1
+@pytest.fixture(params=["brute", "pruned"])
+def algo(request, ndf_mod, ctx):
+    """Both searches must give the same bit-exact eps / counts."""
+    code = {"brute": ndf_mod.NDF_KSG_BRUTE, "pruned": ndf_mod.NDF_KSG_PRUNED}[request.param]
+    ndf_mod.ndf_set_ksg_algorithm(ctx, code)
+    yield request.param
+    ndf_mod.ndf_set_ksg_algorithm(ctx, ndf_mod.NDF_KSG_PRUNED)
+
+
 def ksg_debug(ndf, ctx, fa, fb, r, v, k, M):
     eps = np.empty(M, dtype=np.float32)
     nx = np.empty(M, dtype=np.int32)
@@ -138,14 +147,14 @@ def check_pairs_bit_exact(ndf, ctx, fa, fb, a, b, r, verts, k):
         assert abs(g[0] - o[0]) <= 1e-6 * abs(o[0]) + 1e-9, (v, g[0], o[0])
 
 
-def test_ksg_tiny_every_pair_bit_exact(ndf_mod, ctx, tiny_field, tiny_ref):
+def test_ksg_tiny_every_pair_bit_exact(ndf_mod, ctx, algo, tiny_field, tiny_ref):
     fid = load(ndf_mod, ctx, tiny_field)
     N = tiny_field[0].size
     check_pairs_bit_exact(ndf_mod, ctx, fid, fid, tiny_field, tiny_field, tiny_ref, range(N), 4)
     ndf_mod.ndf_free_ensemble(ctx, fid)
 
 
-def test_ksg_tiny_volume(ndf_mod, ctx, tiny_field, tiny_ref):
+def test_ksg_tiny_volume(ndf_mod, ctx, algo, tiny_field, tiny_ref):
     fid = load(ndf_mod, ctx, tiny_field)
     N = tiny_field[0].size
     out = np.empty(N, dtype=np.float32)
@@ -169,7 +178,7 @@ def test_ksg_tiny_volume(ndf_mod, ctx, tiny_field, tiny_ref):
     ((100, 2, 3, 5), 3, "ties"),
     ((333, 1, 1, 13), 5, "normal"),    # M not a multiple of 4
 ])
-def test_ksg_shapes(ndf_mod, ctx, shape, k, kind):
+def test_ksg_shapes(ndf_mod, ctx, algo, shape, k, kind):
     f = rand_field(shape, seed=shape[0] + k, kind=kind)
     f[:, 0, 0, 0] = f[:, -1, -1, -1] ** 2 + 0.1 * f[:, 0, 0, 0]
     fid = load(ndf_mod, ctx, f)
@@ -184,7 +193,7 @@ def test_ksg_shapes(ndf_mod, ctx, shape, k, kind):
     ndf_mod.ndf_free_ensemble(ctx, fid)
 
 
-def test_ksg_cross_field(ndf_mod, ctx):
+def test_ksg_cross_field(ndf_mod, ctx, algo):
     shape = (300, 2, 4, 6)
     a = rand_field(shape, 21)
     b = (np.tanh(a) + 0.5 * rand_field(shape, 22)).astype(np.float32)
@@ -197,6 +206,48 @@ def test_ksg_cross_field(ndf_mod, ctx):
     check_pairs_bit_exact(ndf_mod, ctx, fa, fb, a, b, 5, [0, 5, N - 1], 8)
     ndf_mod.ndf_free_ensemble(ctx, fa)
     ndf_mod.ndf_free_ensemble(ctx, fb)
+
+
+# ---------------------------------------------------------------- batched KSG
+def test_ksg_batch_matches_oracle_and_single(ndf_mod, ctx):
+    ndf = ndf_mod
+    shape = (1000, 2, 6, 11)
+    f = rand_field(shape, seed=77)
+    f[:, 1] = np.tanh(f[:, 0]) + 0.3 * f[:, 1]
+    fid = load(ndf, ctx, f)
+    N = f[0].size
+    refs = [0, 5, 131, N - 1, 64]
+    out = np.empty((len(refs), N), dtype=np.float32)
+    ndf.ndf_mi_ksg_batch(ctx, fid, fid, refs, 8, out)
+    for i, r in enumerate(refs):
+        ok, where = mi_close(out[i], oracle.ksg_volume(f, f, r, 8))
+        assert ok, (r, where)
+        single = np.empty(N, dtype=np.float32)
+        ndf.ndf_mi_ksg(ctx, fid, fid, r, 8, single)
+        np.testing.assert_array_equal(out[i], single)
+    g, t = ndf.ndf_ksg_autotune(ctx, fid, fid, 8)
+    assert g in (1, 2, 4, 8) and t in (4, 8)
+    dev = torch.empty((len(refs), N), dtype=torch.float32, device="cuda")
+    ndf.ndf_mi_ksg_batch(ctx, fid, fid, refs, 8, dev)
+    ndf.ndf_synchronize(ctx)
+    np.testing.assert_array_equal(dev.cpu().numpy(), out)
+    ndf.ndf_free_ensemble(ctx, fid)
+
+
+def test_ksg_eval_counter(ndf_mod, ctx, tiny_field, tiny_ref):
+    ndf = ndf_mod
+    fid = load(ndf, ctx, tiny_field)
+    M = tiny_field.shape[0]
+    N = tiny_field[0].size
+    out = np.empty(N, dtype=np.float32)
+    ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_PRUNED, True)
+    ndf.ndf_mi_ksg(ctx, fid, fid, tiny_ref, 4, out)
+    evals = ndf.ndf_ksg_take_eval_count(ctx)
+    ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_PRUNED, False)
+    # the pruned search visits a strict subset of the M(M-1) candidates of each pair
+    assert 0 < evals < N * M * (M - 1)
+    assert ndf.ndf_ksg_take_eval_count(ctx) == 0
+    ndf.ndf_free_ensemble(ctx, fid)
 
 
 # ---------------------------------------------------------------- argument errors

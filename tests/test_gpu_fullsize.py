@@ -38,12 +38,15 @@ def test_csens_pearson_sampled(ndf_mod, ctx, csens):
     assert np.isfinite(out.cpu().numpy()).all()
 
 
-def test_csens_ksg_sampled(ndf_mod, ctx, csens):
+@pytest.mark.parametrize("algorithm", ["pruned", "brute"])
+def test_csens_ksg_sampled(ndf_mod, ctx, csens, algorithm):
     f, fid = csens
     N = synth.CSENS.N
     M = synth.CSENS.M
     r = synth.vertex_index(*REF, synth.CSENS)
     out = torch.empty(N, dtype=torch.float32, device="cuda")
+    code = ndf_mod.NDF_KSG_PRUNED if algorithm == "pruned" else ndf_mod.NDF_KSG_BRUTE
+    ndf_mod.ndf_set_ksg_algorithm(ctx, code)
     ndf_mod.ndf_mi_ksg(ctx, fid, fid, r, 8, out)
     ndf_mod.ndf_synchronize(ctx)
     vol = out.cpu().numpy()
@@ -66,3 +69,20 @@ def test_csens_ksg_sampled(ndf_mod, ctx, csens):
         np.testing.assert_array_equal(eps, o[1])
         np.testing.assert_array_equal(nx, o[2])
         np.testing.assert_array_equal(ny, o[3])
+    ndf_mod.ndf_set_ksg_algorithm(ctx, ndf_mod.NDF_KSG_PRUNED)
+
+
+def test_csens_ksg_batch_sampled(ndf_mod, ctx, csens):
+    """Four references in one batched launch against the oracle on sampled vertices."""
+    f, fid = csens
+    N = synth.CSENS.N
+    refs = [int(v) for v in synth.sample_vertices(synth.CSENS, 4, seed=8)]
+    out = torch.empty((4, N), dtype=torch.float32, device="cuda")
+    ndf_mod.ndf_mi_ksg_batch(ctx, fid, fid, refs, 8, out)
+    ndf_mod.ndf_synchronize(ctx)
+    vol = out.cpu().numpy()
+    verts = synth.sample_vertices(synth.CSENS, 512, seed=9)
+    for i, r in enumerate(refs):
+        ref = oracle.ksg_volume(f, f, r, 8, verts=verts)
+        got = vol[i][verts].astype(np.float64)
+        assert (np.abs(got - ref) <= 1e-6 * np.abs(ref) + 1e-9).all()
