@@ -208,6 +208,26 @@ def measure_pearson_batch(ndf, ctx, fid, field, recipe, stream, rank, R=64, reps
     return res
 
 
+def measure_ksg_batch(ndf, ctx, fid, recipe, stream, args, R=64):
+    """R KSG volumes in one persistent launch after the tile autotuner."""
+    import torch
+
+    N = recipe.N
+    g, t = ndf.ndf_ksg_autotune(ctx, fid, fid, K_NN)
+    rng = np.random.default_rng(555)
+    refs = [int(r) for r in rng.integers(0, N, size=R)]
+    out = torch.empty((R, N), dtype=torch.float32, device="cuda")
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ndf.ndf_mi_ksg_batch(ctx, fid, fid, refs, K_NN, out)
+    e1.record(stream)
+    ndf.ndf_synchronize(ctx)
+    ms = e0.elapsed_time(e1)
+    return {"refs": R, "ms": ms, "ms_per_volume": ms / R, "mi_pairs_per_s": R * N / (ms * 1e-3),
+            "refs_per_cta": g, "vertices_per_tile": t}
+
+
 def measure_ndf(ndf, ctx, fid, recipe, stream, args, exact_ms):
     """Learned part: trains a Pearson and a KSG-MI network on the loaded field
     (targets from the GPU estimators), then times volume decoding (1 reference
@@ -222,6 +242,7 @@ def measure_ndf(ndf, ctx, fid, recipe, stream, args, exact_ms):
     for name, measure, k, triples in (("pearson", ndf.NDF_MEASURE_PEARSON, 0, args.ndf_triples),
                                       ("mi", ndf.NDF_MEASURE_MI_KSG, K_NN, args.ndf_mi_triples)):
         cfg = ndf.ndf_train_cfg_default()
+        cfg.res[:] = [int(v) for v in args.ndf_res.split(",")]
         cfg.n_triples = int(triples)
         cfg.time_budget_s = float(args.ndf_seconds)
         t0 = time.perf_counter()
@@ -309,11 +330,15 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--batch", type=int, default=1, help="also time 64-reference Pearson GEMMs")
+    ap.add_argument("--ksg-batch", type=int, default=1, help="also time a 64-reference KSG launch")
+    ap.add_argument("--brute-steps", type=int, default=1, help="volumes timed with brute-force KSG")
     ap.add_argument("--ndf", type=int, default=1, help="also train and time the neural field")
     ap.add_argument("--ndf-seconds", type=float, default=25.0, help="training budget per network")
     ap.add_argument("--ndf-triples", type=int, default=1 << 26, help="Pearson training triples")
     ap.add_argument("--ndf-mi-triples", type=int, default=1 << 24, help="KSG-MI training triples")
     ap.add_argument("--ndf-mi-err-refs", type=int, default=4, help="exact KSG volumes for MI error")
+    ap.add_argument("--ndf-res", default="32,64,128,256",
+                    help="dense grid points per axis of the 4 levels (smaller only for profiling)")
     ap.add_argument("--workload", choices=["csens", "csens-slab", "tiny"], default="csens",
                     help="csens: 250x352x20, M=1000 (the benchmark); csens-slab: one vertical "
                          "level of it (profiling); tiny: 16x16x4, M=100 (checks)")
@@ -393,6 +418,28 @@ def main():
     volumes = args.steps * world
     ms_per_volume = total_ms / volumes
 
+    # ---- distance evaluations the (pruned) KSG kernel performed for the timed references
+    ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_PRUNED, True)
+    for i in range(args.steps):
+        ndf.ndf_mi_ksg(ctx, fid, fid, refs[args.warmup + i], K_NN, out_mi)
+    ksg_evals = ndf.ndf_ksg_take_eval_count(ctx) / args.steps
+    ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_PRUNED, False)
+    # ---- the brute-force search (every member pair) on the same references
+    ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_BRUTE)
+    b0 = torch.cuda.Event(enable_timing=True)
+    b1 = torch.cuda.Event(enable_timing=True)
+    nb = max(1, min(args.brute_steps, args.steps))
+    ndf.ndf_mi_ksg(ctx, fid, fid, refs[args.warmup], K_NN, out_mi)  # warm-up
+    b0.record(stream)
+    for i in range(nb):
+        ndf.ndf_mi_ksg(ctx, fid, fid, refs[args.warmup + i], K_NN, out_mi)
+    b1.record(stream)
+    ndf.ndf_synchronize(ctx)
+    ksg_brute_ms = b0.elapsed_time(b1) / nb
+    ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_PRUNED)
+    # ---- batched KSG: 64 references in one launch (autotuned tile shape)
+    ksg_batch = measure_ksg_batch(ndf, ctx, fid, recipe, stream, args) if args.ksg_batch else None
+
     # ---- batched multi-reference Pearson (64 references per call) per precision
     batch = measure_pearson_batch(ndf, ctx, fid, field, recipe, stream, rank) if args.batch else None
 
@@ -423,8 +470,9 @@ def main():
     peaks = load_peaks()
     props = torch.cuda.get_device_properties(local_rank)
     sms = props.multi_processor_count
-    evals = float(N) * M * (M - 1)
+    evals = float(ksg_evals)  # distance evaluations the pruned kernel performed per volume
     achieved = evals / (ksg_ms * 1e-3) / 1e9  # Gdist/s
+    brute_evals = float(N) * M * (M - 1)
     # peak: 64 ALU-pipe lanes per SM per clock, 2 ALU instructions per evaluation
     # (the abs-max and the threshold compare), at the maximum SM clock
     peak = sms * 64 / 2 * peaks["sm_max_mhz"] * 1e6 / 1e9
@@ -447,9 +495,18 @@ def main():
             "mi_pairs_per_s": N / (ksg_ms * 1e-3),
             "pearson_hbm_gbs": pearson_gbs,
             "pearson_hbm_frac": pearson_gbs / peaks["hbm_gbs"],
-            "roofline": {"bound": "alu", "kernel": "ksg_volume_kernel", "achieved": achieved,
+            "roofline": {"bound": "alu", "kernel": "ksg_pruned_kernel<9>", "achieved": achieved,
                          "peak": peak, "unit": "Gdist/s", "frac": achieved / peak,
-                         "traffic": None, "peak_source": f"{peaks['source']} max SM clock"},
+                         "traffic": None, "peak_source": f"{peaks['source']} max SM clock",
+                         "evals_per_volume": evals},
+            "ksg_brute_ms": ksg_brute_ms,
+            "ksg_brute_roofline": {"bound": "alu", "kernel": "ksg_volume_kernel<9>",
+                                   "achieved": brute_evals / (ksg_brute_ms * 1e-3) / 1e9,
+                                   "peak": peak, "unit": "Gdist/s",
+                                   "frac": brute_evals / (ksg_brute_ms * 1e-3) / 1e9 / peak,
+                                   "evals_per_volume": brute_evals},
+            "ksg_pruned_speedup_vs_brute": ksg_brute_ms / ksg_ms,
+            "ksg_batch64": ksg_batch,
             "e2e": {"value": e2e_per_volume, "unit": "ms",
                     "h2d_bytes_per_step": int(field.nbytes),
                     "d2h_bytes_per_step": int(2 * N * 4)},

@@ -20,7 +20,7 @@
 //           the running top-(k+1) distances in registers tighten early and the
 //           insert branch is rare.  Insertion is a branch-free min/max network.
 //           Counts: binary search in the sorted x (shared by all pairs) and in the
-//           pair's y column sorted by a shared-memory bitonic sort; the search
+//           query column's sorted copy (sorted once per field); the search
 //           predicates are the same FP32 |difference| < eps tests, which are
 //           monotone in sorted order.  The digamma sum is FP64, block-reduced.
 #include <float.h>
@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(1024) ksg_stage_kernel(const float* __restrict
 
 struct KsgArgs {
     const float* field;  // query field [M][N]
+    const float* sorted; // the query field's columns sorted ascending [M][N]
     int M;
     int k;
     int n2;              // power of two >= M
@@ -94,7 +95,7 @@ struct KsgArgs {
 
 // shared-memory carve-up (bytes) for a given M and VT
 struct KsgSmem {
-    size_t xs, perm, ytile, pts, ys, red, total;
+    size_t xs, perm, ytile, ystile, pts, red, total;
     __host__ __device__ KsgSmem(int M, int n2, int VT) {
         size_t o = 0;
         red = o; o += 32 * sizeof(double);
@@ -102,10 +103,11 @@ struct KsgSmem {
         perm = o; o += sizeof(int) * (size_t)M;
         o = (o + 15) & ~size_t(15);
         ytile = o; o += sizeof(float) * (size_t)M * (size_t)VT;
+        ystile = o; o += sizeof(float) * (size_t)M * (size_t)VT;
         o = (o + 15) & ~size_t(15);
         pts = o; o += sizeof(float2) * (size_t)(padi(2 * M) + 4);
-        ys = o; o += sizeof(float) * (size_t)n2;
         total = o;
+        (void)n2;
     }
 };
 
@@ -121,7 +123,7 @@ __global__ void __launch_bounds__(kKsgMaxThreads) ksg_volume_kernel(KsgArgs A) {
     int* perm = reinterpret_cast<int*>(smem + L.perm);
     float* ytile = reinterpret_cast<float*>(smem + L.ytile);
     float2* pts = reinterpret_cast<float2*>(smem + L.pts);
-    float* ys = reinterpret_cast<float*>(smem + L.ys);
+    float* ystile = reinterpret_cast<float*>(smem + L.ystile);
 
     const int M = A.M, T = blockDim.x, tid = threadIdx.x;
     const int64_t N = A.N;
@@ -140,34 +142,18 @@ __global__ void __launch_bounds__(kKsgMaxThreads) ksg_volume_kernel(KsgArgs A) {
         for (int idx = tid; idx < M * A.VT; idx += T) {
             int m = idx / A.VT, p = idx - m * A.VT;
             ytile[p * M + m] = p < vcount ? __ldcs(A.field + (int64_t)m * N + vt0 + p) : 0.0f;
+            ystile[p * M + m] = p < vcount ? __ldcs(A.sorted + (int64_t)m * N + vt0 + p) : 0.0f;
         }
         for (int p = 0; p < vcount; ++p) {
             const float* ycol = ytile + p * M;
-            __syncthreads();  // ytile ready / previous pair done with pts and ys
+            const float* ys = ystile + p * M;  // the column, sorted (for n_y)
+            __syncthreads();  // tiles ready / previous pair done with pts
             for (int s = tid; s < M; s += T) {
                 float2 q = make_float2(xs[s], ycol[perm[s]]);
                 pts[padi(s)] = q;
                 pts[padi(s + M)] = q;
             }
-            for (int i = tid; i < A.n2; i += T) ys[i] = i < M ? ycol[i] : FLT_MAX;
             __syncthreads();
-
-            // ---- sort the pair's y column for the n_y searches
-            for (int kk = 2; kk <= A.n2; kk <<= 1) {
-                for (int j = kk >> 1; j > 0; j >>= 1) {
-                    for (int i = tid; i < A.n2; i += T) {
-                        int l = i ^ j;
-                        if (l > i) {
-                            float u = ys[i], w = ys[l];
-                            if ((u > w) == ((i & kk) == 0)) {
-                                ys[i] = w;
-                                ys[l] = u;
-                            }
-                        }
-                    }
-                    __syncthreads();
-                }
-            }
 
             double acc = 0.0;
             for (int base = 0; base < M; base += kKsgPts * T) {
@@ -270,6 +256,7 @@ cudaError_t launch_ksg(ndf_ctx* ctx, const Field& rf, const Field& qf, int64_t r
 
     KsgArgs A;
     A.field = qf.data;
+    A.sorted = qf.sorted;
     A.M = M;
     A.k = k;
     A.n2 = 1;

@@ -14,9 +14,10 @@
 // Scan lengths differ a lot between points (the sparse tails of the x
 // distribution scan far), so points are handed to threads dynamically from a
 // shared counter.  The marginal counts and the digamma sum run afterwards as a
-// separate, evenly split phase.  The query column's sorted copy (for n_y) is
-// built once per vertex and shared by the G references a CTA holds, so one
-// launch covers R references: work items are (reference group, vertex tile).
+// separate, evenly split phase.  The query column's sorted copy (for n_y) comes
+// from the field's sorted columns (sorted once per field); G references share
+// each loaded column tile, so one launch covers R references: work items are
+// (reference group, vertex tile).
 #include <float.h>
 #include <limits.h>
 
@@ -69,6 +70,7 @@ __global__ void __launch_bounds__(1024)
 
 struct KsgPArgs {
     const float* field;  // query field [M][N]
+    const float* sorted; // its columns sorted ascending [M][N]
     int M, k, n2, VT, G, R;
     int64_t N, v_begin, v_end;
     const float* xs_all; // [R][M] sorted reference values
@@ -84,7 +86,7 @@ struct KsgPArgs {
 };
 
 struct KsgPSmem {
-    size_t red, next, xsg, permg, ytile, ys, pts, eps, total;
+    size_t red, next, xsg, permg, ytile, ystile, pts, eps, total;
     __host__ __device__ KsgPSmem(int M, int n2, int VT, int G) {
         size_t o = 0;
         red = o; o += 33 * sizeof(double);
@@ -93,7 +95,8 @@ struct KsgPSmem {
         permg = o; o += sizeof(int) * (size_t)M * G;
         o = (o + 15) & ~size_t(15);
         ytile = o; o += sizeof(float) * (size_t)M * VT;
-        ys = o; o += sizeof(float) * (size_t)n2;
+        ystile = o; o += sizeof(float) * (size_t)M * VT;
+        (void)n2;
         o = (o + 15) & ~size_t(15);
         pts = o; o += sizeof(float2) * (size_t)M;
         eps = o; o += sizeof(float) * (size_t)M;
@@ -112,7 +115,7 @@ __global__ void __launch_bounds__(kKsgPThreads) ksg_pruned_kernel(KsgPArgs A) {
     float* xsg = reinterpret_cast<float*>(smem + L.xsg);
     int* permg = reinterpret_cast<int*>(smem + L.permg);
     float* ytile = reinterpret_cast<float*>(smem + L.ytile);
-    float* ys = reinterpret_cast<float*>(smem + L.ys);
+    float* ystile = reinterpret_cast<float*>(smem + L.ystile);
     float2* pts = reinterpret_cast<float2*>(smem + L.pts);
     float* eps = reinterpret_cast<float*>(smem + L.eps);
 
@@ -143,72 +146,68 @@ __global__ void __launch_bounds__(kKsgPThreads) ksg_pruned_kernel(KsgPArgs A) {
         for (int idx = tid; idx < M * A.VT; idx += T) {
             const int m = idx / A.VT, p = idx - m * A.VT;
             ytile[p * M + m] = p < vcount ? __ldcs(A.field + (int64_t)m * N + vt0 + p) : 0.0f;
+            ystile[p * M + m] = p < vcount ? __ldcs(A.sorted + (int64_t)m * N + vt0 + p) : 0.0f;
         }
         for (int p = 0; p < vcount; ++p) {
             const float* ycol = ytile + p * M;
             __syncthreads();
-            // ---- the pair's y column, sorted once for all references of the group
-            for (int i = tid; i < A.n2; i += T) ys[i] = i < M ? ycol[i] : FLT_MAX;
-            __syncthreads();
-            for (int kk = 2; kk <= A.n2; kk <<= 1) {
-                for (int j = kk >> 1; j > 0; j >>= 1) {
-                    for (int i = tid; i < A.n2; i += T) {
-                        const int l = i ^ j;
-                        if (l > i) {
-                            const float u = ys[i], w = ys[l];
-                            if ((u > w) == ((i & kk) == 0)) {
-                                ys[i] = w;
-                                ys[l] = u;
-                            }
-                        }
-                    }
-                    __syncthreads();
-                }
-            }
+            const float* ys = ystile + p * M;  // the column, sorted (for n_y)
             for (int g = 0; g < gcount; ++g) {
                 const float* xs = xsg + (size_t)g * M;
                 const int* perm = permg + (size_t)g * M;
                 for (int s = tid; s < M; s += T) pts[s] = make_float2(xs[s], ycol[perm[s]]);
                 if (tid == 0) *next = T;
                 __syncthreads();
-                // ---- phase 1: eps of every point, points handed out dynamically
-                int s = tid;
-                while (s < M) {
+                // ---- phase 1: eps of every point.  One flat loop: each pass either
+                // visits one candidate of the lane's point or, when both sides of
+                // that point have stopped, records eps and takes the next point from
+                // the shared counter, so lanes never wait for a warp-mate's long
+                // scan.  Points are handed out from both ends of the x order first
+                // (the sparse tails scan longest), the middle last.
+                {
+                    auto point_of = [M](int t) { return (t & 1) ? M - 1 - (t >> 1) : (t >> 1); };
+                    int t = tid;
+                    int s = t < M ? point_of(t) : M;
                     float a[K1];
-                    a[0] = 0.0f;  // the point itself
+                    float2 me = make_float2(0.0f, 0.0f);
+                    int jr = 0, jl = 0;
+                    bool on_r = false, on_l = false, tog = false;
+                    auto start = [&](int q) {
+                        a[0] = 0.0f;  // the point itself
 #pragma unroll
-                    for (int j = 1; j < K1; ++j) a[j] = FLT_MAX;
-                    const float2 me = pts[s];
-                    int jr = s + 1, jl = s - 1;
-                    bool on_r = jr < M, on_l = jl >= 0;
-                    while (on_r || on_l) {
-                        if (on_r) {
-                            const float2 c = pts[jr];
-                            const float gap = c.x - me.x;
+                        for (int j = 1; j < K1; ++j) a[j] = FLT_MAX;
+                        me = pts[q];
+                        jr = q + 1;
+                        jl = q - 1;
+                        on_r = jr < M;
+                        on_l = jl >= 0;
+                    };
+                    if (t < M) start(s);
+                    while (t < M) {
+                        if (on_r || on_l) {
+                            const bool right = on_r && (!on_l || tog);
+                            tog = !tog;
+                            const float2 c = pts[right ? jr : jl];
+                            const float gap = right ? c.x - me.x : me.x - c.x;
                             if (gap >= a[K1 - 1]) {
-                                on_r = false;
+                                if (right) on_r = false;
+                                else on_l = false;
                             } else {
                                 const float d = fmaxf(gap, fabsf(c.y - me.y));
                                 if (d < a[K1 - 1]) topk_insert<K1>(a, d);
                                 ++my_evals;
-                                on_r = ++jr < M;
+                                if (right) on_r = ++jr < M;
+                                else on_l = --jl >= 0;
                             }
-                        }
-                        if (on_l) {
-                            const float2 c = pts[jl];
-                            const float gap = me.x - c.x;
-                            if (gap >= a[K1 - 1]) {
-                                on_l = false;
-                            } else {
-                                const float d = fmaxf(gap, fabsf(c.y - me.y));
-                                if (d < a[K1 - 1]) topk_insert<K1>(a, d);
-                                ++my_evals;
-                                on_l = --jl >= 0;
+                        } else {
+                            eps[s] = a[K1 - 1];
+                            t = atomicAdd(next, 1);
+                            if (t < M) {
+                                s = point_of(t);
+                                start(s);
                             }
                         }
                     }
-                    eps[s] = a[K1 - 1];
-                    s = atomicAdd(next, 1);
                 }
                 __syncthreads();
                 // ---- phase 2: marginal counts and the digamma sum
@@ -281,6 +280,7 @@ cudaError_t launch_ksg_pruned(ndf_ctx* ctx, const Field& rf, const Field& qf, co
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     KsgPArgs A;
     A.field = qf.data;
+    A.sorted = qf.sorted;
     A.M = M;
     A.k = k;
     A.n2 = 1;
@@ -344,6 +344,8 @@ extern "C" ndf_status ndf_ksg_autotune(ndf_ctx* ctx, int ref_field, int query_fi
         return fail(ctx, NDF_ERR_ARG, "bad k or M");
     cudaSetDevice(ctx->device);
     if ((st = ensure_psi_table(ctx, rf->M + 1)) != NDF_OK) return st;
+    cudaError_t es = ensure_sorted_columns(ctx, ctx->fields[query_field]);
+    if (es != cudaSuccess) return cuda_fail(ctx, es, "sorted columns");
     // sample: 8 references spread over the grid, the first 32768 query vertices
     const int R = 8;
     const int64_t nv = qf->N < 32768 ? qf->N : 32768;

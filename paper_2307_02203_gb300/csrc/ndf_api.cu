@@ -24,12 +24,13 @@ cudaError_t DevBuf::reserve(size_t need) {
 }
 
 void Field::free_all() {
-    void* ps[] = {data, mean, inv_norm, z_tf32, z_hi, z_lo};
+    void* ps[] = {data, mean, inv_norm, z_tf32, z_hi, z_lo, sorted};
     for (void* q : ps)
         if (q) cudaFree(q);
     data = nullptr;
     mean = inv_norm = nullptr;
     z_tf32 = z_hi = z_lo = nullptr;
+    sorted = nullptr;
     live = false;
 }
 
@@ -384,6 +385,8 @@ ndf_status ndf_mi_ksg(ndf_ctx* ctx, int ref_field, int query_field, int64_t ref_
     if ((st = check_ksg_args(ctx, rf, k)) != NDF_OK) return st;
     cudaSetDevice(ctx->device);
     if ((st = ensure_psi_table(ctx, rf->M + 1)) != NDF_OK) return st;
+    cudaError_t es = ensure_sorted_columns(ctx, ctx->fields[query_field]);
+    if (es != cudaSuccess) return cuda_fail(ctx, es, "sorted columns");
     size_t bytes = sizeof(float) * (size_t)qf->N;
     void* dev_out;
     bool is_host;
@@ -405,6 +408,8 @@ ndf_status ndf_ksg_debug_pair(ndf_ctx* ctx, int ref_field, int query_field, int6
     if ((st = check_ksg_args(ctx, rf, k)) != NDF_OK) return st;
     cudaSetDevice(ctx->device);
     if ((st = ensure_psi_table(ctx, rf->M + 1)) != NDF_OK) return st;
+    cudaError_t es = ensure_sorted_columns(ctx, ctx->fields[query_field]);
+    if (es != cudaSuccess) return cuda_fail(ctx, es, "sorted columns");
     int64_t M = rf->M;
     // layout of the debug block: mi (double) | out (float) | eps[M] | nx[M] | ny[M]
     size_t need = 16 + sizeof(float) * (size_t)M * 3 + 64;
@@ -471,6 +476,8 @@ ndf_status ndf_mi_ksg_batch(ndf_ctx* ctx, int ref_field, int query_field, const 
     if ((st = check_ksg_args(ctx, rf, k)) != NDF_OK) return st;
     cudaSetDevice(ctx->device);
     if ((st = ensure_psi_table(ctx, rf->M + 1)) != NDF_OK) return st;
+    cudaError_t es = ensure_sorted_columns(ctx, ctx->fields[query_field]);
+    if (es != cudaSuccess) return cuda_fail(ctx, es, "sorted columns");
     const size_t bytes = sizeof(float) * (size_t)R * (size_t)qf->N;
     void* dev_out;
     bool is_host;

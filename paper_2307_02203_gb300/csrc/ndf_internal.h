@@ -33,6 +33,9 @@ struct Field {
     void* z_tf32 = nullptr;    // float [N][Kp], TF32-rounded
     void* z_hi = nullptr;      // bf16 [N][Kp]
     void* z_lo = nullptr;      // bf16 [N][Kp]
+    // every vertex column sorted ascending, member-major like `data` (built on
+    // the first KSG call that uses this field as the query field)
+    float* sorted = nullptr;   // [M][N]
     void free_all();
 };
 
@@ -92,6 +95,9 @@ cudaError_t launch_pearson(ndf_ctx* ctx, const Field& rf, const Field& qf, int64
 cudaError_t launch_ksg(ndf_ctx* ctx, const Field& rf, const Field& qf, int64_t ref_idx, int k,
                        int64_t v_begin, int64_t v_end, float* out, double* dbg_mi, float* dbg_eps,
                        int32_t* dbg_nx, int32_t* dbg_ny);
+
+// Builds Field::sorted (one sort per vertex column, kept with the field).
+cudaError_t ensure_sorted_columns(ndf_ctx* ctx, Field& f);
 
 cudaError_t launch_ksg_pruned(ndf_ctx* ctx, const Field& rf, const Field& qf, const int64_t* d_refs,
                               int R, int k, int64_t v_begin, int64_t v_end, float* out,

@@ -595,12 +595,16 @@ ndf_status ndf_train(ndf_ctx* ctx, int ref_field, int query_field, int measure, 
         ndf_model_free(m);
         return s;
     };
-    if (measure == NDF_MEASURE_MI_KSG && (st = ensure_psi_table(ctx, M + 1)) != NDF_OK) return bail(st);
+    if (measure == NDF_MEASURE_MI_KSG) {
+        if ((st = ensure_psi_table(ctx, M + 1)) != NDF_OK) return bail(st);
+        cudaError_t es = ensure_sorted_columns(ctx, ctx->fields[query_field]);
+        if (es != cudaSuccess) return bail(cuda_fail(ctx, es, "sorted columns"));
+    }
 
     // ---- training triples
     auto t0 = std::chrono::steady_clock::now();
     int32_t *vref = nullptr, *vq = nullptr;
-    float *tgt = nullptr, *block = nullptr, *gtgt = nullptr;
+    float *tgt = nullptr, *block = nullptr, *block_sorted = nullptr, *gtgt = nullptr;
     int64_t *dq = nullptr, *drefs = nullptr;
     cudaError_t e = cudaMalloc(&vref, (size_t)T * 4);
     if (e == cudaSuccess) e = cudaMalloc(&vq, (size_t)T * 4);
@@ -608,6 +612,8 @@ ndf_status ndf_train(ndf_ctx* ctx, int ref_field, int query_field, int measure, 
     if (e == cudaSuccess) e = cudaMalloc(&block, (size_t)M * Qg * 4);
     if (e == cudaSuccess) e = cudaMalloc(&dq, (size_t)Qg * 8);
     if (e == cudaSuccess) e = cudaMalloc(&gtgt, (size_t)Rg * Qg * 4);
+    if (e == cudaSuccess && measure == NDF_MEASURE_MI_KSG)
+        e = cudaMalloc(&block_sorted, (size_t)M * Qg * 4);
     if (e == cudaSuccess) e = cudaMalloc(&drefs, (size_t)Rg * 8);
     Field blk;
     blk.live = true;
@@ -617,12 +623,13 @@ ndf_status ndf_train(ndf_ctx* ctx, int ref_field, int query_field, int measure, 
     blk.X = Qg;
     blk.N = Qg;
     blk.data = block;
+    blk.sorted = block_sorted;  // gathered from the query field's sorted columns
     if (e == cudaSuccess && measure == NDF_MEASURE_PEARSON) {
         e = cudaMalloc(&blk.mean, (size_t)Qg * 8);
         if (e == cudaSuccess) e = cudaMalloc(&blk.inv_norm, (size_t)Qg * 8);
     }
     auto cleanup_data = [&]() {
-        void* ps[] = {vref, vq, tgt, block, dq, gtgt, drefs, blk.mean, blk.inv_norm};
+        void* ps[] = {vref, vq, tgt, block, block_sorted, dq, gtgt, drefs, blk.mean, blk.inv_norm};
         for (void* q : ps)
             if (q) cudaFree(q);
     };
@@ -644,6 +651,11 @@ ndf_status ndf_train(ndf_ctx* ctx, int ref_field, int query_field, int measure, 
         if (e != cudaSuccess) break;
         gather_columns_kernel<<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(qf->data, M, N, dq, Qg, block);
         ctx->launches++;
+        if (block_sorted) {
+            gather_columns_kernel<<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(
+                ctx->fields[query_field].sorted, M, N, dq, Qg, block_sorted);
+            ctx->launches++;
+        }
         if (measure == NDF_MEASURE_PEARSON) {
             e = cudaMemsetAsync(d_flag, 0, 4, ctx->stream);
             if (e == cudaSuccess) e = launch_field_stats(ctx, blk, d_flag);
