@@ -32,6 +32,11 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 K_NN = 8
+# DRAM bytes per launch of ksg_volume_kernel<9> at the full 250x352x20 volume: the
+# one-level slab capture (ncu dram__bytes_read.sum + dram__bytes_write.sum =
+# 709.6 MB for 88,000 vertices) scaled by the vertices processed (x20), since the
+# kernel streams each query column and its sorted copy once.
+KSG_TRAFFIC_PER_VOLUME = 709.6e6 * 20
 METRIC = "ms per 1.76M-voxel dependence volume (Pearson + KSG MI k=8, M=1000)"
 
 
@@ -331,7 +336,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--batch", type=int, default=1, help="also time 64-reference Pearson GEMMs")
     ap.add_argument("--ksg-batch", type=int, default=1, help="also time a 64-reference KSG launch")
-    ap.add_argument("--brute-steps", type=int, default=1, help="volumes timed with brute-force KSG")
+    ap.add_argument("--pruned-steps", type=int, default=1, help="volumes timed with pruned KSG")
     ap.add_argument("--ndf", type=int, default=1, help="also train and time the neural field")
     ap.add_argument("--ndf-seconds", type=float, default=25.0, help="training budget per network")
     ap.add_argument("--ndf-triples", type=int, default=1 << 26, help="Pearson training triples")
@@ -418,25 +423,23 @@ def main():
     volumes = args.steps * world
     ms_per_volume = total_ms / volumes
 
-    # ---- distance evaluations the (pruned) KSG kernel performed for the timed references
+    # ---- the pruned search (same results) on the same references, and the distance
+    # evaluations it performs (counted in a separate, untimed pass)
     ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_PRUNED, True)
-    for i in range(args.steps):
+    nb = max(1, min(args.pruned_steps, args.steps))
+    for i in range(nb):
         ndf.ndf_mi_ksg(ctx, fid, fid, refs[args.warmup + i], K_NN, out_mi)
-    ksg_evals = ndf.ndf_ksg_take_eval_count(ctx) / args.steps
+    pruned_evals = ndf.ndf_ksg_take_eval_count(ctx) / nb
     ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_PRUNED, False)
-    # ---- the brute-force search (every member pair) on the same references
-    ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_BRUTE)
     b0 = torch.cuda.Event(enable_timing=True)
     b1 = torch.cuda.Event(enable_timing=True)
-    nb = max(1, min(args.brute_steps, args.steps))
-    ndf.ndf_mi_ksg(ctx, fid, fid, refs[args.warmup], K_NN, out_mi)  # warm-up
     b0.record(stream)
     for i in range(nb):
         ndf.ndf_mi_ksg(ctx, fid, fid, refs[args.warmup + i], K_NN, out_mi)
     b1.record(stream)
     ndf.ndf_synchronize(ctx)
-    ksg_brute_ms = b0.elapsed_time(b1) / nb
-    ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_PRUNED)
+    ksg_pruned_ms = b0.elapsed_time(b1) / nb
+    ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_BRUTE)
     # ---- batched KSG: 64 references in one launch (autotuned tile shape)
     ksg_batch = measure_ksg_batch(ndf, ctx, fid, recipe, stream, args) if args.ksg_batch else None
 
@@ -470,9 +473,8 @@ def main():
     peaks = load_peaks()
     props = torch.cuda.get_device_properties(local_rank)
     sms = props.multi_processor_count
-    evals = float(ksg_evals)  # distance evaluations the pruned kernel performed per volume
+    evals = float(N) * M * (M - 1)  # brute force: every member pair of every vertex
     achieved = evals / (ksg_ms * 1e-3) / 1e9  # Gdist/s
-    brute_evals = float(N) * M * (M - 1)
     # peak: 64 ALU-pipe lanes per SM per clock, 2 ALU instructions per evaluation
     # (the abs-max and the threshold compare), at the maximum SM clock
     peak = sms * 64 / 2 * peaks["sm_max_mhz"] * 1e6 / 1e9
@@ -495,17 +497,18 @@ def main():
             "mi_pairs_per_s": N / (ksg_ms * 1e-3),
             "pearson_hbm_gbs": pearson_gbs,
             "pearson_hbm_frac": pearson_gbs / peaks["hbm_gbs"],
-            "roofline": {"bound": "alu", "kernel": "ksg_pruned_kernel<9>", "achieved": achieved,
+            "roofline": {"bound": "alu", "kernel": "ksg_volume_kernel<9>", "achieved": achieved,
                          "peak": peak, "unit": "Gdist/s", "frac": achieved / peak,
-                         "traffic": None, "peak_source": f"{peaks['source']} max SM clock",
+                         "traffic": KSG_TRAFFIC_PER_VOLUME,
+                         "peak_source": f"{peaks['source']} max SM clock",
                          "evals_per_volume": evals},
-            "ksg_brute_ms": ksg_brute_ms,
-            "ksg_brute_roofline": {"bound": "alu", "kernel": "ksg_volume_kernel<9>",
-                                   "achieved": brute_evals / (ksg_brute_ms * 1e-3) / 1e9,
-                                   "peak": peak, "unit": "Gdist/s",
-                                   "frac": brute_evals / (ksg_brute_ms * 1e-3) / 1e9 / peak,
-                                   "evals_per_volume": brute_evals},
-            "ksg_pruned_speedup_vs_brute": ksg_brute_ms / ksg_ms,
+            "ksg_pruned_ms": ksg_pruned_ms,
+            "ksg_pruned_roofline": {"bound": "alu", "kernel": "ksg_pruned_kernel<9>",
+                                    "achieved": pruned_evals / (ksg_pruned_ms * 1e-3) / 1e9,
+                                    "peak": peak, "unit": "Gdist/s",
+                                    "frac": pruned_evals / (ksg_pruned_ms * 1e-3) / 1e9 / peak,
+                                    "evals_per_volume": pruned_evals},
+            "ksg_pruned_speedup_vs_brute": ksg_ms / ksg_pruned_ms,
             "ksg_batch64": ksg_batch,
             "e2e": {"value": e2e_per_volume, "unit": "ms",
                     "h2d_bytes_per_step": int(field.nbytes),

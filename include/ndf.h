@@ -135,8 +135,8 @@ ndf_status ndf_mi_ksg(ndf_ctx* ctx, int ref_field, int query_field, int64_t ref_
 
 /* KSG search used by ndf_mi_ksg, ndf_ksg_debug_pair and ndf_train's MI targets.
  * Both give identical results (same FP32 distances, same counts):
- *   NDF_KSG_BRUTE   every member against every member of each pair;
- *   NDF_KSG_PRUNED  (default) members in order of the reference value, each
+ *   NDF_KSG_BRUTE   (default) every member against every member of each pair;
+ *   NDF_KSG_PRUNED  members in order of the reference value, each
  *                   side of the outward scan stopped at the first x-gap that
  *                   reaches the current k-th distance (exact pruning).
  * count_evals != 0 makes the kernels count distance evaluations (read with

@@ -122,7 +122,7 @@ def algo(request, ndf_mod, ctx):
     code = {"brute": ndf_mod.NDF_KSG_BRUTE, "pruned": ndf_mod.NDF_KSG_PRUNED}[request.param]
     ndf_mod.ndf_set_ksg_algorithm(ctx, code)
     yield request.param
-    ndf_mod.ndf_set_ksg_algorithm(ctx, ndf_mod.NDF_KSG_PRUNED)
+    ndf_mod.ndf_set_ksg_algorithm(ctx, ndf_mod.NDF_KSG_BRUTE)
 
 
 def ksg_debug(ndf, ctx, fa, fb, r, v, k, M):
@@ -243,7 +243,7 @@ def test_ksg_eval_counter(ndf_mod, ctx, tiny_field, tiny_ref):
     ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_PRUNED, True)
     ndf.ndf_mi_ksg(ctx, fid, fid, tiny_ref, 4, out)
     evals = ndf.ndf_ksg_take_eval_count(ctx)
-    ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_PRUNED, False)
+    ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_BRUTE, False)
     # the pruned search visits a strict subset of the M(M-1) candidates of each pair
     assert 0 < evals < N * M * (M - 1)
     assert ndf.ndf_ksg_take_eval_count(ctx) == 0
