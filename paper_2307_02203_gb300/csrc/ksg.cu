@@ -25,6 +25,7 @@
 //           monotone in sorted order.  The digamma sum is FP64, block-reduced.
 #include <float.h>
 #include <limits.h>
+#include <math.h>
 
 #include "device_common.cuh"
 #include "ksg_common.cuh"
@@ -72,6 +73,17 @@ __global__ void __launch_bounds__(1024) ksg_stage_kernel(const float* __restrict
         xs_out[i] = key[i];
         perm_out[i] = val[i];
     }
+}
+
+__device__ __forceinline__ unsigned long long pack_f2(float2 v) {
+    return ((unsigned long long)__float_as_uint(v.y) << 32) | __float_as_uint(v.x);
+}
+
+// (a.x - b.x, a.y - b.y), each rounded to nearest like a scalar FP32 subtract
+__device__ __forceinline__ float2 sub_f32x2(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return make_float2(__uint_as_float((unsigned)d), __uint_as_float((unsigned)(d >> 32)));
 }
 
 struct KsgArgs {
@@ -160,26 +172,34 @@ __global__ void __launch_bounds__(kKsgMaxThreads) ksg_volume_kernel(KsgArgs A) {
                 const int b0 = base + kKsgPts * tid;
                 const int n_own = M - b0 >= kKsgPts ? kKsgPts : (M - b0 > 0 ? M - b0 : 0);
                 const int R = (M - n_own + 1) >> 1, Lc = (M - n_own) >> 1;
-                // ---- joint k-NN: top-(k+1) distances (self included) per owned point
+                // ---- joint k-NN: top-(k+1) distances (self included) per owned point.
+                // Per candidate: one packed FP32 subtract gives (dx, dy) for a point,
+                // d = max(|dx|, |dy|) is one min/max, and the threshold test moves to
+                // the FMA pipe as u = d - t (exactly negative iff d < t: no flush to
+                // zero); the 4 tests merge with a min tree into one compare.
+                unsigned long long P[kKsgPts];
                 float px[kKsgPts], py[kKsgPts];
                 float a[kKsgPts][K1];
 #pragma unroll
                 for (int q = 0; q < kKsgPts; ++q) {
-                    float2 pq = q < n_own ? pts[padi(b0 + q)] : make_float2(FLT_MAX, FLT_MAX);
+                    // a missing point sits at +inf: its distances are +inf, never inserted
+                    float2 pq = q < n_own ? pts[padi(b0 + q)] : make_float2(INFINITY, INFINITY);
                     px[q] = pq.x;
                     py[q] = pq.y;
+                    P[q] = pack_f2(pq);
 #pragma unroll
                     for (int j = 0; j < K1; ++j) a[q][j] = FLT_MAX;
                 }
                 auto visit = [&](float2 c) {
-                    float d[kKsgPts];
-                    bool any = false;
+                    const unsigned long long C = pack_f2(c);
+                    float d[kKsgPts], u[kKsgPts];
 #pragma unroll
                     for (int q = 0; q < kKsgPts; ++q) {
-                        d[q] = fmaxf(fabsf(px[q] - c.x), fabsf(py[q] - c.y));
-                        any |= d[q] < a[q][K1 - 1];
+                        const float2 dd = sub_f32x2(P[q], C);
+                        d[q] = fmaxf(fabsf(dd.x), fabsf(dd.y));
+                        u[q] = d[q] - a[q][K1 - 1];
                     }
-                    if (any) {
+                    if (fminf(fminf(u[0], u[1]), fminf(u[2], u[3])) < 0.0f) {
 #pragma unroll
                         for (int q = 0; q < kKsgPts; ++q) topk_insert<K1>(a[q], d[q]);
                     }

@@ -520,20 +520,43 @@ __global__ void __launch_bounds__(256)
 }
 
 // ---------------------------------------------------------------- Adam
+// Adam over the flat FP32 master: four parameters per thread and iteration with
+// 16-byte accesses (the parameter count is padded to a multiple of 4 in every
+// buffer); the grid part also refreshes its BF16 copy.
+__device__ __forceinline__ float adam_one(float& p, float g, float& m, float& v, float lr,
+                                          float beta1, float beta2, float eps, float c1, float c2) {
+    m = beta1 * m + (1.0f - beta1) * g;
+    v = beta2 * v + (1.0f - beta2) * g * g;
+    p = p - lr * (m / c1) / (sqrtf(v / c2) + eps);
+    return p;
+}
+
 __global__ void __launch_bounds__(256)
-    adam_kernel(float* __restrict__ p, float* __restrict__ gr, float* __restrict__ m,
+    adam_kernel(float* __restrict__ p, const float* __restrict__ gr, float* __restrict__ m,
                 float* __restrict__ v, int64_t n, int64_t n_grid, __nv_bfloat16* __restrict__ grid_bf,
                 float lr, float beta1, float beta2, float eps, float c1, float c2) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+    const int64_t n4 = (n + 3) >> 2;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const float g = gr[i];
-        const float mi = beta1 * m[i] + (1.0f - beta1) * g;
-        const float vi = beta2 * v[i] + (1.0f - beta2) * g * g;
-        m[i] = mi;
-        v[i] = vi;
-        const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-        p[i] = pi;
-        if (i < n_grid) grid_bf[i] = __float2bfloat16_rn(pi);
+        float4 P = reinterpret_cast<float4*>(p)[i];
+        const float4 G = __ldcs(reinterpret_cast<const float4*>(gr) + i);
+        float4 Mv = reinterpret_cast<float4*>(m)[i];
+        float4 V = reinterpret_cast<float4*>(v)[i];
+        adam_one(P.x, G.x, Mv.x, V.x, lr, beta1, beta2, eps, c1, c2);
+        adam_one(P.y, G.y, Mv.y, V.y, lr, beta1, beta2, eps, c1, c2);
+        adam_one(P.z, G.z, Mv.z, V.z, lr, beta1, beta2, eps, c1, c2);
+        adam_one(P.w, G.w, Mv.w, V.w, lr, beta1, beta2, eps, c1, c2);
+        reinterpret_cast<float4*>(p)[i] = P;
+        reinterpret_cast<float4*>(m)[i] = Mv;
+        reinterpret_cast<float4*>(v)[i] = V;
+        const int64_t e = i << 2;
+        if (e + 3 < n_grid) {  // n_grid is a multiple of 16
+            __nv_bfloat162 lo = __floats2bfloat162_rn(P.x, P.y), hi = __floats2bfloat162_rn(P.z, P.w);
+            uint2 w;
+            w.x = *reinterpret_cast<uint32_t*>(&lo);
+            w.y = *reinterpret_cast<uint32_t*>(&hi);
+            reinterpret_cast<uint2*>(grid_bf)[i] = w;
+        }
     }
 }
 
@@ -632,7 +655,7 @@ ndf_status model_alloc(ndf_ctx* ctx, const int res[kLevels], int measure, int64_
     m->X = X;
     m->Y = Y;
     m->Z = Z;
-    const size_t n = (size_t)m->L.total;
+    const size_t n = ((size_t)m->L.total + 3) & ~size_t(3);  // float4 Adam: pad to 4
     cudaError_t e = cudaMalloc(&m->params, n * 4);
     if (e == cudaSuccess) e = cudaMalloc(&m->grad, n * 4);
     if (e == cudaSuccess) e = cudaMalloc(&m->m, n * 4);
@@ -640,6 +663,7 @@ ndf_status model_alloc(ndf_ctx* ctx, const int res[kLevels], int measure, int64_
     if (e == cudaSuccess) e = cudaMalloc(&m->grid_bf, (size_t)m->L.n_grid * 2);
     if (e == cudaSuccess) e = cudaMalloc(&m->wbf, (size_t)3 * kHid * kHid * 2);
     if (e == cudaSuccess) e = cudaMalloc(&m->wtbf, (size_t)3 * kHid * kHid * 2);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->params, 0, n * 4, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(m->grad, 0, n * 4, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(m->m, 0, n * 4, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(m->v, 0, n * 4, ctx->stream);
@@ -717,7 +741,7 @@ cudaError_t model_step(ndf_model* m, const float* pr, const float* pq, const flo
     NetWork& w = m->work;
     // gradients start from zero every step; the loss sum in w.loss accumulates
     // across steps (callers zero it)
-    cudaError_t e = cudaMemsetAsync(m->grad, 0, (size_t)m->L.total * 4, s);
+    cudaError_t e = cudaMemsetAsync(m->grad, 0, (((size_t)m->L.total + 3) & ~size_t(3)) * 4, s);
     if (e != cudaSuccess) return e;
     const GridDev G = grid_dev(m);
     encode_merge_fwd_kernel<<<(unsigned)((B * kLevels + 255) / 256), 256, 0, s>>>(G, pr, pq, B, w.fr,

@@ -93,5 +93,7 @@ cudaError_t model_forward(ndf_model* m, const float* pr, const float* pq, int64_
 
 // Volume decoding for R references (vertex ids on the device): out[R][N].
 cudaError_t model_infer(ndf_model* m, const int64_t* d_refs, int R, float* out);
+// tcgen05 decoding kernel (needs m->w1f / m->b1f folded for the R references)
+cudaError_t launch_infer_tc(ndf_model* m, int R, float* out);
 
 }  // namespace ndf

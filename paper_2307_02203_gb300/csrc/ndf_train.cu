@@ -14,7 +14,8 @@
 // Decoding: the reference half of the merged input is folded into the first
 // layer once per reference,
 //   W1 [f_r*f_q ; f_r+f_q] + b1 = (W1a diag(f_r) + W1b) f_q + (W1b f_r + b1),
-// so each query vertex needs only its own encoding and a 64-input first layer.
+// so each query vertex needs only its own encoding and a 64-input first layer
+// (the tensor-core decoding kernel is in ndf_decode_tc.cu).
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -78,7 +79,6 @@ __global__ void make_batch_kernel(const int32_t* __restrict__ vref, const int32_
 }
 
 // ---------------------------------------------------------------- decoding (Sec. 5)
-constexpr int kFoldStride = kLF + 8;  // padded bf16 row stride of the folded first layer
 
 struct GridArgs {
     const __nv_bfloat16* grid;
@@ -165,156 +165,6 @@ __global__ void __launch_bounds__(128)
     b1f[(int64_t)r * kHid + o] = b;
 }
 
-struct InferArgs {
-    GridArgs G;
-    const __nv_bfloat16* w1f;  // [R][128][64]
-    const float* b1f;          // [R][128]
-    const __nv_bfloat16* w23;  // W2, W3 bf16 [2][128][128]
-    const float* params;
-    int64_t offb2, offb3, offw4, offb4;
-    int64_t N, X, Y, Z;
-    int measure;
-    float* out;                // [R][N]
-};
-
-__device__ __forceinline__ void mma16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0,
-                                         uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-constexpr int kInferWarps = 8;
-constexpr size_t kInferSmem = (size_t)kHid * kFoldStride * 2 + (size_t)2 * kHid * kWStride * 2 +
-                              (size_t)kInferWarps * 16 * kFoldStride * 2;
-
-// grid (CTAs per reference, R); each warp decodes 16 query vertices at a time
-__global__ void __launch_bounds__(256) infer_volume_kernel(InferArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __nv_bfloat16* sW1 = reinterpret_cast<__nv_bfloat16*>(smem);          // [128][72]
-    __nv_bfloat16* sW23 = sW1 + kHid * kFoldStride;                          // [2][128][136]
-    __nv_bfloat16* sEnc = sW23 + 2 * kHid * kWStride;                        // [warps][16][72]
-    const int r = blockIdx.y;
-    const __nv_bfloat16* w1 = a.w1f + (int64_t)r * kHid * kLF;
-    for (int i = threadIdx.x; i < kHid * (kLF / 8); i += blockDim.x) {
-        const int row = i / (kLF / 8), c8 = i % (kLF / 8);
-        *reinterpret_cast<uint4*>(sW1 + row * kFoldStride + c8 * 8) =
-            reinterpret_cast<const uint4*>(w1 + row * kLF)[c8];
-    }
-    for (int i = threadIdx.x; i < 2 * kHid * (kHid / 8); i += blockDim.x) {
-        const int mat = i / (kHid * kHid / 8), rem = i % (kHid * kHid / 8);
-        const int row = rem / (kHid / 8), c8 = rem % (kHid / 8);
-        *reinterpret_cast<uint4*>(sW23 + (size_t)mat * kHid * kWStride + row * kWStride + c8 * 8) =
-            reinterpret_cast<const uint4*>(a.w23 + (size_t)mat * kHid * kHid)[row * (kHid / 8) + c8];
-    }
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    __nv_bfloat16* enc = sEnc + warp * 16 * kFoldStride;
-    const float* b1 = a.b1f + (int64_t)r * kHid;
-    const float* b2 = a.params + a.offb2;
-    const float* b3 = a.params + a.offb3;
-    const float* w4 = a.params + a.offw4;
-    const float b4 = a.params[a.offb4];
-    float* out = a.out + (int64_t)r * a.N;
-    const int64_t tiles = (a.N + 15) / 16;
-    for (int64_t tile = (int64_t)blockIdx.x * kInferWarps + warp; tile < tiles;
-         tile += (int64_t)gridDim.x * kInferWarps) {
-        const int64_t v0 = tile * 16;
-        // encode 16 vertices x 4 levels (two tasks per lane) into the warp's tile
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int task = lane + 32 * h, row = task >> 2, l = task & 3;
-            const int64_t v = v0 + row;
-            float f[kFeat];
-            if (v < a.N) {
-                float p[3];
-                vertex_pos(v, a.X, a.Y, a.Z, p);
-                encode_level_any(a.G, l, p, f);
-            } else {
-#pragma unroll
-                for (int q = 0; q < kFeat; ++q) f[q] = 0.0f;
-            }
-            uint4* d = reinterpret_cast<uint4*>(enc + row * kFoldStride + l * kFeat);
-            d[0] = make_uint4(f2bf2(f[0], f[1]), f2bf2(f[2], f[3]), f2bf2(f[4], f[5]), f2bf2(f[6], f[7]));
-            d[1] = make_uint4(f2bf2(f[8], f[9]), f2bf2(f[10], f[11]), f2bf2(f[12], f[13]), f2bf2(f[14], f[15]));
-        }
-        __syncwarp();
-        uint32_t A[8][4];
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-            const int c = 16 * kk + 2 * t;
-            A[kk][0] = *reinterpret_cast<const uint32_t*>(enc + g * kFoldStride + c);
-            A[kk][1] = *reinterpret_cast<const uint32_t*>(enc + (g + 8) * kFoldStride + c);
-            A[kk][2] = *reinterpret_cast<const uint32_t*>(enc + g * kFoldStride + c + 8);
-            A[kk][3] = *reinterpret_cast<const uint32_t*>(enc + (g + 8) * kFoldStride + c + 8);
-        }
-        __syncwarp();
-        float c[16][4];
-        // layer 1 (folded, K = 64)
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const float x0 = b1[8 * j + 2 * t], x1 = b1[8 * j + 2 * t + 1];
-            c[j][0] = x0; c[j][1] = x1; c[j][2] = x0; c[j][3] = x1;
-        }
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const __nv_bfloat16* row = sW1 + (8 * j + g) * kFoldStride + 16 * kk + 2 * t;
-                mma16816(c[j], A[kk], *reinterpret_cast<const uint32_t*>(row),
-                         *reinterpret_cast<const uint32_t*>(row + 8));
-            }
-        // layers 2 and 3
-#pragma unroll
-        for (int l = 0; l < 2; ++l) {
-#pragma unroll
-            for (int kk = 0; kk < 8; ++kk) {
-                A[kk][0] = f2bf2(fmaxf(c[2 * kk][0], 0.f), fmaxf(c[2 * kk][1], 0.f));
-                A[kk][1] = f2bf2(fmaxf(c[2 * kk][2], 0.f), fmaxf(c[2 * kk][3], 0.f));
-                A[kk][2] = f2bf2(fmaxf(c[2 * kk + 1][0], 0.f), fmaxf(c[2 * kk + 1][1], 0.f));
-                A[kk][3] = f2bf2(fmaxf(c[2 * kk + 1][2], 0.f), fmaxf(c[2 * kk + 1][3], 0.f));
-            }
-            const float* bias = l == 0 ? b2 : b3;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const float x0 = bias[8 * j + 2 * t], x1 = bias[8 * j + 2 * t + 1];
-                c[j][0] = x0; c[j][1] = x1; c[j][2] = x0; c[j][3] = x1;
-            }
-            const __nv_bfloat16* W = sW23 + (size_t)l * kHid * kWStride;
-#pragma unroll
-            for (int kk = 0; kk < 8; ++kk)
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const __nv_bfloat16* row = W + (8 * j + g) * kWStride + 16 * kk + 2 * t;
-                    mma16816(c[j], A[kk], *reinterpret_cast<const uint32_t*>(row),
-                             *reinterpret_cast<const uint32_t*>(row + 8));
-                }
-        }
-        // output: o = w4 . relu(h3) (as BF16) + b4
-        float s0 = 0.0f, s1 = 0.0f;
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int col = 8 * j + 2 * t;
-            const float2 ha = bf2f2(f2bf2(fmaxf(c[j][0], 0.f), fmaxf(c[j][1], 0.f)));
-            const float2 hb = bf2f2(f2bf2(fmaxf(c[j][2], 0.f), fmaxf(c[j][3], 0.f)));
-            s0 = fmaf(w4[col], ha.x, fmaf(w4[col + 1], ha.y, s0));
-            s1 = fmaf(w4[col], hb.x, fmaf(w4[col + 1], hb.y, s1));
-        }
-        s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
-        s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
-        s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
-        s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
-        if (t == 0) {
-            const int64_t va = v0 + g, vb = v0 + g + 8;
-            const float oa = s0 + b4, ob = s1 + b4;
-            if (va < a.N) out[va] = a.measure == 0 ? tanhf(oa) : (oa > 20.f ? oa : log1pf(expf(oa)));
-            if (vb < a.N) out[vb] = a.measure == 0 ? tanhf(ob) : (ob > 20.f ? ob : log1pf(expf(ob)));
-        }
-    }
-}
-
 cudaError_t model_infer(ndf_model* m, const int64_t* d_refs, int R, float* out) {
     ndf_ctx* ctx = m->ctx;
     if (m->infer_cap < R) {
@@ -327,9 +177,6 @@ cudaError_t model_infer(ndf_model* m, const int64_t* d_refs, int R, float* out) 
         if (e == cudaSuccess) e = cudaMalloc(&m->b1f, (size_t)R * kHid * 4);
         if (e != cudaSuccess) return e;
         m->infer_cap = R;
-        e = cudaFuncSetAttribute(infer_volume_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kInferSmem);
-        if (e != cudaSuccess) return e;
     }
     GridArgs G;
     G.grid = m->grid_bf;
@@ -339,30 +186,10 @@ cudaError_t model_infer(ndf_model* m, const int64_t* d_refs, int R, float* out) 
     }
     infer_fold_kernel<<<R, kHid, 0, ctx->stream>>>(G, m->params, m->L.W1, m->L.b1, d_refs, m->X,
                                                    m->Y, m->Z, m->w1f, m->b1f);
-    InferArgs a;
-    a.G = G;
-    a.w1f = m->w1f;
-    a.b1f = m->b1f;
-    a.w23 = m->wbf + (size_t)kHid * kHid;  // W2, W3
-    a.params = m->params;
-    a.offb2 = m->L.b2;
-    a.offb3 = m->L.b3;
-    a.offw4 = m->L.w4;
-    a.offb4 = m->L.b4;
-    a.N = m->X * m->Y * m->Z;
-    a.X = m->X;
-    a.Y = m->Y;
-    a.Z = m->Z;
-    a.measure = m->measure;
-    a.out = out;
-    int per_ref = (int)((ctx->sm_count * 2 + R - 1) / R);
-    const int64_t tiles = (a.N + 15) / 16;
-    const int64_t need = (tiles + kInferWarps - 1) / kInferWarps;
-    if (per_ref > need) per_ref = (int)need;
-    if (per_ref < 1) per_ref = 1;
-    infer_volume_kernel<<<dim3(per_ref, R), 256, kInferSmem, ctx->stream>>>(a);
-    ctx->launches += 2;
-    return cudaGetLastError();
+    ctx->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_infer_tc(m, R, out);
 }
 
 }  // namespace ndf
