@@ -32,11 +32,12 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 K_NN = 8
-# DRAM bytes per launch of ksg_volume_kernel<9> at the full 250x352x20 volume: the
-# one-level slab capture (ncu dram__bytes_read.sum + dram__bytes_write.sum =
-# 709.6 MB for 88,000 vertices) scaled by the vertices processed (x20), since the
-# kernel streams each query column and its sorted copy once.
-KSG_TRAFFIC_PER_VOLUME = 709.6e6 * 20
+# DRAM bytes per launch of the KSG kernels at the full 250x352x20 volume, from a
+# one-level slab capture (ncu dram__bytes_read.sum + dram__bytes_write.sum for
+# 88,000 vertices) scaled by the vertices processed (x20): the kernels stream each
+# query column and its sorted copy once.  None until captured for the current code.
+KSG_PRUNED_TRAFFIC_PER_VOLUME = None
+KSG_BRUTE_TRAFFIC_PER_VOLUME = None
 METRIC = "ms per 1.76M-voxel dependence volume (Pearson + KSG MI k=8, M=1000)"
 
 
@@ -213,12 +214,12 @@ def measure_pearson_batch(ndf, ctx, fid, field, recipe, stream, rank, R=64, reps
     return res
 
 
-def measure_ksg_batch(ndf, ctx, fid, recipe, stream, args, R=64):
-    """R KSG volumes in one persistent launch after the tile autotuner."""
+def measure_ksg_batch(ndf, ctx, fid, recipe, stream, args, R=16):
+    """R KSG volumes in one persistent launch (pruned search: one work counter over
+    all (reference, vertex) pairs)."""
     import torch
 
     N = recipe.N
-    g, t = ndf.ndf_ksg_autotune(ctx, fid, fid, K_NN)
     rng = np.random.default_rng(555)
     refs = [int(r) for r in rng.integers(0, N, size=R)]
     out = torch.empty((R, N), dtype=torch.float32, device="cuda")
@@ -229,8 +230,7 @@ def measure_ksg_batch(ndf, ctx, fid, recipe, stream, args, R=64):
     e1.record(stream)
     ndf.ndf_synchronize(ctx)
     ms = e0.elapsed_time(e1)
-    return {"refs": R, "ms": ms, "ms_per_volume": ms / R, "mi_pairs_per_s": R * N / (ms * 1e-3),
-            "refs_per_cta": g, "vertices_per_tile": t}
+    return {"refs": R, "ms": ms, "ms_per_volume": ms / R, "mi_pairs_per_s": R * N / (ms * 1e-3)}
 
 
 def measure_ndf(ndf, ctx, fid, recipe, stream, args, exact_ms):
@@ -335,8 +335,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--batch", type=int, default=1, help="also time 64-reference Pearson GEMMs")
-    ap.add_argument("--ksg-batch", type=int, default=1, help="also time a 64-reference KSG launch")
-    ap.add_argument("--pruned-steps", type=int, default=1, help="volumes timed with pruned KSG")
+    ap.add_argument("--ksg-batch", type=int, default=1, help="also time a 16-reference KSG launch")
+    ap.add_argument("--brute-steps", type=int, default=1,
+                    help="volumes timed with the brute-force KSG search (same results)")
     ap.add_argument("--ndf", type=int, default=1, help="also train and time the neural field")
     ap.add_argument("--ndf-seconds", type=float, default=25.0, help="training budget per network")
     ap.add_argument("--ndf-triples", type=int, default=1 << 26, help="Pearson training triples")
@@ -423,14 +424,14 @@ def main():
     volumes = args.steps * world
     ms_per_volume = total_ms / volumes
 
-    # ---- the pruned search (same results) on the same references, and the distance
-    # evaluations it performs (counted in a separate, untimed pass)
+    # ---- distance evaluations of the pruned search on the same references (counted
+    # in a separate, untimed pass), and the brute-force search timed beside it
+    nb = max(1, min(args.brute_steps, args.steps))
     ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_PRUNED, True)
-    nb = max(1, min(args.pruned_steps, args.steps))
     for i in range(nb):
         ndf.ndf_mi_ksg(ctx, fid, fid, refs[args.warmup + i], K_NN, out_mi)
     pruned_evals = ndf.ndf_ksg_take_eval_count(ctx) / nb
-    ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_PRUNED, False)
+    ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_BRUTE, False)
     b0 = torch.cuda.Event(enable_timing=True)
     b1 = torch.cuda.Event(enable_timing=True)
     b0.record(stream)
@@ -438,9 +439,9 @@ def main():
         ndf.ndf_mi_ksg(ctx, fid, fid, refs[args.warmup + i], K_NN, out_mi)
     b1.record(stream)
     ndf.ndf_synchronize(ctx)
-    ksg_pruned_ms = b0.elapsed_time(b1) / nb
-    ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_BRUTE)
-    # ---- batched KSG: 64 references in one launch (autotuned tile shape)
+    ksg_brute_ms = b0.elapsed_time(b1) / nb
+    ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_PRUNED, False)
+    # ---- batched KSG: 16 references in one launch
     ksg_batch = measure_ksg_batch(ndf, ctx, fid, recipe, stream, args) if args.ksg_batch else None
 
     # ---- batched multi-reference Pearson (64 references per call) per precision
@@ -473,11 +474,12 @@ def main():
     peaks = load_peaks()
     props = torch.cuda.get_device_properties(local_rank)
     sms = props.multi_processor_count
-    evals = float(N) * M * (M - 1)  # brute force: every member pair of every vertex
-    achieved = evals / (ksg_ms * 1e-3) / 1e9  # Gdist/s
+    brute_evals = float(N) * M * (M - 1)  # every member pair of every vertex
     # peak: 64 ALU-pipe lanes per SM per clock, 2 ALU instructions per evaluation
-    # (the abs-max and the threshold compare), at the maximum SM clock
+    # (the abs-max distance and its threshold compare), at the maximum SM clock
     peak = sms * 64 / 2 * peaks["sm_max_mhz"] * 1e6 / 1e9
+    achieved = pruned_evals / (ksg_ms * 1e-3) / 1e9  # Gdist/s performed
+    brute_achieved = brute_evals / (ksg_brute_ms * 1e-3) / 1e9
     pearson_gbs = (4.0 * M * N + 4.0 * N + 16.0 * N) / (pearson_ms * 1e-3) / 1e9
 
     result = None
@@ -497,19 +499,20 @@ def main():
             "mi_pairs_per_s": N / (ksg_ms * 1e-3),
             "pearson_hbm_gbs": pearson_gbs,
             "pearson_hbm_frac": pearson_gbs / peaks["hbm_gbs"],
-            "roofline": {"bound": "alu", "kernel": "ksg_volume_kernel<9>", "achieved": achieved,
+            "roofline": {"bound": "alu", "kernel": "ksg_pruned_kernel<9>", "achieved": achieved,
                          "peak": peak, "unit": "Gdist/s", "frac": achieved / peak,
-                         "traffic": KSG_TRAFFIC_PER_VOLUME,
+                         "traffic": KSG_PRUNED_TRAFFIC_PER_VOLUME,
                          "peak_source": f"{peaks['source']} max SM clock",
-                         "evals_per_volume": evals},
-            "ksg_pruned_ms": ksg_pruned_ms,
-            "ksg_pruned_roofline": {"bound": "alu", "kernel": "ksg_pruned_kernel<9>",
-                                    "achieved": pruned_evals / (ksg_pruned_ms * 1e-3) / 1e9,
-                                    "peak": peak, "unit": "Gdist/s",
-                                    "frac": pruned_evals / (ksg_pruned_ms * 1e-3) / 1e9 / peak,
-                                    "evals_per_volume": pruned_evals},
-            "ksg_pruned_speedup_vs_brute": ksg_ms / ksg_pruned_ms,
-            "ksg_batch64": ksg_batch,
+                         "evals_per_volume": pruned_evals,
+                         "brute_force_equivalent_gdist_s": brute_evals / (ksg_ms * 1e-3) / 1e9},
+            "ksg_brute_force": {"ms": ksg_brute_ms, "kernel": "ksg_volume_kernel<9>",
+                                "roofline": {"bound": "alu", "achieved": brute_achieved,
+                                             "peak": peak, "unit": "Gdist/s",
+                                             "frac": brute_achieved / peak,
+                                             "traffic": KSG_BRUTE_TRAFFIC_PER_VOLUME,
+                                             "evals_per_volume": brute_evals},
+                                "pruned_speedup": ksg_brute_ms / ksg_ms},
+            "ksg_batch16": ksg_batch,
             "e2e": {"value": e2e_per_volume, "unit": "ms",
                     "h2d_bytes_per_step": int(field.nbytes),
                     "d2h_bytes_per_step": int(2 * N * 4)},

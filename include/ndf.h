@@ -133,14 +133,18 @@ ndf_status ndf_pearson_batch(ndf_ctx* ctx, int ref_field, int query_field, const
 ndf_status ndf_mi_ksg(ndf_ctx* ctx, int ref_field, int query_field, int64_t ref_idx, int k,
                       float* out);
 
-/* KSG search used by ndf_mi_ksg, ndf_ksg_debug_pair and ndf_train's MI targets.
- * Both give identical results (same FP32 distances, same counts):
- *   NDF_KSG_BRUTE   (default) every member against every member of each pair;
- *   NDF_KSG_PRUNED  members in order of the reference value, each
- *                   side of the outward scan stopped at the first x-gap that
- *                   reaches the current k-th distance (exact pruning).
+/* KSG search used by ndf_mi_ksg, ndf_mi_ksg_batch, ndf_ksg_debug_pair and
+ * ndf_train's MI targets.  Both give identical results (same FP32 distances,
+ * same counts):
+ *   NDF_KSG_PRUNED  (default) one warp per (reference, vertex) pair; members in
+ *                   order of the reference value, each side of a member's
+ *                   outward scan stopped at the first x-gap that reaches its
+ *                   current k-th distance (exact pruning).  When the per-warp
+ *                   arrays do not fit in shared memory (M above ~3400 at k = 8)
+ *                   the brute-force kernel runs instead;
+ *   NDF_KSG_BRUTE   every member against every member of each pair.
  * count_evals != 0 makes the kernels count distance evaluations (read with
- * ndf_ksg_take_eval_count); it costs one atomic per warp per pair. */
+ * ndf_ksg_take_eval_count); it costs one atomic per warp per launch. */
 typedef enum { NDF_KSG_BRUTE = 0, NDF_KSG_PRUNED = 1 } ndf_ksg_algorithm;
 ndf_status ndf_set_ksg_algorithm(ndf_ctx* ctx, int algorithm, int count_evals);
 
@@ -148,15 +152,17 @@ ndf_status ndf_set_ksg_algorithm(ndf_ctx* ctx, int algorithm, int count_evals);
  * counting is off). */
 ndf_status ndf_ksg_take_eval_count(ndf_ctx* ctx, uint64_t* evals);
 
-/* R KSG volumes in one persistent launch (pruned search): out[i*N + v] =
- * I(e^ref(ref_idx[i]); e^query(v)).  References are processed in groups that
- * share each loaded query column and its sorted copy; the group size and tile
- * come from ndf_ksg_autotune (defaults 4 references x 8 vertices). */
+/* R KSG volumes in one persistent launch (the context's search): out[i*N + v] =
+ * I(e^ref(ref_idx[i]); e^query(v)).  The pruned search takes (reference,
+ * vertex) pairs from one work counter; the brute-force search processes
+ * references in groups that share each loaded query column and its sorted copy,
+ * the group size and tile from ndf_ksg_autotune (defaults 4 references x 8
+ * vertices). */
 ndf_status ndf_mi_ksg_batch(ndf_ctx* ctx, int ref_field, int query_field, const int64_t* ref_idx,
                             int R, int k, float* out);
 
-/* Times a few (references per CTA, vertices per tile) shapes of the batched KSG
- * kernel on a sample (8 references x up to 32768 query vertices) and keeps the
+/* Times a few (references per CTA, vertices per tile) shapes of the batched
+ * brute-force KSG kernel on a sample (8 references x up to 32768 query vertices) and keeps the
  * fastest for later ndf_mi_ksg_batch / ndf_train calls on this context.  The
  * chosen shape is written to *best_group / *best_tile (either may be NULL). */
 ndf_status ndf_ksg_autotune(ndf_ctx* ctx, int ref_field, int query_field, int k, int* best_group,

@@ -1,6 +1,6 @@
-// KSG mutual-information volume: algorithm 1 of the k-NN estimator cited in
-// Sec. 3.2 (timed on the CPU in Sec. 6.2, Table 1), for the reference vertex
-// against every vertex of the query field.
+// KSG mutual-information volumes: algorithm 1 of the k-NN estimator cited in
+// Sec. 3.2 (timed on the CPU in Sec. 6.2, Table 1), for R reference vertices
+// against every query vertex.
 //
 // Per pair (x = reference column, y = query column, M joint samples):
 //   d_ij  = max(|x_i - x_j|, |y_i - y_j|)           FP32, exactly rounded
@@ -10,19 +10,31 @@
 //   I     = psi(k) + psi(M) - (1/M) sum_i [psi(nx_i + 1) + psi(ny_i + 1)]   (FP64)
 //
 // GPU design:
-//   stage   one CTA sorts the reference column once per launch (values + member ids).
-//   volume  persistent CTAs walk tiles of VT query vertices.  A tile's y columns
-//           are loaded once (coalesced across the VT vertices of each member row).
-//           For each vertex the CTA builds the joint points in x-sorted order in a
-//           doubled, padded shared array; thread t owns the 4 consecutive sorted
-//           points 4t..4t+3 (and 4(t+T).. for M > 4T) and visits every other point exactly once, outward in
-//           x-order (nearest in x first, wrapping through the doubled array), so
-//           the running top-(k+1) distances in registers tighten early and the
-//           insert branch is rare.  Insertion is a branch-free min/max network.
-//           Counts: binary search in the sorted x (shared by all pairs) and in the
-//           query column's sorted copy (sorted once per field); the search
-//           predicates are the same FP32 |difference| < eps tests, which are
-//           monotone in sorted order.  The digamma sum is FP64, block-reduced.
+//   stage   one CTA per reference sorts its column (values + member ids).
+//   volume  persistent CTAs walk work items (reference group, tile of VT query
+//           vertices).  The tile's query columns and their sorted copies (sorted
+//           once per field) are loaded once, coalesced across the VT vertices, and
+//           serve the G references of the group.  For each (reference, vertex)
+//           the CTA lays the joint points out in x-sorted order in a padded shared
+//           array; thread t owns the 4 consecutive sorted points 4t..4t+3 (and
+//           4(t+T).. when M > 4T) and visits candidates outward in x-order, all
+//           lanes of a warp in lockstep on consecutive positions (no bank
+//           conflicts), the running top-(k+1) distances in registers.  Per
+//           candidate one packed subtract per point gives (dx, dy), the distance
+//           is one min/max, the threshold test u = d - t runs on the FMA pipe
+//           (negative exactly when d < t; no flush to zero), the four tests merge
+//           in a min tree, and a branch-free min/max network inserts.
+//   modes   brute force: every other point exactly once, wrapping through a
+//           doubled copy of the array.  Pruned (exact): no wrap; one side of a
+//           thread's scan ends at the first candidate whose x-gap to the thread's
+//           outermost point on that side reaches the largest current threshold of
+//           its points.  Every later candidate on that side has at least that gap,
+//           hence at least that max-norm distance, and an insert needs a strictly
+//           smaller one; thresholds only shrink, so eps_i is the brute-force value
+//           bit for bit.  A warp leaves the scan when all its lanes are done.
+//   counts  binary search in the sorted x and in the column's sorted copy with the
+//           same FP32 |difference| < eps predicate (monotone in sorted order); the
+//           digamma sum is FP64, block-reduced.
 #include <float.h>
 #include <limits.h>
 #include <math.h>
@@ -34,16 +46,20 @@
 namespace ndf {
 
 constexpr int kKsgPts = 4;  // sorted points owned by one thread
+constexpr int kKsgMaxThreads = 512;
 
-__host__ __device__ __forceinline__ int padi(int i) { return i + (i >> 2); }  // bank-conflict padding
+__host__ __device__ __forceinline__ int padi(int i) { return i + (i >> 2); }  // bank padding
 
-// ---------------------------------------------------------------- stage (a2)
-__global__ void __launch_bounds__(1024) ksg_stage_kernel(const float* __restrict__ field, int M,
-                                                          int64_t N, int64_t ref,
-                                                          float* __restrict__ xs_out,
-                                                          int* __restrict__ perm_out) {
+// ---------------------------------------------------------------- stage
+// one CTA per reference: sorted reference values and their member ids
+// (refs == nullptr: the single reference ref0)
+__global__ void __launch_bounds__(1024)
+    ksg_stage_kernel(const float* __restrict__ field, int M, int64_t N,
+                     const int64_t* __restrict__ refs, int64_t ref0, float* __restrict__ xs_all,
+                     int* __restrict__ perm_all) {
     __shared__ float key[kKsgMaxM];
     __shared__ int val[kKsgMaxM];
+    const int64_t ref = refs ? refs[blockIdx.x] : ref0;
     int n2 = 1;
     while (n2 < M) n2 <<= 1;
     for (int i = threadIdx.x; i < n2; i += blockDim.x) {
@@ -54,12 +70,12 @@ __global__ void __launch_bounds__(1024) ksg_stage_kernel(const float* __restrict
     for (int kk = 2; kk <= n2; kk <<= 1) {
         for (int j = kk >> 1; j > 0; j >>= 1) {
             for (int i = threadIdx.x; i < n2; i += blockDim.x) {
-                int l = i ^ j;
+                const int l = i ^ j;
                 if (l > i) {
-                    bool up = (i & kk) == 0;
-                    float a = key[i], b = key[l];
-                    int va = val[i], vb = val[l];
-                    bool gt = (a > b) || (a == b && va > vb);
+                    const bool up = (i & kk) == 0;
+                    const float a = key[i], b = key[l];
+                    const int va = val[i], vb = val[l];
+                    const bool gt = (a > b) || (a == b && va > vb);
                     if (gt == up) {
                         key[i] = b; key[l] = a;
                         val[i] = vb; val[l] = va;
@@ -69,12 +85,15 @@ __global__ void __launch_bounds__(1024) ksg_stage_kernel(const float* __restrict
             __syncthreads();
         }
     }
+    float* xs = xs_all + (int64_t)blockIdx.x * M;
+    int* pm = perm_all + (int64_t)blockIdx.x * M;
     for (int i = threadIdx.x; i < M; i += blockDim.x) {
-        xs_out[i] = key[i];
-        perm_out[i] = val[i];
+        xs[i] = key[i];
+        pm[i] = val[i];
     }
 }
 
+// ---------------------------------------------------------------- helpers
 __device__ __forceinline__ unsigned long long pack_f2(float2 v) {
     return ((unsigned long long)__float_as_uint(v.y) << 32) | __float_as_uint(v.x);
 }
@@ -87,238 +106,536 @@ __device__ __forceinline__ float2 sub_f32x2(unsigned long long a, unsigned long 
 }
 
 struct KsgArgs {
-    const float* field;  // query field [M][N]
-    const float* sorted; // the query field's columns sorted ascending [M][N]
-    int M;
-    int k;
-    int n2;              // power of two >= M
-    int VT;              // vertices per tile
-    int64_t N;
-    int64_t v_begin, v_end;
-    const float* xs;     // sorted reference values [M]
-    const int* perm;     // member of each sorted position [M]
-    const double* psi;   // psi(n), n <= M + 1
-    float* out;          // out[v - v_begin]
-    double* dbg_mi;      // debug (single vertex) outputs, may be null
+    const float* field;   // query field [M][N]
+    const float* sorted;  // its columns sorted ascending [M][N]
+    int M, k, VT, G, R;
+    int64_t N, v_begin, v_end;
+    const float* xs_all;  // [R][M] sorted reference values
+    const int* perm_all;  // [R][M] member id of each sorted position
+    const double* psi;    // psi(n), n <= M + 1
+    float* out;           // out[r * out_stride + (v - v_begin)]
+    int64_t out_stride;
+    double* dbg_mi;       // debug outputs for (reference 0, vertex v_begin), may be null
     float* dbg_eps;
     int32_t* dbg_nx;
     int32_t* dbg_ny;
+    unsigned long long* evals;  // distance evaluations performed (self excluded), may be null
 };
 
-// shared-memory carve-up (bytes) for a given M and VT
+// shared-memory carve-up (bytes) of the brute-force kernel
 struct KsgSmem {
-    size_t xs, perm, ytile, ystile, pts, red, total;
-    __host__ __device__ KsgSmem(int M, int n2, int VT) {
+    size_t red, xsg, permg, ytile, ystile, pts, total;
+    __host__ __device__ KsgSmem(int M, int VT, int G) {
         size_t o = 0;
-        red = o; o += 32 * sizeof(double);
-        xs = o; o += sizeof(float) * (size_t)M;
-        perm = o; o += sizeof(int) * (size_t)M;
+        red = o; o += 33 * sizeof(double);
+        xsg = o; o += sizeof(float) * (size_t)M * G;
+        permg = o; o += sizeof(int) * (size_t)M * G;
         o = (o + 15) & ~size_t(15);
-        ytile = o; o += sizeof(float) * (size_t)M * (size_t)VT;
-        ystile = o; o += sizeof(float) * (size_t)M * (size_t)VT;
+        ytile = o; o += sizeof(float) * (size_t)M * VT;
+        ystile = o; o += sizeof(float) * (size_t)M * VT;
         o = (o + 15) & ~size_t(15);
         pts = o; o += sizeof(float2) * (size_t)(padi(2 * M) + 4);
         total = o;
-        (void)n2;
     }
 };
 
-// ---------------------------------------------------------------- volume (a4-a6)
-constexpr int kKsgMaxThreads = 512;
-
+// ---------------------------------------------------------------- volume
 template <int K1>
 __global__ void __launch_bounds__(kKsgMaxThreads) ksg_volume_kernel(KsgArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const KsgSmem L(A.M, A.n2, A.VT);
+    const KsgSmem L(A.M, A.VT, A.G);
     double* red = reinterpret_cast<double*>(smem + L.red);
-    float* xs = reinterpret_cast<float*>(smem + L.xs);
-    int* perm = reinterpret_cast<int*>(smem + L.perm);
+    float* xsg = reinterpret_cast<float*>(smem + L.xsg);
+    int* permg = reinterpret_cast<int*>(smem + L.permg);
     float* ytile = reinterpret_cast<float*>(smem + L.ytile);
-    float2* pts = reinterpret_cast<float2*>(smem + L.pts);
     float* ystile = reinterpret_cast<float*>(smem + L.ystile);
+    float2* pts = reinterpret_cast<float2*>(smem + L.pts);
 
     const int M = A.M, T = blockDim.x, tid = threadIdx.x;
     const int64_t N = A.N;
-    for (int i = tid; i < M; i += T) {
-        xs[i] = A.xs[i];
-        perm[i] = A.perm[i];
-    }
-    const double psi_k = A.psi[A.k], psi_M = A.psi[M];
-
     const int64_t nv = A.v_end - A.v_begin;
-    const int64_t ntiles = (nv + A.VT - 1) / A.VT;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t tiles = (nv + A.VT - 1) / A.VT;
+    const int groups = (A.R + A.G - 1) / A.G;
+    const double psi_k = A.psi[A.k], psi_M = A.psi[M];
+    unsigned long long my_evals = 0;
+    int loaded_group = -1;
+
+    for (int64_t item = blockIdx.x; item < (int64_t)groups * tiles; item += gridDim.x) {
+        const int group = (int)(item / tiles);
+        const int64_t tile = item - (int64_t)group * tiles;
+        const int r0 = group * A.G;
+        const int gcount = A.R - r0 < A.G ? A.R - r0 : A.G;
         const int64_t vt0 = A.v_begin + tile * A.VT;
         const int vcount = (int)(A.v_end - vt0 < A.VT ? A.v_end - vt0 : A.VT);
-        __syncthreads();  // previous tile's readers are done with ytile
+        __syncthreads();  // the previous item is done with every shared buffer
+        if (group != loaded_group) {
+            for (int i = tid; i < gcount * M; i += T) {
+                xsg[i] = A.xs_all[(int64_t)r0 * M + i];
+                permg[i] = A.perm_all[(int64_t)r0 * M + i];
+            }
+            loaded_group = group;
+        }
         for (int idx = tid; idx < M * A.VT; idx += T) {
-            int m = idx / A.VT, p = idx - m * A.VT;
-            ytile[p * M + m] = p < vcount ? __ldcs(A.field + (int64_t)m * N + vt0 + p) : 0.0f;
-            ystile[p * M + m] = p < vcount ? __ldcs(A.sorted + (int64_t)m * N + vt0 + p) : 0.0f;
+            const int m = idx / A.VT, p = idx - m * A.VT;
+            const bool in = p < vcount;
+            ytile[p * M + m] = in ? __ldcs(A.field + (int64_t)m * N + vt0 + p) : 0.0f;
+            ystile[p * M + m] = in ? __ldcs(A.sorted + (int64_t)m * N + vt0 + p) : 0.0f;
         }
         for (int p = 0; p < vcount; ++p) {
             const float* ycol = ytile + p * M;
             const float* ys = ystile + p * M;  // the column, sorted (for n_y)
-            __syncthreads();  // tiles ready / previous pair done with pts
-            for (int s = tid; s < M; s += T) {
-                float2 q = make_float2(xs[s], ycol[perm[s]]);
-                pts[padi(s)] = q;
-                pts[padi(s + M)] = q;
-            }
-            __syncthreads();
-
-            double acc = 0.0;
-            for (int base = 0; base < M; base += kKsgPts * T) {
-                const int b0 = base + kKsgPts * tid;
-                const int n_own = M - b0 >= kKsgPts ? kKsgPts : (M - b0 > 0 ? M - b0 : 0);
-                const int R = (M - n_own + 1) >> 1, Lc = (M - n_own) >> 1;
-                // ---- joint k-NN: top-(k+1) distances (self included) per owned point.
-                // Per candidate: one packed FP32 subtract gives (dx, dy) for a point,
-                // d = max(|dx|, |dy|) is one min/max, and the threshold test moves to
-                // the FMA pipe as u = d - t (exactly negative iff d < t: no flush to
-                // zero); the 4 tests merge with a min tree into one compare.
-                unsigned long long P[kKsgPts];
-                float px[kKsgPts], py[kKsgPts];
-                float a[kKsgPts][K1];
-#pragma unroll
-                for (int q = 0; q < kKsgPts; ++q) {
-                    // a missing point sits at +inf: its distances are +inf, never inserted
-                    float2 pq = q < n_own ? pts[padi(b0 + q)] : make_float2(INFINITY, INFINITY);
-                    px[q] = pq.x;
-                    py[q] = pq.y;
-                    P[q] = pack_f2(pq);
-#pragma unroll
-                    for (int j = 0; j < K1; ++j) a[q][j] = FLT_MAX;
+            for (int g = 0; g < gcount; ++g) {
+                const float* xs = xsg + (size_t)g * M;
+                const int* perm = permg + (size_t)g * M;
+                __syncthreads();  // tiles ready / the previous pair is done with pts
+                for (int s = tid; s < M; s += T) {
+                    const float2 q = make_float2(xs[s], ycol[perm[s]]);
+                    pts[padi(s)] = q;
+                    pts[padi(s + M)] = q;
                 }
-                auto visit = [&](float2 c) {
-                    const unsigned long long C = pack_f2(c);
-                    float d[kKsgPts], u[kKsgPts];
+                __syncthreads();
+
+                double acc = 0.0;
+                for (int base = 0; base < M; base += kKsgPts * T) {
+                    const int b0 = base + kKsgPts * tid;
+                    const int n_own = M - b0 >= kKsgPts ? kKsgPts : (M - b0 > 0 ? M - b0 : 0);
+                    // ---- joint k-NN: top-(k+1) distances (self included) per owned point
+                    unsigned long long P[kKsgPts];
+                    float px[kKsgPts], py[kKsgPts];
+                    float a[kKsgPts][K1];
 #pragma unroll
                     for (int q = 0; q < kKsgPts; ++q) {
-                        const float2 dd = sub_f32x2(P[q], C);
-                        d[q] = fmaxf(fabsf(dd.x), fabsf(dd.y));
-                        u[q] = d[q] - a[q][K1 - 1];
-                    }
-                    if (fminf(fminf(u[0], u[1]), fminf(u[2], u[3])) < 0.0f) {
+                        // a missing point sits at +inf: never inserted
+                        const bool valid = q < n_own;
+                        const float2 pq = valid ? pts[padi(b0 + q)] : make_float2(INFINITY, INFINITY);
+                        px[q] = pq.x;
+                        py[q] = pq.y;
+                        P[q] = pack_f2(pq);
 #pragma unroll
-                        for (int q = 0; q < kKsgPts; ++q) topk_insert<K1>(a[q], d[q]);
+                        for (int j = 0; j < K1; ++j) a[q][j] = FLT_MAX;
                     }
-                };
-                if (n_own > 0) {
+                    auto visit = [&](float2 c) {
+                        const unsigned long long C = pack_f2(c);
+                        float d[kKsgPts], u[kKsgPts];
 #pragma unroll
-                    for (int c = 0; c < kKsgPts; ++c)
-                        if (c < n_own) visit(pts[padi(b0 + c)]);
-                    const int rb = b0 + n_own - 1, lb = b0 + M;
-                    for (int o = 1; o <= R; ++o) {
-                        visit(pts[padi(rb + o)]);
-                        if (o <= Lc) visit(pts[padi(lb - o)]);
+                        for (int q = 0; q < kKsgPts; ++q) {
+                            const float2 dd = sub_f32x2(P[q], C);
+                            d[q] = fmaxf(fabsf(dd.x), fabsf(dd.y));
+                            u[q] = d[q] - a[q][K1 - 1];
+                        }
+                        if (fminf(fminf(u[0], u[1]), fminf(u[2], u[3])) < 0.0f) {
+#pragma unroll
+                            for (int q = 0; q < kKsgPts; ++q) topk_insert<K1>(a[q], d[q]);
+                        }
+                    };
+                    if (n_own > 0) {
+#pragma unroll
+                        for (int c = 0; c < kKsgPts; ++c)
+                            if (c < n_own) visit(pts[padi(b0 + c)]);
                     }
-                }
-                // ---- marginal counts and the digamma sum
+                    if (n_own > 0) {
+                        const int rb = b0 + n_own - 1, lb = b0 + M;
+                        const int Rn = (M - n_own + 1) >> 1, Ln = (M - n_own) >> 1;
+                        for (int o = 1; o <= Rn; ++o) {
+                            visit(pts[padi(rb + o)]);
+                            if (o <= Ln) visit(pts[padi(lb - o)]);
+                        }
+                        my_evals += (unsigned long long)n_own * (unsigned long long)(M - 1);
+                    }
+                    // ---- marginal counts and the digamma sum
+                    const bool dbg = A.dbg_eps && r0 + g == 0 && p == 0 && tile == 0;
 #pragma unroll
-                for (int q = 0; q < kKsgPts; ++q) {
-                    if (q < n_own) {
-                        const float e = a[q][K1 - 1];
-                        const int self = e > 0.0f ? 1 : 0;
-                        const int cx = count_within(xs, M, px[q], e) - self;
-                        const int cy = count_within(ys, M, py[q], e) - self;
-                        acc += A.psi[cx + 1] + A.psi[cy + 1];
-                        if (A.dbg_eps) {
-                            const int mi = perm[b0 + q];
-                            A.dbg_eps[mi] = e;
-                            A.dbg_nx[mi] = cx;
-                            A.dbg_ny[mi] = cy;
+                    for (int q = 0; q < kKsgPts; ++q) {
+                        if (q < n_own) {
+                            const float e = a[q][K1 - 1];
+                            const int self = e > 0.0f ? 1 : 0;
+                            const int cx = count_within(xs, M, px[q], e) - self;
+                            const int cy = count_within(ys, M, py[q], e) - self;
+                            acc += A.psi[cx + 1] + A.psi[cy + 1];
+                            if (dbg) {
+                                const int mi = perm[b0 + q];
+                                A.dbg_eps[mi] = e;
+                                A.dbg_nx[mi] = cx;
+                                A.dbg_ny[mi] = cy;
+                            }
                         }
                     }
                 }
-            }
-            const double tot = block_sum(acc, red);
-            if (tid == 0) {
-                const double mi = psi_k + psi_M - tot / (double)M;
-                const int64_t v = vt0 + p;
-                A.out[v - A.v_begin] = (float)mi;
-                if (A.dbg_mi) *A.dbg_mi = mi;
+                const double tot = block_sum(acc, red);
+                if (tid == 0) {
+                    const double mi = psi_k + psi_M - tot / (double)M;
+                    const int64_t v = vt0 + p;
+                    A.out[(int64_t)(r0 + g) * A.out_stride + (v - A.v_begin)] = (float)mi;
+                    if (A.dbg_mi && r0 + g == 0 && p == 0 && tile == 0) *A.dbg_mi = mi;
+                }
             }
         }
     }
+    if (A.evals) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) my_evals += __shfl_xor_sync(0xffffffffu, my_evals, o);
+        if ((tid & 31) == 0) atomicAdd(A.evals, my_evals);
+    }
+}
+
+// ---------------------------------------------------------------- pruned volume
+// Exact pruned search, one warp per (reference, vertex) pair.  Work items are
+// taken from a global counter, so warps never wait for one another.  Within a
+// pair each lane scans one point at a time, outward in x-order; a side of the
+// scan stops at the first candidate whose x-gap reaches the point's current k-th
+// distance (self excluded: the list b holds the k nearest others, eps_i = b[k-1]).
+// Every later candidate on that side is at least that far in x, hence in the
+// max-norm, and an insert needs a strictly smaller distance; the threshold only
+// shrinks, so eps_i equals the brute-force value bit for bit.
+//
+// Each step takes two candidates: one per side while both sides are open, two
+// consecutive ones on the open side otherwise.  The step is branch-free: the
+// point array carries two sentinels at each end (x = -inf / +inf, an x-gap no
+// threshold passes), an idle lane's distances are +inf, and both distances enter
+// the list through one merge network.  A lane that has finished its point takes
+// the next one every kServiceSteps steps (a ballot hands them out, extremes of the
+// x distribution first: their scans are the longest).  The counts and the digamma
+// sum follow in an evenly split loop over the points.
+constexpr int kServiceSteps = 4;
+constexpr int kPad = 2;                                                 // sentinels per end
+constexpr int kWarpSmemPerM = sizeof(float2) + 2 * sizeof(float);       // pts, ys, eps
+constexpr int kWarpSmemFixed = 2 * kPad * sizeof(float2);
+constexpr int kMaxWarpsPerCta = 14;
+
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// b ascending; inserts lo <= hi, keeping the KK smallest:
+// new b[p] = min(b[p], max(b[p-1], lo), max(b[p-2], hi))
+template <int KK>
+__device__ __forceinline__ void insert2(float (&b)[KK], float lo, float hi) {
+#pragma unroll
+    for (int p = KK - 1; p >= 2; --p) b[p] = fmin3(b[p], fmaxf(b[p - 1], lo), fmaxf(b[p - 2], hi));
+    if (KK >= 2) b[1] = fmin3(b[1], fmaxf(b[0], lo), hi);
+    b[0] = fminf(b[0], lo);
+}
+
+__device__ __forceinline__ int count_within_x(const float2* a, int n, float c, float e) {
+    int lo = 0, len = n;
+    while (len > 0) {  // first p with fl(c - a[p].x) < e
+        const int h = len >> 1;
+        if (!((c - a[lo + h].x) < e)) { lo += h + 1; len -= h + 1; }
+        else len = h;
+    }
+    int hi = 0;
+    len = n;
+    while (len > 0) {  // first p with fl(a[p].x - c) >= e
+        const int h = len >> 1;
+        if (!((a[hi + h].x - c) >= e)) { hi += h + 1; len -= h + 1; }
+        else len = h;
+    }
+    return hi > lo ? hi - lo : 0;
 }
 
 template <int K1>
-static cudaError_t launch_ksg_k(ndf_ctx* ctx, const KsgArgs& A, int threads, size_t smem,
-                                int64_t ntiles) {
-    cudaError_t e = cudaFuncSetAttribute(ksg_volume_kernel<K1>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+__global__ void __launch_bounds__(32 * kMaxWarpsPerCta, 1) ksg_pruned_kernel(KsgArgs A,
+                                                                             unsigned long long* work) {
+    constexpr int KK = K1 - 1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int M = A.M, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    float2* S = reinterpret_cast<float2*>(smem) + (size_t)warp * (M + 2 * kPad) + kPad;
+    float* ys = reinterpret_cast<float*>(reinterpret_cast<float2*>(smem) + (size_t)nw * (M + 2 * kPad)) +
+                (size_t)warp * 2 * M;
+    float* epsw = ys + M;
+    const int64_t N = A.N, nv = A.v_end - A.v_begin;
+    const unsigned long long items = (unsigned long long)A.R * (unsigned long long)nv;
+    const double psi_k = A.psi[A.k], psi_M = A.psi[M];
+    const unsigned lt_mask = (1u << lane) - 1u;
+    if (lane < kPad) {
+        S[-1 - lane] = make_float2(-INFINITY, 0.0f);
+        S[M + lane] = make_float2(INFINITY, 0.0f);
+    }
+    unsigned my_evals = 0;
+    unsigned long long evals_total = 0;
+
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(work, 1ull);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= items) break;
+        const int r = (int)(item / (unsigned long long)nv);
+        const int64_t v = A.v_begin + (int64_t)(item - (unsigned long long)r * nv);
+        const float* xs = A.xs_all + (int64_t)r * M;
+        const int* perm = A.perm_all + (int64_t)r * M;
+        __syncwarp();  // the previous pair's reads are done
+        for (int s = lane; s < M; s += 32) {
+            S[s] = make_float2(xs[s], A.field[(int64_t)perm[s] * N + v]);
+            ys[s] = A.sorted[(int64_t)s * N + v];
+        }
+        __syncwarp();
+
+        // ---- joint k-NN distances
+        int i = -1, next = 0, pr = 0, pl = 0;  // next right / left candidate positions
+        bool on_r = false, on_l = false;
+        unsigned long long P = 0;
+        float b[KK];
+#pragma unroll
+        for (int c = 0; c < KK; ++c) b[c] = FLT_MAX;
+        for (;;) {
+            if (i >= 0 && !on_r && !on_l) {
+                epsw[i] = b[KK - 1];
+                i = -1;
+            }
+            const unsigned idle = __ballot_sync(0xffffffffu, i < 0);
+            if (next >= M && idle == 0xffffffffu) break;
+            if (next < M && idle != 0u) {
+                const int g = next + __popc(idle & lt_mask);
+                if (i < 0 && g < M) {
+                    i = (g & 1) ? M - 1 - (g >> 1) : (g >> 1);
+                    P = pack_f2(S[i]);
+#pragma unroll
+                    for (int c = 0; c < KK; ++c) b[c] = FLT_MAX;
+                    pr = i + 1;
+                    pl = i - 1;
+                    on_r = true;
+                    on_l = true;
+                }
+                next += __popc(idle);
+            }
+#pragma unroll
+            for (int st = 0; st < kServiceSteps; ++st) {
+                const bool act = on_r || on_l, both = on_r && on_l;
+                const int j1 = on_r ? pr : pl;
+                const int j2 = on_l ? (on_r ? pl : pl - 1) : pr + 1;
+                const float2 e1 = sub_f32x2(P, pack_f2(S[j1]));
+                const float2 e2 = sub_f32x2(P, pack_f2(S[j2]));
+                const float g1 = fabsf(e1.x), g2 = fabsf(e2.x);
+                const float t = b[KK - 1];
+                const float d1 = act ? fmaxf(g1, fabsf(e1.y)) : INFINITY;
+                const float d2 = act ? fmaxf(g2, fabsf(e2.y)) : INFINITY;
+                insert2<KK>(b, fminf(d1, d2), fmaxf(d1, d2));
+                // the pre-insert threshold makes the side test conservative (exact)
+                const bool go1 = act && g1 < t, go2 = act && g2 < t;
+                my_evals += (unsigned)go1 + (unsigned)go2;
+                const int adv = (int)go1 + (int)go2;  // one open side: g2 >= g1
+                pr += both ? (int)go1 : (on_r ? adv : 0);
+                pl -= both ? (int)go2 : (on_l ? adv : 0);
+                const bool nr = both ? go1 : (on_r && go2);
+                const bool nl = both ? go2 : (on_l && go2);
+                on_r = nr;
+                on_l = nl;
+            }
+        }
+        __syncwarp();
+
+        // ---- marginal counts and the digamma sum
+        const bool dbg = A.dbg_eps && r == 0 && v == A.v_begin;
+        double acc = 0.0;
+        for (int s = lane; s < M; s += 32) {
+            const float e = epsw[s];
+            const float2 ps = S[s];
+            const int self = e > 0.0f ? 1 : 0;
+            const int cx = count_within_x(S, M, ps.x, e) - self;
+            const int cy = count_within(ys, M, ps.y, e) - self;
+            acc += A.psi[cx + 1] + A.psi[cy + 1];
+            if (dbg) {
+                const int mi = perm[s];
+                A.dbg_eps[mi] = e;
+                A.dbg_nx[mi] = cx;
+                A.dbg_ny[mi] = cy;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+            const double mi = psi_k + psi_M - acc / (double)M;
+            A.out[(int64_t)r * A.out_stride + (v - A.v_begin)] = (float)mi;
+            if (dbg && A.dbg_mi) *A.dbg_mi = mi;
+        }
+        evals_total += my_evals;
+        my_evals = 0;
+    }
+    if (A.evals) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) evals_total += __shfl_xor_sync(0xffffffffu, evals_total, o);
+        if (lane == 0) atomicAdd(A.evals, evals_total);
+    }
+}
+
+template <class Kern>
+static cudaError_t launch_persistent(ndf_ctx* ctx, Kern kern, const KsgArgs& A, int threads,
+                                    size_t smem, int64_t items) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ksg_volume_kernel<K1>, threads,
-                                                      smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)ctx->sm_count * per_sm;
-    if (grid > ntiles) grid = ntiles;
-    ksg_volume_kernel<K1><<<(unsigned)grid, threads, smem, ctx->stream>>>(A);
+    if (grid > items) grid = items;
+    kern<<<(unsigned)grid, threads, smem, ctx->stream>>>(A);
     ctx->launches++;
     return cudaGetLastError();
 }
 
-cudaError_t launch_ksg(ndf_ctx* ctx, const Field& rf, const Field& qf, int64_t ref_idx, int k,
-                       int64_t v_begin, int64_t v_end, float* out, double* dbg_mi, float* dbg_eps,
-                       int32_t* dbg_nx, int32_t* dbg_ny) {
+template <int K1>
+static cudaError_t launch_ksg_k(ndf_ctx* ctx, KsgArgs A, bool prune) {
+    const int M = A.M;
+    if (prune) {
+        // one warp per pair; as many warps per CTA as fit in shared memory
+        const size_t per_warp = (size_t)kWarpSmemPerM * M + kWarpSmemFixed;
+        int wpc = (int)((227 * 1024) / per_warp);
+        if (wpc > kMaxWarpsPerCta) wpc = kMaxWarpsPerCta;
+        if (wpc < 1) wpc = 1;
+        const size_t smem = (size_t)wpc * per_warp;
+        cudaError_t e = ctx->ksg_work.reserve(sizeof(unsigned long long));
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(ctx->ksg_work.ptr, 0, sizeof(unsigned long long), ctx->stream);
+        if (e != cudaSuccess) return e;
+        auto kern = ksg_pruned_kernel<K1>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * wpc, smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+        const int64_t pairs = (int64_t)A.R * (A.v_end - A.v_begin);
+        int64_t grid = (int64_t)ctx->sm_count * per_sm;
+        if (grid * wpc > pairs) grid = (pairs + wpc - 1) / wpc;
+        kern<<<(unsigned)grid, 32 * wpc, smem, ctx->stream>>>(
+            A, ctx->ksg_work.as<unsigned long long>());
+        ctx->launches++;
+        return cudaGetLastError();
+    }
+    // two CTAs per SM: at most ~112 KB of shared memory each
+    const size_t budget = 112 * 1024;
+    while (A.G > 1 && KsgSmem(M, A.VT, A.G).total > budget) A.G >>= 1;
+    while (A.VT > 1 && KsgSmem(M, A.VT, A.G).total > budget) A.VT >>= 1;
+    const size_t smem = KsgSmem(M, A.VT, A.G).total;
+    const int64_t items =
+        (int64_t)((A.R + A.G - 1) / A.G) * ((A.v_end - A.v_begin + A.VT - 1) / A.VT);
+    int threads = ((M + kKsgPts - 1) / kKsgPts + 31) / 32 * 32;
+    if (threads > kKsgMaxThreads) threads = kKsgMaxThreads;
+    return launch_persistent(ctx, ksg_volume_kernel<K1>, A, threads, smem, items);
+}
+
+cudaError_t launch_ksg(ndf_ctx* ctx, const Field& rf, const Field& qf, const int64_t* d_refs,
+                       int64_t ref0, int R, int k, int64_t v_begin, int64_t v_end, float* out,
+                       int64_t out_stride, bool prune, int G, int VT, double* dbg_mi,
+                       float* dbg_eps, int32_t* dbg_nx, int32_t* dbg_ny,
+                       unsigned long long* evals) {
     const int M = (int)rf.M;
-    cudaError_t e = ctx->stage_x.reserve(sizeof(float) * (size_t)M);
-    if (e == cudaSuccess) e = ctx->stage_perm.reserve(sizeof(int) * (size_t)M);
+    if (!qf.sorted || R < 1 || v_end <= v_begin) return cudaErrorInvalidValue;
+    if (!d_refs && R != 1) return cudaErrorInvalidValue;
+    cudaError_t e = ctx->stage_x.reserve(sizeof(float) * (size_t)M * (size_t)R);
+    if (e == cudaSuccess) e = ctx->stage_perm.reserve(sizeof(int) * (size_t)M * (size_t)R);
     if (e != cudaSuccess) return e;
-    ksg_stage_kernel<<<1, 1024, 0, ctx->stream>>>(rf.data, M, rf.N, ref_idx,
+    ksg_stage_kernel<<<R, 1024, 0, ctx->stream>>>(rf.data, M, rf.N, d_refs, ref0,
                                                    ctx->stage_x.as<float>(),
                                                    ctx->stage_perm.as<int>());
     ctx->launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-
     KsgArgs A;
     A.field = qf.data;
     A.sorted = qf.sorted;
     A.M = M;
     A.k = k;
-    A.n2 = 1;
-    while (A.n2 < M) A.n2 <<= 1;
+    A.G = G < 1 ? 1 : G > R ? R : G;
+    A.VT = VT < 1 ? 1 : VT;
+    A.R = R;
     A.N = qf.N;
     A.v_begin = v_begin;
     A.v_end = v_end;
-    A.xs = ctx->stage_x.as<float>();
-    A.perm = ctx->stage_perm.as<int>();
+    A.xs_all = ctx->stage_x.as<float>();
+    A.perm_all = ctx->stage_perm.as<int>();
     A.psi = ctx->psi.as<double>();
     A.out = out;
+    A.out_stride = out_stride;
     A.dbg_mi = dbg_mi;
     A.dbg_eps = dbg_eps;
     A.dbg_nx = dbg_nx;
     A.dbg_ny = dbg_ny;
-    int threads = ((M + kKsgPts - 1) / kKsgPts + 31) / 32 * 32;
-    if (threads > kKsgMaxThreads) threads = kKsgMaxThreads;
-    // vertices per tile: up to 8, bounded by a ~96 KB shared-memory budget
-    int VT = 8;
-    while (VT > 1 && KsgSmem(M, A.n2, VT).total > 96 * 1024) VT >>= 1;
-    A.VT = VT;
-    size_t smem = KsgSmem(M, A.n2, VT).total;
-    int64_t ntiles = (v_end - v_begin + VT - 1) / VT;
+    A.evals = evals;
     switch (k + 1) {
-        case 2: return launch_ksg_k<2>(ctx, A, threads, smem, ntiles);
-        case 3: return launch_ksg_k<3>(ctx, A, threads, smem, ntiles);
-        case 4: return launch_ksg_k<4>(ctx, A, threads, smem, ntiles);
-        case 5: return launch_ksg_k<5>(ctx, A, threads, smem, ntiles);
-        case 6: return launch_ksg_k<6>(ctx, A, threads, smem, ntiles);
-        case 7: return launch_ksg_k<7>(ctx, A, threads, smem, ntiles);
-        case 8: return launch_ksg_k<8>(ctx, A, threads, smem, ntiles);
-        case 9: return launch_ksg_k<9>(ctx, A, threads, smem, ntiles);
-        case 10: return launch_ksg_k<10>(ctx, A, threads, smem, ntiles);
-        case 11: return launch_ksg_k<11>(ctx, A, threads, smem, ntiles);
-        case 12: return launch_ksg_k<12>(ctx, A, threads, smem, ntiles);
-        case 13: return launch_ksg_k<13>(ctx, A, threads, smem, ntiles);
-        case 14: return launch_ksg_k<14>(ctx, A, threads, smem, ntiles);
-        case 15: return launch_ksg_k<15>(ctx, A, threads, smem, ntiles);
-        case 16: return launch_ksg_k<16>(ctx, A, threads, smem, ntiles);
-        case 17: return launch_ksg_k<17>(ctx, A, threads, smem, ntiles);
+        case 2: return launch_ksg_k<2>(ctx, A, prune);
+        case 3: return launch_ksg_k<3>(ctx, A, prune);
+        case 4: return launch_ksg_k<4>(ctx, A, prune);
+        case 5: return launch_ksg_k<5>(ctx, A, prune);
+        case 6: return launch_ksg_k<6>(ctx, A, prune);
+        case 7: return launch_ksg_k<7>(ctx, A, prune);
+        case 8: return launch_ksg_k<8>(ctx, A, prune);
+        case 9: return launch_ksg_k<9>(ctx, A, prune);
+        case 10: return launch_ksg_k<10>(ctx, A, prune);
+        case 11: return launch_ksg_k<11>(ctx, A, prune);
+        case 12: return launch_ksg_k<12>(ctx, A, prune);
+        case 13: return launch_ksg_k<13>(ctx, A, prune);
+        case 14: return launch_ksg_k<14>(ctx, A, prune);
+        case 15: return launch_ksg_k<15>(ctx, A, prune);
+        case 16: return launch_ksg_k<16>(ctx, A, prune);
+        case 17: return launch_ksg_k<17>(ctx, A, prune);
         default: return cudaErrorInvalidValue;
     }
 }
 
 }  // namespace ndf
+
+using namespace ndf;
+
+extern "C" ndf_status ndf_ksg_autotune(ndf_ctx* ctx, int ref_field, int query_field, int k,
+                                       int* best_group, int* best_tile) {
+    if (!ctx) return NDF_ERR_ARG;
+    const Field *rf, *qf;
+    ndf_status st = check_pair(ctx, ref_field, query_field, 0, &rf, &qf);
+    if (st != NDF_OK) return st;
+    if (k < 1 || k >= rf->M || k > kKsgMaxK || rf->M > kKsgMaxM)
+        return fail(ctx, NDF_ERR_ARG, "bad k or M");
+    cudaSetDevice(ctx->device);
+    if ((st = ensure_psi_table(ctx, rf->M + 1)) != NDF_OK) return st;
+    cudaError_t es = ensure_sorted_columns(ctx, ctx->fields[query_field]);
+    if (es != cudaSuccess) return cuda_fail(ctx, es, "sorted columns");
+    // sample: 8 references spread over the grid, the first 16384 query vertices
+    const int R = 8;
+    const int64_t nv = qf->N < 16384 ? qf->N : 16384;
+    int64_t refs[R];
+    for (int i = 0; i < R; ++i) refs[i] = (int64_t)((double)(i + 0.5) / R * (double)(rf->N - 1));
+    float* out = nullptr;
+    int64_t* d_refs = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&out, sizeof(float) * (size_t)R * (size_t)nv);
+    if (e == cudaSuccess) e = cudaMalloc(&d_refs, sizeof refs);
+    if (e == cudaSuccess) e = cudaMemcpy(d_refs, refs, sizeof refs, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const int cand[][2] = {{1, 4}, {1, 8}, {2, 4}, {2, 8}, {4, 4}, {4, 8}};
+    const bool prune = false;  // the shapes belong to the brute-force kernel
+    float best = 3.4e38f;
+    int bg = ctx->ksg_group, bt = ctx->ksg_tile;
+    for (const auto& c : cand) {
+        if (e != cudaSuccess) break;
+        // warm-up, then timed
+        e = launch_ksg(ctx, *rf, *qf, d_refs, 0, R, k, 0, nv, out, nv, prune, c[0], c[1], nullptr,
+                       nullptr, nullptr, nullptr, nullptr);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+        if (e == cudaSuccess)
+            e = launch_ksg(ctx, *rf, *qf, d_refs, 0, R, k, 0, nv, out, nv, prune, c[0], c[1],
+                           nullptr, nullptr, nullptr, nullptr, nullptr);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best) {
+            best = ms;
+            bg = c[0];
+            bt = c[1];
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (out) cudaFree(out);
+    if (d_refs) cudaFree(d_refs);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "ksg autotune");
+    ctx->ksg_group = bg;
+    ctx->ksg_tile = bt;
+    if (best_group) *best_group = bg;
+    if (best_tile) *best_tile = bt;
+    return NDF_OK;
+}

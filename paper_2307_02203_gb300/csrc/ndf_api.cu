@@ -217,6 +217,7 @@ void ndf_destroy(ndf_ctx* ctx) {
     ctx->zr.release();
     ctx->refidx.release();
     ctx->evals.release();
+    ctx->ksg_work.release();
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     delete ctx;
 }
@@ -363,17 +364,10 @@ static ndf_status check_ksg_args(ndf_ctx* ctx, const Field* rf, int k) {
 static cudaError_t run_ksg_one(ndf_ctx* ctx, const Field& rf, const Field& qf, int64_t ref_idx,
                                int k, int64_t v_begin, int64_t v_end, float* out, double* dbg_mi,
                                float* dbg_eps, int32_t* dbg_nx, int32_t* dbg_ny) {
-    if (ctx->ksg_algorithm == NDF_KSG_BRUTE)
-        return launch_ksg(ctx, rf, qf, ref_idx, k, v_begin, v_end, out, dbg_mi, dbg_eps, dbg_nx,
-                          dbg_ny);
-    cudaError_t e = ctx->refidx.reserve(sizeof(int64_t));
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(ctx->refidx.ptr, &ref_idx, sizeof(int64_t), cudaMemcpyHostToDevice,
-                            ctx->stream);
-    if (e != cudaSuccess) return e;
-    return launch_ksg_pruned(ctx, rf, qf, ctx->refidx.as<int64_t>(), 1, k, v_begin, v_end, out,
-                             0, 1, 8, dbg_mi, dbg_eps, dbg_nx, dbg_ny,
-                             ctx->count_evals ? ctx->evals.as<unsigned long long>() : nullptr);
+    return launch_ksg(ctx, rf, qf, nullptr, ref_idx, 1, k, v_begin, v_end, out, 0,
+                      ctx->ksg_algorithm == NDF_KSG_PRUNED, 1, ctx->ksg_tile, dbg_mi, dbg_eps,
+                      dbg_nx, dbg_ny,
+                      ctx->count_evals ? ctx->evals.as<unsigned long long>() : nullptr);
 }
 
 ndf_status ndf_mi_ksg(ndf_ctx* ctx, int ref_field, int query_field, int64_t ref_idx, int k,
@@ -487,10 +481,10 @@ ndf_status ndf_mi_ksg_batch(ndf_ctx* ctx, int ref_field, int query_field, const 
         e = cudaMemcpyAsync(ctx->refidx.ptr, ref_idx, sizeof(int64_t) * (size_t)R,
                             cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess)
-        e = launch_ksg_pruned(ctx, *rf, *qf, ctx->refidx.as<int64_t>(), R, k, 0, qf->N,
-                              static_cast<float*>(dev_out), qf->N, ctx->ksg_group, ctx->ksg_tile,
-                              nullptr, nullptr, nullptr, nullptr,
-                              ctx->count_evals ? ctx->evals.as<unsigned long long>() : nullptr);
+        e = launch_ksg(ctx, *rf, *qf, ctx->refidx.as<int64_t>(), 0, R, k, 0, qf->N,
+                       static_cast<float*>(dev_out), qf->N, ctx->ksg_algorithm == NDF_KSG_PRUNED,
+                       ctx->ksg_group, ctx->ksg_tile, nullptr, nullptr, nullptr, nullptr,
+                       ctx->count_evals ? ctx->evals.as<unsigned long long>() : nullptr);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "ksg batch launch");
     return finish_out(ctx, out, dev_out, bytes, is_host);
 }

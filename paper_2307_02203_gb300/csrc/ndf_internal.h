@@ -57,11 +57,12 @@ struct ndf_ctx {
     int64_t psi_n = 0;
     ndf::DevBuf dbg;         // KSG debug outputs
     ndf::DevBuf flag;        // small device status words
-    int ksg_algorithm = NDF_KSG_BRUTE;
+    int ksg_algorithm = NDF_KSG_PRUNED;
     int ksg_group = 4;       // references per CTA in batched KSG (tuned by ndf_ksg_autotune)
     int ksg_tile = 8;        // query vertices per tile
     bool count_evals = false;
     ndf::DevBuf evals;       // KSG distance evaluations (when counting is on)
+    ndf::DevBuf ksg_work;    // pruned KSG: work-item counter
     ndf::DevBuf zr;          // batched Pearson: standardised reference rows
     ndf::DevBuf refidx;      // batched calls: reference indices on the device
 };
@@ -92,17 +93,18 @@ double digamma_int_host(int64_t n);
 cudaError_t launch_field_stats(ndf_ctx* ctx, const Field& f, int* d_nonfinite);
 cudaError_t launch_pearson(ndf_ctx* ctx, const Field& rf, const Field& qf, int64_t ref_idx,
                            float* out);
-cudaError_t launch_ksg(ndf_ctx* ctx, const Field& rf, const Field& qf, int64_t ref_idx, int k,
-                       int64_t v_begin, int64_t v_end, float* out, double* dbg_mi, float* dbg_eps,
-                       int32_t* dbg_nx, int32_t* dbg_ny);
+// KSG MI for R references (d_refs on the device, or the single reference ref0
+// when d_refs is null) against query vertices [v_begin, v_end):
+// out[r * out_stride + (v - v_begin)].  prune selects the exact pruned scan over
+// brute force; G references share a CTA's query tile of VT vertices.
+cudaError_t launch_ksg(ndf_ctx* ctx, const Field& rf, const Field& qf, const int64_t* d_refs,
+                       int64_t ref0, int R, int k, int64_t v_begin, int64_t v_end, float* out,
+                       int64_t out_stride, bool prune, int G, int VT, double* dbg_mi,
+                       float* dbg_eps, int32_t* dbg_nx, int32_t* dbg_ny,
+                       unsigned long long* evals);
 
 // Builds Field::sorted (one sort per vertex column, kept with the field).
 cudaError_t ensure_sorted_columns(ndf_ctx* ctx, Field& f);
-
-cudaError_t launch_ksg_pruned(ndf_ctx* ctx, const Field& rf, const Field& qf, const int64_t* d_refs,
-                              int R, int k, int64_t v_begin, int64_t v_end, float* out,
-                              int64_t out_stride, int G, int VT, double* dbg_mi, float* dbg_eps,
-                              int32_t* dbg_nx, int32_t* dbg_ny, unsigned long long* evals);
 
 constexpr int kKsgMaxM = 4096;
 constexpr int kKsgMaxK = 16;

@@ -500,9 +500,9 @@ ndf_status ndf_train(ndf_ctx* ctx, int ref_field, int query_field, int measure, 
                 e = launch_pearson(ctx, *rf, blk, hrefs[(size_t)r], gtgt + r * Qg);
         } else if (e == cudaSuccess) {
             // all references of the group in one launch; each query column is sorted once
-            e = launch_ksg_pruned(ctx, *rf, blk, drefs, (int)rows, k, 0, Qg, gtgt, Qg,
-                                  ctx->ksg_group, ctx->ksg_tile, nullptr, nullptr, nullptr,
-                                  nullptr, nullptr);
+            e = launch_ksg(ctx, *rf, blk, drefs, 0, (int)rows, k, 0, Qg, gtgt, Qg,
+                           ctx->ksg_algorithm == NDF_KSG_PRUNED, ctx->ksg_group, ctx->ksg_tile,
+                           nullptr, nullptr, nullptr, nullptr, nullptr);
         }
         const int64_t take = std::min<int64_t>(T - filled, rows * Qg);
         if (e == cudaSuccess)

@@ -122,7 +122,7 @@ def algo(request, ndf_mod, ctx):
     code = {"brute": ndf_mod.NDF_KSG_BRUTE, "pruned": ndf_mod.NDF_KSG_PRUNED}[request.param]
     ndf_mod.ndf_set_ksg_algorithm(ctx, code)
     yield request.param
-    ndf_mod.ndf_set_ksg_algorithm(ctx, ndf_mod.NDF_KSG_BRUTE)
+    ndf_mod.ndf_set_ksg_algorithm(ctx, ndf_mod.NDF_KSG_PRUNED)
 
 
 def ksg_debug(ndf, ctx, fa, fb, r, v, k, M):
@@ -173,6 +173,9 @@ def test_ksg_tiny_volume(ndf_mod, ctx, algo, tiny_field, tiny_ref):
     ((1000, 2, 8, 25), 8, "normal"),   # paper-scale M, several tiles + ragged tail
     ((1000, 1, 3, 7), 8, "ties"),      # heavy ties: eps = 0 and equal distances
     ((2500, 1, 2, 9), 8, "normal"),    # M > 2048: threads own two point blocks
+    ((4096, 1, 1, 3), 16, "normal"),   # largest M and k (the pruned search's per-point
+                                       # lists do not fit in shared memory: brute force)
+    ((3000, 1, 1, 4), 8, "normal"),    # M > 2048 with the pruned search in shared memory
     ((2, 1, 2, 2), 1, "normal"),       # smallest M
     ((17, 1, 3, 3), 16, "normal"),     # k = M - 1 = 16 (largest supported k)
     ((100, 2, 3, 5), 3, "ties"),
@@ -209,7 +212,7 @@ def test_ksg_cross_field(ndf_mod, ctx, algo):
 
 
 # ---------------------------------------------------------------- batched KSG
-def test_ksg_batch_matches_oracle_and_single(ndf_mod, ctx):
+def test_ksg_batch_matches_oracle_and_single(ndf_mod, ctx, algo):
     ndf = ndf_mod
     shape = (1000, 2, 6, 11)
     f = rand_field(shape, seed=77)
@@ -243,7 +246,7 @@ def test_ksg_eval_counter(ndf_mod, ctx, tiny_field, tiny_ref):
     ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_PRUNED, True)
     ndf.ndf_mi_ksg(ctx, fid, fid, tiny_ref, 4, out)
     evals = ndf.ndf_ksg_take_eval_count(ctx)
-    ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_BRUTE, False)
+    ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_PRUNED, False)
     # the pruned search visits a strict subset of the M(M-1) candidates of each pair
     assert 0 < evals < N * M * (M - 1)
     assert ndf.ndf_ksg_take_eval_count(ctx) == 0

@@ -69,7 +69,7 @@ def test_csens_ksg_sampled(ndf_mod, ctx, csens, algorithm):
         np.testing.assert_array_equal(eps, o[1])
         np.testing.assert_array_equal(nx, o[2])
         np.testing.assert_array_equal(ny, o[3])
-    ndf_mod.ndf_set_ksg_algorithm(ctx, ndf_mod.NDF_KSG_BRUTE)
+    ndf_mod.ndf_set_ksg_algorithm(ctx, ndf_mod.NDF_KSG_PRUNED)
 
 
 def test_csens_ksg_batch_sampled(ndf_mod, ctx, csens):
