@@ -35,9 +35,9 @@ K_NN = 8
 # DRAM bytes per launch of the KSG kernels at the full 250x352x20 volume, from a
 # one-level slab capture (ncu dram__bytes_read.sum + dram__bytes_write.sum for
 # 88,000 vertices) scaled by the vertices processed (x20): the kernels stream each
-# query column and its sorted copy once.  None until captured for the current code.
-KSG_PRUNED_TRAFFIC_PER_VOLUME = None
-KSG_BRUTE_TRAFFIC_PER_VOLUME = None
+# query column and its sorted copy once (algorithmic 14.08 GB + 7 MB output).
+KSG_PRUNED_TRAFFIC_PER_VOLUME = (706.494e6 + 4.789e6) * 20
+KSG_BRUTE_TRAFFIC_PER_VOLUME = (705.845e6 + 4.089e6) * 20
 METRIC = "ms per 1.76M-voxel dependence volume (Pearson + KSG MI k=8, M=1000)"
 
 
@@ -299,6 +299,31 @@ def measure_ndf(ndf, ctx, fid, recipe, stream, args, exact_ms):
     return out
 
 
+def rank_references(N, count, rank):
+    """Reference vertices of one rank: an independent seeded stream per rank, so
+    that every rank computes its own volumes (weak scaling, no data-path
+    collective)."""
+    rng = np.random.default_rng(20230705 + rank)
+    return [int(r) for r in rng.integers(0, N, size=count)]
+
+
+def max_over_ranks(values, world, device):
+    """Element-wise maximum of per-rank timings: the slowest rank sets the job time."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def job_ms_per_volume(total_ms, steps, world):
+    """Whole-job time per volume: the max-over-ranks time of the timed region over
+    the volumes all ranks processed."""
+    return total_ms / (steps * world)
+
+
 def run_reference(args, recipe):
     rank = env_int("RANK", 0)
     if rank != 0:
@@ -379,8 +404,7 @@ def main():
     M, Z, Y, X = field.shape
     N = recipe.N
     fid = ndf.ndf_load_ensemble(ctx, field_t, M, Z, Y, X)
-    rng = np.random.default_rng(20230705 + rank)
-    refs = [int(r) for r in rng.integers(0, N, size=args.warmup + args.steps)]
+    refs = rank_references(N, args.warmup + args.steps, rank)
     out_r = torch.empty(N, dtype=torch.float32, device="cuda")
     out_mi = torch.empty(N, dtype=torch.float32, device="cuda")
 
@@ -417,12 +441,8 @@ def main():
     total_ms = t_start.elapsed_time(t_end)
     pearson_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
     ksg_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
-    if world > 1:
-        t = torch.tensor([total_ms, pearson_ms, ksg_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms, pearson_ms, ksg_ms = [float(v) for v in t.tolist()]
-    volumes = args.steps * world
-    ms_per_volume = total_ms / volumes
+    total_ms, pearson_ms, ksg_ms = max_over_ranks([total_ms, pearson_ms, ksg_ms], world, "cuda")
+    ms_per_volume = job_ms_per_volume(total_ms, args.steps, world)
 
     # ---- distance evaluations of the pruned search on the same references (counted
     # in a separate, untimed pass), and the brute-force search timed beside it
@@ -463,12 +483,8 @@ def main():
         ndf.ndf_mi_ksg(ctx, fid2, fid2, refs[args.warmup + i], K_NN, host_mi)
         ndf.ndf_free_ensemble(ctx, fid2)
     barrier()
-    e2e_ms = (time.perf_counter() - t0) * 1e3
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_per_volume = e2e_ms / (e2e_steps * world)
+    e2e_ms = max_over_ranks([(time.perf_counter() - t0) * 1e3], world, "cuda")[0]
+    e2e_per_volume = job_ms_per_volume(e2e_ms, e2e_steps, world)
 
     # ---- roofline of the dominant kernel (KSG: ALU-bound distance evaluations)
     peaks = load_peaks()

@@ -288,11 +288,10 @@ __global__ void __launch_bounds__(kKsgMaxThreads) ksg_volume_kernel(KsgArgs A) {
 // max-norm, and an insert needs a strictly smaller distance; the threshold only
 // shrinks, so eps_i equals the brute-force value bit for bit.
 //
-// Each step takes two candidates: one per side while both sides are open, two
-// consecutive ones on the open side otherwise.  The step is branch-free: the
-// point array carries two sentinels at each end (x = -inf / +inf, an x-gap no
-// threshold passes), an idle lane's distances are +inf, and both distances enter
-// the list through one merge network.  A lane that has finished its point takes
+// Each step takes two candidates, one per scan slot, and is branch-free: the point
+// array carries two sentinels at each end (x = -inf / +inf, an x-gap no threshold
+// passes), a closed slot re-reads a candidate beyond its threshold, and both
+// distances enter the list through one merge network.  A lane that has finished its point takes
 // the next one every kServiceSteps steps (a ballot hands them out, extremes of the
 // x distribution first: their scans are the longest).  The counts and the digamma
 // sum follow in an evenly split loop over the points.
@@ -302,19 +301,13 @@ constexpr int kWarpSmemPerM = sizeof(float2) + 2 * sizeof(float);       // pts, 
 constexpr int kWarpSmemFixed = 2 * kPad * sizeof(float2);
 constexpr int kMaxWarpsPerCta = 14;
 
-__device__ __forceinline__ float fmin3(float a, float b, float c) {
-    float r;
-    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-    return r;
-}
-
 // b ascending; inserts lo <= hi, keeping the KK smallest:
 // new b[p] = min(b[p], max(b[p-1], lo), max(b[p-2], hi))
 template <int KK>
 __device__ __forceinline__ void insert2(float (&b)[KK], float lo, float hi) {
 #pragma unroll
-    for (int p = KK - 1; p >= 2; --p) b[p] = fmin3(b[p], fmaxf(b[p - 1], lo), fmaxf(b[p - 2], hi));
-    if (KK >= 2) b[1] = fmin3(b[1], fmaxf(b[0], lo), hi);
+    for (int p = KK - 1; p >= 2; --p) b[p] = fminf(fminf(b[p], fmaxf(b[p - 1], lo)), fmaxf(b[p - 2], hi));
+    if (KK >= 2) b[1] = fminf(fminf(b[1], fmaxf(b[0], lo)), hi);
     b[0] = fminf(b[0], lo);
 }
 
@@ -373,17 +366,41 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerCta, 1) ksg_pruned_kernel(Ksg
         }
         __syncwarp();
 
-        // ---- joint k-NN distances
-        int i = -1, next = 0, pr = 0, pl = 0;  // next right / left candidate positions
-        bool on_r = false, on_l = false;
+        // ---- joint k-NN distances.  Two scan slots per lane, each a position and a
+        // stride: slot 1 starts right of the point (+1), slot 2 left (-1).  A slot
+        // advances while its candidate's x-gap is below the threshold and otherwise
+        // stays on that candidate, so a closed side costs no bookkeeping.  At the
+        // service points a lane whose one side has closed sends that slot to the
+        // other side (the two slots then interleave with stride 2), a lane whose
+        // both sides have closed stores eps and takes a new point.  Idle lanes point
+        // both slots at sentinels.
+        int i = -1, next = 0, pr = M, pl = -1, sr = 1, sl = -1;
+        unsigned steps = 0;
+        float px = 0.0f;
         unsigned long long P = 0;
         float b[KK];
 #pragma unroll
         for (int c = 0; c < KK; ++c) b[c] = FLT_MAX;
         for (;;) {
-            if (i >= 0 && !on_r && !on_l) {
-                epsw[i] = b[KK - 1];
-                i = -1;
+            if (i >= 0) {
+                const float t = b[KK - 1];
+                const bool dead1 = fabsf(px - S[pr].x) >= t;
+                const bool dead2 = fabsf(px - S[pl].x) >= t;
+                if (dead1 && dead2) {
+                    epsw[i] = t;
+                    my_evals += 2u * steps;
+                    i = -1;
+                    pr = M;
+                    pl = -1;
+                } else if (dead1 && sr == 1) {
+                    pr = pl + sl;  // slot 1 joins the left side
+                    sr = 2 * sl;
+                    sl = sr;
+                } else if (dead2 && sl == -1) {
+                    pl = pr + sr;  // slot 2 joins the right side
+                    sl = 2 * sr;
+                    sr = sl;
+                }
             }
             const unsigned idle = __ballot_sync(0xffffffffu, i < 0);
             if (next >= M && idle == 0xffffffffu) break;
@@ -391,38 +408,31 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerCta, 1) ksg_pruned_kernel(Ksg
                 const int g = next + __popc(idle & lt_mask);
                 if (i < 0 && g < M) {
                     i = (g & 1) ? M - 1 - (g >> 1) : (g >> 1);
-                    P = pack_f2(S[i]);
+                    const float2 pi = S[i];
+                    px = pi.x;
+                    P = pack_f2(pi);
 #pragma unroll
                     for (int c = 0; c < KK; ++c) b[c] = FLT_MAX;
                     pr = i + 1;
                     pl = i - 1;
-                    on_r = true;
-                    on_l = true;
+                    sr = 1;
+                    sl = -1;
+                    steps = 0;
                 }
                 next += __popc(idle);
             }
+            if (i >= 0) steps += kServiceSteps;
 #pragma unroll
             for (int st = 0; st < kServiceSteps; ++st) {
-                const bool act = on_r || on_l, both = on_r && on_l;
-                const int j1 = on_r ? pr : pl;
-                const int j2 = on_l ? (on_r ? pl : pl - 1) : pr + 1;
-                const float2 e1 = sub_f32x2(P, pack_f2(S[j1]));
-                const float2 e2 = sub_f32x2(P, pack_f2(S[j2]));
+                const float2 e1 = sub_f32x2(P, pack_f2(S[pr]));
+                const float2 e2 = sub_f32x2(P, pack_f2(S[pl]));
                 const float g1 = fabsf(e1.x), g2 = fabsf(e2.x);
                 const float t = b[KK - 1];
-                const float d1 = act ? fmaxf(g1, fabsf(e1.y)) : INFINITY;
-                const float d2 = act ? fmaxf(g2, fabsf(e2.y)) : INFINITY;
+                const float d1 = fmaxf(g1, fabsf(e1.y)), d2 = fmaxf(g2, fabsf(e2.y));
                 insert2<KK>(b, fminf(d1, d2), fmaxf(d1, d2));
                 // the pre-insert threshold makes the side test conservative (exact)
-                const bool go1 = act && g1 < t, go2 = act && g2 < t;
-                my_evals += (unsigned)go1 + (unsigned)go2;
-                const int adv = (int)go1 + (int)go2;  // one open side: g2 >= g1
-                pr += both ? (int)go1 : (on_r ? adv : 0);
-                pl -= both ? (int)go2 : (on_l ? adv : 0);
-                const bool nr = both ? go1 : (on_r && go2);
-                const bool nl = both ? go2 : (on_l && go2);
-                on_r = nr;
-                on_l = nl;
+                if (g1 < t) pr += sr;
+                if (g2 < t) pl += sl;
             }
         }
         __syncwarp();
