@@ -279,27 +279,36 @@ __global__ void __launch_bounds__(kKsgMaxThreads) ksg_volume_kernel(KsgArgs A) {
 }
 
 // ---------------------------------------------------------------- pruned volume
-// Exact pruned search, one warp per (reference, vertex) pair.  Work items are
-// taken from a global counter, so warps never wait for one another.  Within a
-// pair each lane scans one point at a time, outward in x-order; a side of the
-// scan stops at the first candidate whose x-gap reaches the point's current k-th
-// distance (self excluded: the list b holds the k nearest others, eps_i = b[k-1]).
-// Every later candidate on that side is at least that far in x, hence in the
-// max-norm, and an insert needs a strictly smaller distance; the threshold only
-// shrinks, so eps_i equals the brute-force value bit for bit.
+// Exact pruned search.  A group of kGroupWarps warps takes one (reference, vertex)
+// pair at a time from a global counter, so groups never wait for one another.
+// Within a pair each lane scans one point at a time, outward in x-order; a side of
+// the scan stops at the first candidate whose x-gap reaches the point's current
+// k-th distance (self excluded: the list b holds the k nearest others, eps_i =
+// b[k-1]).  Every later candidate on that side is at least that far in x, hence
+// in the max-norm, and an insert needs a strictly smaller distance; the threshold
+// only shrinks, so eps_i equals the brute-force value bit for bit.
 //
-// Each step takes two candidates, one per scan slot, and is branch-free: the point
-// array carries two sentinels at each end (x = -inf / +inf, an x-gap no threshold
-// passes), a closed slot re-reads a candidate beyond its threshold, and both
-// distances enter the list through one merge network.  A lane that has finished its point takes
-// the next one every kServiceSteps steps (a ballot hands them out, extremes of the
-// x distribution first: their scans are the longest).  The counts and the digamma
-// sum follow in an evenly split loop over the points.
+// Each step takes two candidates, one per scan slot, and is branch-free: the
+// point array carries two sentinels at each end (x = -inf / +inf, an x-gap no
+// threshold passes), a closed slot re-reads a candidate beyond its threshold, and
+// both distances enter the list through one merge network (measured 10% faster
+// than two single inserts).  Every kServiceSteps steps a lane whose point is done
+// stores eps and takes the next point from the group's counter (extremes of the x
+// distribution first: their scans are the longest).  The counts and the digamma
+// sum follow in an evenly split loop over the points.  The group's warps share
+// the pair's arrays (16 B x M), which sets how many warps fit on an SM.
 constexpr int kServiceSteps = 4;
-constexpr int kPad = 2;                                                 // sentinels per end
-constexpr int kWarpSmemPerM = sizeof(float2) + 2 * sizeof(float);       // pts, ys, eps
-constexpr int kWarpSmemFixed = 2 * kPad * sizeof(float2);
-constexpr int kMaxWarpsPerCta = 14;
+constexpr int kPad = 2;            // sentinels per end
+constexpr int kGroupWarps = 2;     // warps per pair
+constexpr int kMaxGroupsPerCta = 14;
+constexpr int kGroupSmemPerM = sizeof(float2) + 2 * sizeof(float);  // pts, ys, eps
+struct GroupCtl {
+    unsigned long long item;
+    int next;
+    int pad;
+    double part[kGroupWarps];
+};
+constexpr int kGroupSmemFixed = 2 * kPad * sizeof(float2) + sizeof(GroupCtl);
 
 // b ascending; inserts lo <= hi, keeping the KK smallest:
 // new b[p] = min(b[p], max(b[p-1], lo), max(b[p-2], hi))
@@ -328,43 +337,56 @@ __device__ __forceinline__ int count_within_x(const float2* a, int n, float c, f
     return hi > lo ? hi - lo : 0;
 }
 
+__device__ __forceinline__ void group_sync(int group) {
+    asm volatile("bar.sync %0, %1;" ::"r"(group + 1), "r"(32 * kGroupWarps) : "memory");
+}
+
 template <int K1>
-__global__ void __launch_bounds__(32 * kMaxWarpsPerCta, 1) ksg_pruned_kernel(KsgArgs A,
-                                                                             unsigned long long* work) {
+__global__ void __launch_bounds__(32 * kGroupWarps * kMaxGroupsPerCta, 1)
+    ksg_pruned_kernel(KsgArgs A, unsigned long long* work) {
     constexpr int KK = K1 - 1;
+    constexpr int GT = 32 * kGroupWarps;  // threads per group
     extern __shared__ __align__(16) unsigned char smem[];
     const int M = A.M, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nw = blockDim.x >> 5;
-    float2* S = reinterpret_cast<float2*>(smem) + (size_t)warp * (M + 2 * kPad) + kPad;
-    float* ys = reinterpret_cast<float*>(reinterpret_cast<float2*>(smem) + (size_t)nw * (M + 2 * kPad)) +
-                (size_t)warp * 2 * M;
+    const int group = warp / kGroupWarps, gw = warp % kGroupWarps, gt = threadIdx.x % GT;
+    const int ngroups = blockDim.x / GT;
+    GroupCtl* ctl = reinterpret_cast<GroupCtl*>(smem) + group;
+    float2* S = reinterpret_cast<float2*>(reinterpret_cast<GroupCtl*>(smem) + ngroups) +
+                (size_t)group * (M + 2 * kPad) + kPad;
+    float* ys = reinterpret_cast<float*>(reinterpret_cast<float2*>(reinterpret_cast<GroupCtl*>(smem) +
+                                                                   ngroups) +
+                                         (size_t)ngroups * (M + 2 * kPad)) +
+                (size_t)group * 2 * M;
     float* epsw = ys + M;
     const int64_t N = A.N, nv = A.v_end - A.v_begin;
     const unsigned long long items = (unsigned long long)A.R * (unsigned long long)nv;
     const double psi_k = A.psi[A.k], psi_M = A.psi[M];
     const unsigned lt_mask = (1u << lane) - 1u;
-    if (lane < kPad) {
-        S[-1 - lane] = make_float2(-INFINITY, 0.0f);
-        S[M + lane] = make_float2(INFINITY, 0.0f);
+    if (gt < kPad) {
+        S[-1 - gt] = make_float2(-INFINITY, 0.0f);
+        S[M + gt] = make_float2(INFINITY, 0.0f);
     }
     unsigned my_evals = 0;
     unsigned long long evals_total = 0;
 
     for (;;) {
-        unsigned long long item = 0;
-        if (lane == 0) item = atomicAdd(work, 1ull);
-        item = __shfl_sync(0xffffffffu, item, 0);
+        group_sync(group);  // the previous pair is finished by both warps
+        if (gt == 0) {
+            ctl->item = atomicAdd(work, 1ull);
+            ctl->next = 0;
+        }
+        group_sync(group);
+        const unsigned long long item = ctl->item;
         if (item >= items) break;
         const int r = (int)(item / (unsigned long long)nv);
         const int64_t v = A.v_begin + (int64_t)(item - (unsigned long long)r * nv);
         const float* xs = A.xs_all + (int64_t)r * M;
         const int* perm = A.perm_all + (int64_t)r * M;
-        __syncwarp();  // the previous pair's reads are done
-        for (int s = lane; s < M; s += 32) {
+        for (int s = gt; s < M; s += GT) {
             S[s] = make_float2(xs[s], A.field[(int64_t)perm[s] * N + v]);
             ys[s] = A.sorted[(int64_t)s * N + v];
         }
-        __syncwarp();
+        group_sync(group);
 
         // ---- joint k-NN distances.  Two scan slots per lane, each a position and a
         // stride: slot 1 starts right of the point (+1), slot 2 left (-1).  A slot
@@ -374,7 +396,8 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerCta, 1) ksg_pruned_kernel(Ksg
         // other side (the two slots then interleave with stride 2), a lane whose
         // both sides have closed stores eps and takes a new point.  Idle lanes point
         // both slots at sentinels.
-        int i = -1, next = 0, pr = M, pl = -1, sr = 1, sl = -1;
+        int i = -1, pr = M, pl = -1, sr = 1, sl = -1;
+        bool drained = false;  // the group's counter has passed M
         unsigned steps = 0;
         float px = 0.0f;
         unsigned long long P = 0;
@@ -403,9 +426,12 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerCta, 1) ksg_pruned_kernel(Ksg
                 }
             }
             const unsigned idle = __ballot_sync(0xffffffffu, i < 0);
-            if (next >= M && idle == 0xffffffffu) break;
-            if (next < M && idle != 0u) {
-                const int g = next + __popc(idle & lt_mask);
+            if (drained && idle == 0xffffffffu) break;
+            if (!drained && idle != 0u) {
+                int base = 0;
+                if (lane == 0) base = atomicAdd(&ctl->next, __popc(idle));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                const int g = base + __popc(idle & lt_mask);
                 if (i < 0 && g < M) {
                     i = (g & 1) ? M - 1 - (g >> 1) : (g >> 1);
                     const float2 pi = S[i];
@@ -419,7 +445,7 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerCta, 1) ksg_pruned_kernel(Ksg
                     sl = -1;
                     steps = 0;
                 }
-                next += __popc(idle);
+                drained = base + __popc(idle) >= M;
             }
             if (i >= 0) steps += kServiceSteps;
 #pragma unroll
@@ -435,12 +461,12 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerCta, 1) ksg_pruned_kernel(Ksg
                 if (g2 < t) pl += sl;
             }
         }
-        __syncwarp();
+        group_sync(group);  // every eps of the pair is stored
 
         // ---- marginal counts and the digamma sum
         const bool dbg = A.dbg_eps && r == 0 && v == A.v_begin;
         double acc = 0.0;
-        for (int s = lane; s < M; s += 32) {
+        for (int s = gt; s < M; s += GT) {
             const float e = epsw[s];
             const float2 ps = S[s];
             const int self = e > 0.0f ? 1 : 0;
@@ -456,8 +482,13 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerCta, 1) ksg_pruned_kernel(Ksg
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) {
-            const double mi = psi_k + psi_M - acc / (double)M;
+        if (lane == 0) ctl->part[gw] = acc;
+        group_sync(group);
+        if (gt == 0) {
+            double tot = 0.0;
+#pragma unroll
+            for (int w = 0; w < kGroupWarps; ++w) tot += ctl->part[w];
+            const double mi = psi_k + psi_M - tot / (double)M;
             A.out[(int64_t)r * A.out_stride + (v - A.v_begin)] = (float)mi;
             if (dbg && A.dbg_mi) *A.dbg_mi = mi;
         }
@@ -491,12 +522,13 @@ template <int K1>
 static cudaError_t launch_ksg_k(ndf_ctx* ctx, KsgArgs A, bool prune) {
     const int M = A.M;
     if (prune) {
-        // one warp per pair; as many warps per CTA as fit in shared memory
-        const size_t per_warp = (size_t)kWarpSmemPerM * M + kWarpSmemFixed;
-        int wpc = (int)((227 * 1024) / per_warp);
-        if (wpc > kMaxWarpsPerCta) wpc = kMaxWarpsPerCta;
-        if (wpc < 1) wpc = 1;
-        const size_t smem = (size_t)wpc * per_warp;
+        // one warp group per pair; as many groups per CTA as fit in shared memory
+        const size_t per_group = (size_t)kGroupSmemPerM * M + kGroupSmemFixed;
+        int gpc = (int)((227 * 1024) / per_group);
+        if (gpc > kMaxGroupsPerCta) gpc = kMaxGroupsPerCta;
+        if (gpc < 1) gpc = 1;
+        const size_t smem = (size_t)gpc * per_group;
+        const int threads = 32 * kGroupWarps * gpc;
         cudaError_t e = ctx->ksg_work.reserve(sizeof(unsigned long long));
         if (e == cudaSuccess)
             e = cudaMemsetAsync(ctx->ksg_work.ptr, 0, sizeof(unsigned long long), ctx->stream);
@@ -505,13 +537,13 @@ static cudaError_t launch_ksg_k(ndf_ctx* ctx, KsgArgs A, bool prune) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * wpc, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
         const int64_t pairs = (int64_t)A.R * (A.v_end - A.v_begin);
         int64_t grid = (int64_t)ctx->sm_count * per_sm;
-        if (grid * wpc > pairs) grid = (pairs + wpc - 1) / wpc;
-        kern<<<(unsigned)grid, 32 * wpc, smem, ctx->stream>>>(
+        if (grid * gpc > pairs) grid = (pairs + gpc - 1) / gpc;
+        kern<<<(unsigned)grid, threads, smem, ctx->stream>>>(
             A, ctx->ksg_work.as<unsigned long long>());
         ctx->launches++;
         return cudaGetLastError();
