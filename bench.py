@@ -475,13 +475,18 @@ def main():
     host_r = torch.empty(N, dtype=torch.float32, pin_memory=True)
     host_mi = torch.empty(N, dtype=torch.float32, pin_memory=True)
     e2e_steps = max(1, min(args.e2e_steps, args.steps))
+
+    def e2e_volume(ref):
+        fid2 = ndf.ndf_load_ensemble(ctx, field_t, M, Z, Y, X)
+        ndf.ndf_pearson(ctx, fid2, fid2, ref, host_r)
+        ndf.ndf_mi_ksg(ctx, fid2, fid2, ref, K_NN, host_mi)
+        ndf.ndf_free_ensemble(ctx, fid2)
+
+    e2e_volume(refs[0])  # warm-up: first-touch of the second field's device pages
     barrier()
     t0 = time.perf_counter()
     for i in range(e2e_steps):
-        fid2 = ndf.ndf_load_ensemble(ctx, field_t, M, Z, Y, X)
-        ndf.ndf_pearson(ctx, fid2, fid2, refs[args.warmup + i], host_r)
-        ndf.ndf_mi_ksg(ctx, fid2, fid2, refs[args.warmup + i], K_NN, host_mi)
-        ndf.ndf_free_ensemble(ctx, fid2)
+        e2e_volume(refs[args.warmup + i])
     barrier()
     e2e_ms = max_over_ranks([(time.perf_counter() - t0) * 1e3], world, "cuda")[0]
     e2e_per_volume = job_ms_per_volume(e2e_ms, e2e_steps, world)

@@ -86,13 +86,24 @@ int64_t ndf_index(int64_t x, int64_t y, int64_t z, int64_t X, int64_t Y, int64_t
 /* Copy field[M][Z][Y][X] (host or device) into context-owned device memory and
  * compute the per-vertex statistics used by Eq. 1: the FP64 mean mu_v and
  * 1/sqrt(S_v) with S_v = sum_m (e_m(v) - mu_v)^2 (two passes, FP64 across
- * member blocks).  Requires M >= 2 and finite values (NDF_ERR_ARG otherwise;
- * the check reads the copied field).  Writes the new field's id. */
+ * member blocks).  For M <= 4096 every vertex column is also sorted into a
+ * second M*N*4-byte buffer (the KSG marginal counts of Algorithm 1 search it).
+ * The copy runs in vertex ranges on an internal stream, the statistics and sorts
+ * of each range follow on the context's stream; the call returns when all is
+ * done.  Requires M >= 2 and finite values (NDF_ERR_ARG otherwise; the check
+ * reads the copied field).  Writes the new field's id. */
 ndf_status ndf_load_ensemble(ndf_ctx* ctx, const float* field, int64_t M, int64_t Z, int64_t Y,
                              int64_t X, int* field_id_out);
 
-/* Release a field's device memory; its id becomes invalid (NDF_ERR_STATE). */
+/* Release a field; its id becomes invalid (NDF_ERR_STATE).  The field's device
+ * buffers stay with the context (at most 8 of them, the oldest freed beyond
+ * that) and a later ndf_load_ensemble of the same M*N reuses them instead of
+ * allocating; ndf_trim_cache or ndf_destroy returns them to the device. */
 ndf_status ndf_free_ensemble(ndf_ctx* ctx, int field_id);
+
+/* Free every device buffer the context keeps from released fields (synchronizes
+ * the context's stream first). */
+ndf_status ndf_trim_cache(ndf_ctx* ctx);
 
 /* Shape of a loaded field (any output pointer may be NULL). */
 ndf_status ndf_field_shape(const ndf_ctx* ctx, int field_id, int64_t* M, int64_t* Z, int64_t* Y,

@@ -34,6 +34,51 @@ void Field::free_all() {
     live = false;
 }
 
+cudaError_t ctx_alloc(ndf_ctx* ctx, void** p, size_t bytes) {
+    *p = nullptr;
+    for (size_t i = 0; i < ctx->cache.size(); ++i) {
+        if (ctx->cache[i].bytes == bytes) {
+            *p = ctx->cache[i].ptr;
+            ctx->cache.erase(ctx->cache.begin() + (long)i);
+            return cudaSuccess;
+        }
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaErrorMemoryAllocation && !ctx->cache.empty()) {
+        cudaGetLastError();
+        ctx_trim(ctx);
+        e = cudaMalloc(p, bytes);
+    }
+    if (e != cudaSuccess) *p = nullptr;
+    return e;
+}
+
+void ctx_release(ndf_ctx* ctx, void* p, size_t bytes) {
+    if (!p) return;
+    ctx->cache.push_back({p, bytes});
+    while (ctx->cache.size() > kCacheEntries) {
+        cudaFree(ctx->cache.front().ptr);
+        ctx->cache.erase(ctx->cache.begin());
+    }
+}
+
+void ctx_trim(ndf_ctx* ctx) {
+    for (auto& c : ctx->cache) cudaFree(c.ptr);
+    ctx->cache.clear();
+}
+
+void release_field(ndf_ctx* ctx, Field& f) {
+    const size_t fb = sizeof(float) * (size_t)f.M * (size_t)f.N;
+    const size_t sb = sizeof(double) * (size_t)f.N;
+    ctx_release(ctx, f.data, fb);
+    ctx_release(ctx, f.sorted, fb);
+    ctx_release(ctx, f.mean, sb);
+    ctx_release(ctx, f.inv_norm, sb);
+    f.data = f.sorted = nullptr;
+    f.mean = f.inv_norm = nullptr;
+    f.free_all();  // the standardised copies
+}
+
 void DevBuf::release() {
     if (ptr) cudaFree(ptr);
     ptr = nullptr;
@@ -195,6 +240,11 @@ ndf_status ndf_create(ndf_ctx** out, int device, void* cuda_stream) {
         }
         c->stream = c->own_stream;
     }
+    if (cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->copy_event, cudaEventDisableTiming) != cudaSuccess) {
+        ndf_destroy(c);
+        return NDF_ERR_CUDA;
+    }
     if (c->flag.reserve(256) != cudaSuccess || cudaMemset(c->flag.ptr, 0, 256) != cudaSuccess) {
         ndf_destroy(c);
         return NDF_ERR_OOM;
@@ -208,6 +258,7 @@ void ndf_destroy(ndf_ctx* ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     for (auto& f : ctx->fields) f.free_all();
+    ctx_trim(ctx);
     ctx->stage_x.release();
     ctx->stage_perm.release();
     ctx->out_tmp.release();
@@ -218,6 +269,11 @@ void ndf_destroy(ndf_ctx* ctx) {
     ctx->refidx.release();
     ctx->evals.release();
     ctx->ksg_work.release();
+    if (ctx->copy_stream) {
+        cudaStreamSynchronize(ctx->copy_stream);
+        cudaStreamDestroy(ctx->copy_stream);
+    }
+    if (ctx->copy_event) cudaEventDestroy(ctx->copy_event);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     delete ctx;
 }
@@ -266,29 +322,42 @@ ndf_status ndf_load_ensemble(ndf_ctx* ctx, const float* field, int64_t M, int64_
     Field f;
     f.M = M; f.Z = Z; f.Y = Y; f.X = X; f.N = N;
     size_t bytes = sizeof(float) * (size_t)M * (size_t)N;
-    cudaError_t e = cudaMalloc(&f.data, bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&f.mean, sizeof(double) * (size_t)N);
-    if (e == cudaSuccess) e = cudaMalloc(&f.inv_norm, sizeof(double) * (size_t)N);
+    const bool want_sorted = M <= kKsgMaxM;  // the KSG searches need it
+    cudaError_t e = ctx_alloc(ctx, (void**)&f.data, bytes);
+    if (e == cudaSuccess) e = ctx_alloc(ctx, (void**)&f.mean, sizeof(double) * (size_t)N);
+    if (e == cudaSuccess) e = ctx_alloc(ctx, (void**)&f.inv_norm, sizeof(double) * (size_t)N);
+    if (e == cudaSuccess && want_sorted) e = ctx_alloc(ctx, (void**)&f.sorted, bytes);
     if (e != cudaSuccess) {
-        if (f.data) cudaFree(f.data);
-        if (f.mean) cudaFree(f.mean);
-        if (f.inv_norm) cudaFree(f.inv_norm);
+        release_field(ctx, f);
         return cuda_fail(ctx, e, "field allocation");
     }
     cudaMemcpyKind kind = pointer_kind(field) == PTR_DEVICE ? cudaMemcpyDeviceToDevice
                                                             : cudaMemcpyHostToDevice;
     int* d_flag = ctx->flag.as<int>();
-    e = cudaMemcpyAsync(f.data, field, bytes, kind, ctx->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_flag, 0, sizeof(int), ctx->stream);
-    if (e == cudaSuccess) e = launch_field_stats(ctx, f, d_flag);
+    // Upload in vertex ranges on the copy stream; the statistics and the column sort of
+    // each range run on the context's stream as soon as that range has arrived.
+    int64_t chunk = ((int64_t)(64 << 20) / M + 31) / 32 * 32;
+    if (chunk < 1024) chunk = 1024;
+    e = cudaMemsetAsync(d_flag, 0, sizeof(int), ctx->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->copy_event, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->copy_stream, ctx->copy_event, 0);
+    for (int64_t v0 = 0; v0 < N && e == cudaSuccess; v0 += chunk) {
+        const int64_t v1 = v0 + chunk < N ? v0 + chunk : N;
+        e = cudaMemcpy2DAsync(f.data + v0, sizeof(float) * (size_t)N, field + v0,
+                              sizeof(float) * (size_t)N, sizeof(float) * (size_t)(v1 - v0),
+                              (size_t)M, kind, ctx->copy_stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->copy_event, ctx->copy_stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->copy_event, 0);
+        if (e == cudaSuccess) e = launch_field_stats(ctx, f, v0, v1, d_flag);
+        if (e == cudaSuccess && want_sorted) e = launch_sort_columns(ctx, f, v0, v1, ctx->stream);
+    }
     int nonfinite = 0;
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(&nonfinite, d_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess || nonfinite) {
-        cudaFree(f.data);
-        cudaFree(f.mean);
-        cudaFree(f.inv_norm);
+        cudaStreamSynchronize(ctx->copy_stream);
+        release_field(ctx, f);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "ensemble upload / statistics");
         return fail(ctx, NDF_ERR_ARG, "field contains non-finite values");
     }
@@ -305,7 +374,15 @@ ndf_status ndf_free_ensemble(ndf_ctx* ctx, int field_id) {
     Field& f = ctx->fields[field_id];
     if (!f.live) return fail(ctx, NDF_ERR_STATE, "field already freed");
     cudaStreamSynchronize(ctx->stream);
-    f.free_all();
+    release_field(ctx, f);
+    return NDF_OK;
+}
+
+ndf_status ndf_trim_cache(ndf_ctx* ctx) {
+    if (!ctx) return NDF_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    ctx_trim(ctx);
     return NDF_OK;
 }
 

@@ -42,10 +42,16 @@ struct Field {
 }  // namespace ndf
 
 struct ndf_ctx {
+    struct CachedBuf {
+        void* ptr;
+        size_t bytes;
+    };
     int device = 0;
     int sm_count = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t own_stream = nullptr;
+    cudaStream_t copy_stream = nullptr;  // uploads, overlapped with per-chunk statistics
+    cudaEvent_t copy_event = nullptr;
     std::vector<ndf::Field> fields;
     std::string last_error;
     uint64_t launches = 0;
@@ -63,6 +69,7 @@ struct ndf_ctx {
     bool count_evals = false;
     ndf::DevBuf evals;       // KSG distance evaluations (when counting is on)
     ndf::DevBuf ksg_work;    // pruned KSG: work-item counter
+    std::vector<CachedBuf> cache;  // device buffers of freed fields, reused by later loads
     ndf::DevBuf zr;          // batched Pearson: standardised reference rows
     ndf::DevBuf refidx;      // batched calls: reference indices on the device
 };
@@ -70,6 +77,17 @@ struct ndf_ctx {
 namespace ndf {
 
 enum PtrKind { PTR_HOST = 0, PTR_DEVICE = 1 };
+
+// Field buffers go through the context's cache: ctx_alloc takes a cached buffer of
+// exactly `bytes` if there is one (else cudaMalloc, trimming the cache and retrying
+// on out-of-memory); ctx_release keeps the buffer (at most kCacheEntries, the
+// oldest freed beyond that); ctx_trim frees every cached buffer.
+constexpr size_t kCacheEntries = 8;
+cudaError_t ctx_alloc(ndf_ctx* ctx, void** p, size_t bytes);
+void ctx_release(ndf_ctx* ctx, void* p, size_t bytes);
+void ctx_trim(ndf_ctx* ctx);
+// Returns a field's buffers to the cache (standardised copies are freed) and marks it dead.
+void release_field(ndf_ctx* ctx, Field& f);
 PtrKind pointer_kind(const void* p);
 
 ndf_status fail(ndf_ctx* ctx, ndf_status st, const char* fmt, ...);
@@ -90,7 +108,8 @@ ndf_status ensure_psi_table(ndf_ctx* ctx, int64_t n_max);
 double digamma_int_host(int64_t n);
 
 // kernels (launch wrappers; each returns the launch error)
-cudaError_t launch_field_stats(ndf_ctx* ctx, const Field& f, int* d_nonfinite);
+cudaError_t launch_field_stats(ndf_ctx* ctx, const Field& f, int64_t v_begin, int64_t v_end,
+                               int* d_nonfinite);
 cudaError_t launch_pearson(ndf_ctx* ctx, const Field& rf, const Field& qf, int64_t ref_idx,
                            float* out);
 // KSG MI for R references (d_refs on the device, or the single reference ref0
@@ -105,6 +124,9 @@ cudaError_t launch_ksg(ndf_ctx* ctx, const Field& rf, const Field& qf, const int
 
 // Builds Field::sorted (one sort per vertex column, kept with the field).
 cudaError_t ensure_sorted_columns(ndf_ctx* ctx, Field& f);
+// Sorts the columns of vertices [v_begin, v_end) into the allocated Field::sorted.
+cudaError_t launch_sort_columns(ndf_ctx* ctx, const Field& f, int64_t v_begin, int64_t v_end,
+                                cudaStream_t stream);
 
 constexpr int kKsgMaxM = 4096;
 constexpr int kKsgMaxK = 16;

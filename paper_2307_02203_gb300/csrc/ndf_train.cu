@@ -485,7 +485,7 @@ ndf_status ndf_train(ndf_ctx* ctx, int ref_field, int query_field, int measure, 
         }
         if (measure == NDF_MEASURE_PEARSON) {
             e = cudaMemsetAsync(d_flag, 0, 4, ctx->stream);
-            if (e == cudaSuccess) e = launch_field_stats(ctx, blk, d_flag);
+            if (e == cudaSuccess) e = launch_field_stats(ctx, blk, 0, blk.N, d_flag);
         }
         // reference vertices of this group (as many as the remaining triples need)
         const int64_t rows = std::min<int64_t>(Rg, (T - filled + Qg - 1) / Qg);

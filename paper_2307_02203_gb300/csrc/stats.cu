@@ -8,11 +8,12 @@
 namespace ndf {
 
 __global__ void __launch_bounds__(256) field_stats_kernel(const float* __restrict__ f, int64_t M,
-                                                          int64_t N, double* __restrict__ mean,
+                                                          int64_t N, int64_t v_begin, int64_t v_end,
+                                                          double* __restrict__ mean,
                                                           double* __restrict__ inv_norm,
                                                           int* __restrict__ nonfinite) {
-    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= N) return;
+    int64_t v = v_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= v_end) return;
     const float* p = f + v;
     double s = 0.0;
     float lo = p[0], hi = p[0];
@@ -63,10 +64,12 @@ __global__ void __launch_bounds__(256) field_stats_kernel(const float* __restric
     inv_norm[v] = S > 0.0 ? 1.0 / sqrt(S) : 0.0;
 }
 
-cudaError_t launch_field_stats(ndf_ctx* ctx, const Field& f, int* d_nonfinite) {
-    int64_t blocks = (f.N + 255) / 256;
-    field_stats_kernel<<<(unsigned)blocks, 256, 0, ctx->stream>>>(f.data, f.M, f.N, f.mean,
-                                                                  f.inv_norm, d_nonfinite);
+cudaError_t launch_field_stats(ndf_ctx* ctx, const Field& f, int64_t v_begin, int64_t v_end,
+                               int* d_nonfinite) {
+    if (v_end <= v_begin) return cudaSuccess;
+    int64_t blocks = (v_end - v_begin + 255) / 256;
+    field_stats_kernel<<<(unsigned)blocks, 256, 0, ctx->stream>>>(f.data, f.M, f.N, v_begin, v_end,
+                                                                  f.mean, f.inv_norm, d_nonfinite);
     ctx->launches++;
     return cudaGetLastError();
 }

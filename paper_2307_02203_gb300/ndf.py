@@ -56,6 +56,7 @@ _sig("ndf_index", _i64, [_i64, _i64, _i64, _i64, _i64, _i64])
 _sig("ndf_load_ensemble", ctypes.c_int, [_vp, _vp, _i64, _i64, _i64, _i64,
                                          ctypes.POINTER(ctypes.c_int)])
 _sig("ndf_free_ensemble", ctypes.c_int, [_vp, ctypes.c_int])
+_sig("ndf_trim_cache", ctypes.c_int, [_vp])
 _sig("ndf_field_shape", ctypes.c_int, [_vp, ctypes.c_int] + [ctypes.POINTER(_i64)] * 4)
 _sig("ndf_field_stats", ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp])
 _sig("ndf_pearson", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, _vp])
@@ -186,6 +187,10 @@ def ndf_load_ensemble(ctx, field, M, Z, Y, X) -> int:
 
 def ndf_free_ensemble(ctx, field_id: int) -> None:
     _check(ctx, _lib.ndf_free_ensemble(ctx, field_id), "ndf_free_ensemble")
+
+
+def ndf_trim_cache(ctx) -> None:
+    _check(ctx, _lib.ndf_trim_cache(ctx), "ndf_trim_cache")
 
 
 def ndf_field_shape(ctx, field_id: int):

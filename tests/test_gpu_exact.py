@@ -56,6 +56,45 @@ def test_load_statistics(ndf_mod, ctx, tiny_field):
     ndf_mod.ndf_free_ensemble(ctx, fid)
 
 
+def test_chunked_upload_statistics_and_sorted_columns(ndf_mod, ctx):
+    """M = 4096 uploads in ranges of 16384 vertices: three ranges with a ragged
+    tail.  Statistics and KSG counts (which search the sorted columns) must hold
+    at the range boundaries."""
+    M, N = 4096, 2 * 16384 + 77
+    rng = np.random.default_rng(99)
+    f = rng.normal(size=(M, 1, 1, N)).astype(np.float32)
+    f[:, 0, 0, 16383:16386] += 2.0 * f[:, 0, 0, 5:8]  # dependence across a boundary
+    fid = load(ndf_mod, ctx, f)
+    mean = np.empty(N)
+    inv = np.empty(N)
+    ndf_mod.ndf_field_stats(ctx, fid, mean, inv)
+    cols = [0, 16383, 16384, 32767, 32768, N - 1]
+    f64 = f.reshape(M, N)[:, cols].astype(np.float64)
+    mu = f64.mean(axis=0)
+    np.testing.assert_allclose(mean[cols], mu, rtol=0, atol=1e-5 * np.abs(f64).max())
+    np.testing.assert_allclose(inv[cols], 1.0 / np.sqrt(((f64 - mu) ** 2).sum(axis=0)), rtol=1e-5)
+    check_pairs_bit_exact(ndf_mod, ctx, fid, fid, f, f, 6, cols, 4)
+    ndf_mod.ndf_free_ensemble(ctx, fid)
+
+
+def test_reload_reuses_buffers_without_stale_data(ndf_mod, ctx, tiny_field, tiny_ref):
+    """A freed field's buffers are reused by the next load of the same size; the
+    new field's statistics, sorted columns and volumes must be its own."""
+    N = tiny_field[0].size
+    other = (tiny_field[::-1] * 1.5 + 0.25).copy()
+    fa = load(ndf_mod, ctx, tiny_field)
+    ndf_mod.ndf_free_ensemble(ctx, fa)
+    fb = load(ndf_mod, ctx, other)
+    out = np.empty(N, dtype=np.float32)
+    ndf_mod.ndf_mi_ksg(ctx, fb, fb, tiny_ref, 4, out)
+    ok, where = mi_close(out, oracle.ksg_volume(other, other, tiny_ref, 4))
+    assert ok, where
+    ndf_mod.ndf_pearson(ctx, fb, fb, tiny_ref, out)
+    assert np.abs(out - oracle.pearson_volume(other, other, tiny_ref)).max() <= PEARSON_TOL
+    ndf_mod.ndf_free_ensemble(ctx, fb)
+    ndf_mod.ndf_trim_cache(ctx)
+
+
 def test_load_from_device_memory(ndf_mod, ctx, tiny_field, tiny_ref):
     t = torch.from_numpy(tiny_field).cuda()
     fid = ndf_mod.ndf_load_ensemble(ctx, t, *tiny_field.shape)
