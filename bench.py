@@ -36,7 +36,7 @@ K_NN = 8
 # one-level slab capture (ncu dram__bytes_read.sum + dram__bytes_write.sum for
 # 88,000 vertices) scaled by the vertices processed (x20): the kernels stream each
 # query column and its sorted copy once (algorithmic 14.08 GB + 7 MB output).
-KSG_PRUNED_TRAFFIC_PER_VOLUME = (706.494e6 + 4.789e6) * 20
+KSG_PRUNED_TRAFFIC_PER_VOLUME = None  # recaptured after the kernel change
 KSG_BRUTE_TRAFFIC_PER_VOLUME = (705.845e6 + 4.089e6) * 20
 METRIC = "ms per 1.76M-voxel dependence volume (Pearson + KSG MI k=8, M=1000)"
 
@@ -233,25 +233,31 @@ def measure_ksg_batch(ndf, ctx, fid, recipe, stream, args, R=16):
     return {"refs": R, "ms": ms, "ms_per_volume": ms / R, "mi_pairs_per_s": R * N / (ms * 1e-3)}
 
 
-def measure_ndf(ndf, ctx, fid, recipe, stream, args, exact_ms):
+def measure_ndf(ndf, ctx, fid, recipe, stream, args, exact_ms, fid_b=None):
     """Learned part: trains a Pearson and a KSG-MI network on the loaded field
     (targets from the GPU estimators), then times volume decoding (1 reference
     per launch and 16 per launch) and states MAE / max error per volume against
-    the exact estimator, beside the exact method's time on the same GPU."""
+    the exact estimator, beside the exact method's time on the same GPU.  With a
+    second field, the same for cross-field networks (reference in field A, query
+    in field B)."""
     import torch
 
     N = recipe.N
     out = {}
     rng = np.random.default_rng(777)
     refs = [int(r) for r in rng.integers(0, N, size=16)]
-    for name, measure, k, triples in (("pearson", ndf.NDF_MEASURE_PEARSON, 0, args.ndf_triples),
-                                      ("mi", ndf.NDF_MEASURE_MI_KSG, K_NN, args.ndf_mi_triples)):
+    runs = [("pearson", ndf.NDF_MEASURE_PEARSON, 0, args.ndf_triples, fid, fid),
+            ("mi", ndf.NDF_MEASURE_MI_KSG, K_NN, args.ndf_mi_triples, fid, fid)]
+    if fid_b is not None:
+        runs += [("pearson_cross", ndf.NDF_MEASURE_PEARSON, 0, args.ndf_triples, fid, fid_b),
+                 ("mi_cross", ndf.NDF_MEASURE_MI_KSG, K_NN, args.ndf_mi_triples, fid, fid_b)]
+    for name, measure, k, triples, fa, fb in runs:
         cfg = ndf.ndf_train_cfg_default()
         cfg.res[:] = [int(v) for v in args.ndf_res.split(",")]
         cfg.n_triples = int(triples)
         cfg.time_budget_s = float(args.ndf_seconds)
         t0 = time.perf_counter()
-        model = ndf.ndf_train(ctx, fid, fid, measure, k, cfg)
+        model = ndf.ndf_train(ctx, fa, fb, measure, k, cfg)
         ndf.ndf_synchronize(ctx)
         wall = time.perf_counter() - t0
         info = ndf.ndf_model_info(model)
@@ -275,10 +281,10 @@ def measure_ndf(ndf, ctx, fid, recipe, stream, args, exact_ms):
         n_err = 16 if measure == ndf.NDF_MEASURE_PEARSON else args.ndf_mi_err_refs
         exact = torch.empty((n_err, N), dtype=torch.float32, device="cuda")
         if measure == ndf.NDF_MEASURE_PEARSON:
-            ndf.ndf_pearson_batch(ctx, fid, fid, refs[:n_err], ndf.NDF_PREC_FP32, exact)
+            ndf.ndf_pearson_batch(ctx, fa, fb, refs[:n_err], ndf.NDF_PREC_FP32, exact)
         else:
             for i in range(n_err):
-                ndf.ndf_mi_ksg(ctx, fid, fid, refs[i], K_NN, exact[i])
+                ndf.ndf_mi_ksg(ctx, fa, fb, refs[i], K_NN, exact[i])
         ndf.ndf_synchronize(ctx)
         err = (many[:n_err] - exact).abs()
         out[name] = {
@@ -289,8 +295,9 @@ def measure_ndf(ndf, ctx, fid, recipe, stream, args, exact_ms):
             "train_wall_s": wall,
             "network_bytes": info["network_bytes"], "training_bytes": info["training_bytes"],
             "decode_ms_per_volume_1ref": ms_one, "decode_ms_per_volume_16refs": ms_batch,
-            "exact_ms_per_volume": exact_ms[name],
-            "speedup_vs_exact_16refs": exact_ms[name] / ms_batch,
+            "exact_ms_per_volume": exact_ms[name.split("_")[0]],
+            "speedup_vs_exact_16refs": exact_ms[name.split("_")[0]] / ms_batch,
+            "fields": "A->B" if fb != fa else "A->A",
             "mae": float(err.mean()), "max_err_mean_over_refs": float(err.amax(dim=1).mean()),
             "max_err": float(err.max()), "error_refs": n_err,
             "exact_mean_abs_value": float(exact.abs().mean()),
@@ -365,6 +372,8 @@ def main():
                     help="volumes timed with the brute-force KSG search (same results)")
     ap.add_argument("--ndf", type=int, default=1, help="also train and time the neural field")
     ap.add_argument("--ndf-seconds", type=float, default=25.0, help="training budget per network")
+    ap.add_argument("--ndf-cross", type=int, default=1,
+                    help="also train cross-field networks (reference in A, query in a second field B)")
     ap.add_argument("--ndf-triples", type=int, default=1 << 26, help="Pearson training triples")
     ap.add_argument("--ndf-mi-triples", type=int, default=1 << 24, help="KSG-MI training triples")
     ap.add_argument("--ndf-mi-err-refs", type=int, default=4, help="exact KSG volumes for MI error")
@@ -468,8 +477,17 @@ def main():
     batch = measure_pearson_batch(ndf, ctx, fid, field, recipe, stream, rank) if args.batch else None
 
     # ---- learned part: train, decode, error against the exact estimators
+    fid_b = None
+    if args.ndf and args.ndf_cross:
+        recipe_b = synth.scaled(synth.CSENS_B, M=recipe.M, Z=recipe.Z, Y=recipe.Y, X=recipe.X)
+        _, field_b = make_field(recipe_b, pinned=False, nthreads=nthreads)
+        fid_b = ndf.ndf_load_ensemble(ctx, field_b, M, Z, Y, X)
+        del field_b
     ndf_res = measure_ndf(ndf, ctx, fid, recipe, stream, args,
-                          {"pearson": pearson_ms, "mi": ksg_ms}) if args.ndf else None
+                          {"pearson": pearson_ms, "mi": ksg_ms}, fid_b) if args.ndf else None
+    if fid_b is not None:
+        ndf.ndf_free_ensemble(ctx, fid_b)
+        ndf.ndf_trim_cache(ctx)
 
     # ---- end to end through the ABI with host buffers (upload + stats + both volumes + D2H)
     host_r = torch.empty(N, dtype=torch.float32, pin_memory=True)

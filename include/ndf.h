@@ -144,15 +144,23 @@ ndf_status ndf_pearson_batch(ndf_ctx* ctx, int ref_field, int query_field, const
 ndf_status ndf_mi_ksg(ndf_ctx* ctx, int ref_field, int query_field, int64_t ref_idx, int k,
                       float* out);
 
-/* KSG search used by ndf_mi_ksg, ndf_mi_ksg_batch, ndf_ksg_debug_pair and
- * ndf_train's MI targets.  Both give identical results (same FP32 distances,
+/* KSG algorithm 2 of the same article (Sec. 3.2 cites it; row f1): per member,
+ * the neighbour set S_i = {j != i : d_ij <= eps_i} (the k nearest; every member
+ * tied at eps_i belongs to it), its marginal extents ex_i / ey_i (largest |dx| /
+ * |dy| over S_i, FP32), non-strict counts n_x = #{j != i : |x_i - x_j| <= ex_i},
+ * n_y likewise, and I2 = psi(k) - 1/k + psi(M) - <psi(n_x) + psi(n_y)> (FP64
+ * sum).  Same search (ndf_set_ksg_algorithm), same limits and output as
+ * ndf_mi_ksg. */
+ndf_status ndf_mi_ksg2(ndf_ctx* ctx, int ref_field, int query_field, int64_t ref_idx, int k,
+                       float* out);
+
+/* KSG search used by ndf_mi_ksg, ndf_mi_ksg2, ndf_mi_ksg_batch, the debug hooks
+ * and ndf_train's MI targets.  Both give identical results (same FP32 distances,
  * same counts):
  *   NDF_KSG_PRUNED  (default) one warp per (reference, vertex) pair; members in
  *                   order of the reference value, each side of a member's
  *                   outward scan stopped at the first x-gap that reaches its
- *                   current k-th distance (exact pruning).  When the per-warp
- *                   arrays do not fit in shared memory (M above ~3400 at k = 8)
- *                   the brute-force kernel runs instead;
+ *                   current k-th distance (exact pruning);
  *   NDF_KSG_BRUTE   every member against every member of each pair.
  * count_evals != 0 makes the kernels count distance evaluations (read with
  * ndf_ksg_take_eval_count); it costs one atomic per warp per launch. */
@@ -187,6 +195,12 @@ ndf_status ndf_ksg_autotune(ndf_ctx* ctx, int ref_field, int query_field, int k,
 ndf_status ndf_ksg_debug_pair(ndf_ctx* ctx, int ref_field, int query_field, int64_t ref_idx,
                               int64_t query_idx, int k, float* eps, int32_t* nx, int32_t* ny,
                               double* mi);
+
+/* The same hook for algorithm 2: ex[M], ey[M] (marginal extents of each
+ * member's neighbour set), nx[M], ny[M] (non-strict counts) and *mi. */
+ndf_status ndf_ksg2_debug_pair(ndf_ctx* ctx, int ref_field, int query_field, int64_t ref_idx,
+                               int64_t query_idx, int k, float* ex, float* ey, int32_t* nx,
+                               int32_t* ny, double* mi);
 
 /* ---- neural dependence field (Sec. 4) ------------------------------------ */
 

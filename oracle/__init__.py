@@ -81,6 +81,11 @@ def _load():
             lib.oracle_ksg_volume.argtypes = [_f32p, _f32p, ctypes.c_int64, ctypes.c_int64,
                                               ctypes.c_int64, ctypes.c_int, _i64p, ctypes.c_int64,
                                               _f64p, ctypes.c_int]
+            lib.oracle_ksg2_pair.restype = ctypes.c_double
+            lib.oracle_ksg2_pair.argtypes = [_f32p, _f32p, ctypes.c_int64, ctypes.c_int, _f32p,
+                                             _f32p, _i32p, _i32p]
+            lib.oracle_ksg2_volume.restype = ctypes.c_int
+            lib.oracle_ksg2_volume.argtypes = lib.oracle_ksg_volume.argtypes
             lib.oracle_threads.restype = ctypes.c_int
             lib.oracle_threads.argtypes = [ctypes.c_int]
             _lib = lib
@@ -174,6 +179,47 @@ def ksg_volume(ref_field, q_field, ref_idx: int, k: int, verts=None, nthreads: i
                                    int(nthreads))
     if rc != 0:
         raise ValueError("oracle_ksg_volume: bad arguments")
+    return out
+
+
+def ksg2_pair(x, y, k: int):
+    """KSG algorithm 2 on one pair: returns (mi, ex[M], ey[M], nx[M], ny[M])."""
+    x, px = _f32(x)
+    y, py = _f32(y)
+    if x.shape != y.shape or x.ndim != 1:
+        raise ValueError("x and y must be 1-D of equal length")
+    M = x.shape[0]
+    ex = np.empty(M, dtype=np.float32)
+    ey = np.empty(M, dtype=np.float32)
+    nx = np.empty(M, dtype=np.int32)
+    ny = np.empty(M, dtype=np.int32)
+    mi = _load().oracle_ksg2_pair(px, py, M, int(k), ex.ctypes.data_as(_f32p),
+                                  ey.ctypes.data_as(_f32p), nx.ctypes.data_as(_i32p),
+                                  ny.ctypes.data_as(_i32p))
+    if np.isnan(mi):
+        raise ValueError("oracle_ksg2_pair: bad arguments (need 1 <= k < M)")
+    return mi, ex, ey, nx, ny
+
+
+def ksg2_volume(ref_field, q_field, ref_idx: int, k: int, verts=None, nthreads: int = 0):
+    """KSG algorithm-2 MI (reference vertex of ref_field, v of q_field)."""
+    rf, M = _field2d(ref_field)
+    qf, Mq = _field2d(q_field)
+    if Mq != M or rf.shape != qf.shape:
+        raise ValueError("fields differ in shape")
+    N = rf.shape[1]
+    if verts is None:
+        out = np.empty(N, dtype=np.float64)
+        vp, nv = None, 0
+    else:
+        verts = np.ascontiguousarray(verts, dtype=np.int64)
+        out = np.empty(verts.shape[0], dtype=np.float64)
+        vp, nv = verts.ctypes.data_as(_i64p), verts.shape[0]
+    rc = _load().oracle_ksg2_volume(rf.ctypes.data_as(_f32p), qf.ctypes.data_as(_f32p), M, N,
+                                    int(ref_idx), int(k), vp, nv, out.ctypes.data_as(_f64p),
+                                    int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle_ksg2_volume: bad arguments")
     return out
 
 

@@ -173,4 +173,80 @@ int oracle_ksg_volume(const float* ref_field, const float* q_field, int64_t M, i
     return bad ? -1 : 0;
 }
 
+// KSG algorithm 2 (the second estimator of the article cited in Sec. 3.2), one pair:
+//   d_ij, eps_i      as in algorithm 1 (k-th smallest joint max-norm distance, j != i)
+//   neighbour set    S_i = {j != i : d_ij <= eps_i}: the k nearest; with ties at the
+//                    k-th distance every tied member belongs to it (reading)
+//   ex_i, ey_i       max over S_i of |x_i - x_j| and of |y_i - y_j| (FP32)
+//   nx_i             #{j != i : |x_i - x_j| <= ex_i}, ny_i likewise   (non-strict)
+//   I2               psi(k) - 1/k + psi(M) - (1/M) sum_i [psi(nx_i) + psi(ny_i)]
+double oracle_ksg2_pair(const float* x, const float* y, int64_t M, int k, float* ex, float* ey,
+                        int32_t* nx, int32_t* ny) {
+    if (!x || !y || M < 2 || k < 1 || k >= M) return std::numeric_limits<double>::quiet_NaN();
+    std::vector<long double> psi = digamma_table(M + 1);
+    std::vector<float> d(static_cast<size_t>(M - 1));
+    long double acc = 0.0L;
+    for (int64_t i = 0; i < M; ++i) {
+        int64_t c = 0;
+        for (int64_t j = 0; j < M; ++j) {
+            if (j == i) continue;
+            d[static_cast<size_t>(c++)] = std::max(std::fabs(x[i] - x[j]), std::fabs(y[i] - y[j]));
+        }
+        std::nth_element(d.begin(), d.begin() + (k - 1), d.end());
+        const float e = d[static_cast<size_t>(k - 1)];
+        float wx = 0.0f, wy = 0.0f;
+        for (int64_t j = 0; j < M; ++j) {
+            if (j == i) continue;
+            const float dx = std::fabs(x[i] - x[j]), dy = std::fabs(y[i] - y[j]);
+            if (std::max(dx, dy) <= e) {
+                wx = std::max(wx, dx);
+                wy = std::max(wy, dy);
+            }
+        }
+        int32_t cx = 0, cy = 0;
+        for (int64_t j = 0; j < M; ++j) {
+            if (j == i) continue;
+            if (std::fabs(x[i] - x[j]) <= wx) ++cx;
+            if (std::fabs(y[i] - y[j]) <= wy) ++cy;
+        }
+        if (ex) ex[i] = wx;
+        if (ey) ey[i] = wy;
+        if (nx) nx[i] = cx;
+        if (ny) ny[i] = cy;
+        acc += psi[static_cast<size_t>(cx)] + psi[static_cast<size_t>(cy)];
+    }
+    long double mi = psi[static_cast<size_t>(k)] - 1.0L / static_cast<long double>(k) +
+                     psi[static_cast<size_t>(M)] - acc / static_cast<long double>(M);
+    return static_cast<double>(mi);
+}
+
+int oracle_ksg2_volume(const float* ref_field, const float* q_field, int64_t M, int64_t N,
+                       int64_t ref_idx, int k, const int64_t* verts, int64_t nverts, double* out,
+                       int nthreads) {
+    if (!ref_field || !q_field || !out || M < 2 || N < 1 || ref_idx < 0 || ref_idx >= N || k < 1 ||
+        k >= M)
+        return -1;
+    int64_t count = verts ? nverts : N;
+    std::vector<float> x(static_cast<size_t>(M));
+    gather_column(ref_field, M, N, ref_idx, x.data());
+    set_threads(nthreads);
+    int bad = 0;
+#pragma omp parallel
+    {
+        std::vector<float> y(static_cast<size_t>(M));
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t i = 0; i < count; ++i) {
+            int64_t v = verts ? verts[i] : i;
+            if (v < 0 || v >= N) {
+#pragma omp atomic write
+                bad = 1;
+                continue;
+            }
+            gather_column(q_field, M, N, v, y.data());
+            out[i] = oracle_ksg2_pair(x.data(), y.data(), M, k, nullptr, nullptr, nullptr, nullptr);
+        }
+    }
+    return bad ? -1 : 0;
+}
+
 }  // extern "C"

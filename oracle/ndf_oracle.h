@@ -10,6 +10,8 @@
  *     algorithm 1 of the estimator the paper cites in Sec. 3.2 / Sec. 6.2
  *     (max-norm in the joint space, strict counts, self excluded), by brute
  *     force with FP32 distances and long-double digamma sums;
+ *   - its algorithm 2 (the second estimator of the same article): the extents
+ *     of each member's k-nearest set in each marginal, non-strict counts;
  *   - digamma at positive integers by the recurrence psi(n+1) = psi(n) + 1/n.
  */
 #ifndef NDF_ORACLE_H
@@ -43,6 +45,17 @@ double oracle_ksg_pair(const float* x, const float* y, int64_t M, int k, float* 
 int oracle_ksg_volume(const float* ref_field, const float* q_field, int64_t M, int64_t N,
                       int64_t ref_idx, int k, const int64_t* verts, int64_t nverts, double* out,
                       int nthreads);
+
+/* KSG algorithm-2 estimate for one pair of samples.  ex/ey/nx/ny (length M, may
+ * be NULL) receive per member the marginal extents of its neighbour set and the
+ * non-strict marginal counts.  Returns MI in nats, or NaN (need 1 <= k < M). */
+double oracle_ksg2_pair(const float* x, const float* y, int64_t M, int k, float* ex, float* ey,
+                        int32_t* nx, int32_t* ny);
+
+/* KSG algorithm-2 MI between the reference vertex and the selected query vertices. */
+int oracle_ksg2_volume(const float* ref_field, const float* q_field, int64_t M, int64_t N,
+                       int64_t ref_idx, int k, const int64_t* verts, int64_t nverts, double* out,
+                       int nthreads);
 
 /* number of OpenMP threads a parallel region gets with the given request */
 int oracle_threads(int nthreads);

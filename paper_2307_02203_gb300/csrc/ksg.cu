@@ -115,8 +115,10 @@ struct KsgArgs {
     const double* psi;    // psi(n), n <= M + 1
     float* out;           // out[r * out_stride + (v - v_begin)]
     int64_t out_stride;
+    int variant;          // KSG algorithm 1 or 2
     double* dbg_mi;       // debug outputs for (reference 0, vertex v_begin), may be null
-    float* dbg_eps;
+    float* dbg_eps;       // eps (algorithm 1) or the x extent (algorithm 2)
+    float* dbg_ey;        // the y extent (algorithm 2)
     int32_t* dbg_nx;
     int32_t* dbg_ny;
     unsigned long long* evals;  // distance evaluations performed (self excluded), may be null
@@ -248,13 +250,24 @@ __global__ void __launch_bounds__(kKsgMaxThreads) ksg_volume_kernel(KsgArgs A) {
                     for (int q = 0; q < kKsgPts; ++q) {
                         if (q < n_own) {
                             const float e = a[q][K1 - 1];
-                            const int self = e > 0.0f ? 1 : 0;
-                            const int cx = count_within(xs, M, px[q], e) - self;
-                            const int cy = count_within(ys, M, py[q], e) - self;
-                            acc += A.psi[cx + 1] + A.psi[cy + 1];
+                            int cx, cy;
+                            float ex = e, ey = e;
+                            if (A.variant == 2) {
+                                alg2_extents([&](int j) { return pts[padi(j)]; }, M, b0 + q,
+                                             make_float2(px[q], py[q]), e, ex, ey);
+                                cx = count_le([&](int j) { return xs[j]; }, M, px[q], ex) - 1;
+                                cy = count_le([&](int j) { return ys[j]; }, M, py[q], ey) - 1;
+                                acc += A.psi[cx] + A.psi[cy];
+                            } else {
+                                const int self = e > 0.0f ? 1 : 0;
+                                cx = count_within(xs, M, px[q], e) - self;
+                                cy = count_within(ys, M, py[q], e) - self;
+                                acc += A.psi[cx + 1] + A.psi[cy + 1];
+                            }
                             if (dbg) {
                                 const int mi = perm[b0 + q];
-                                A.dbg_eps[mi] = e;
+                                A.dbg_eps[mi] = ex;
+                                if (A.dbg_ey) A.dbg_ey[mi] = ey;
                                 A.dbg_nx[mi] = cx;
                                 A.dbg_ny[mi] = cy;
                             }
@@ -263,7 +276,7 @@ __global__ void __launch_bounds__(kKsgMaxThreads) ksg_volume_kernel(KsgArgs A) {
                 }
                 const double tot = block_sum(acc, red);
                 if (tid == 0) {
-                    const double mi = psi_k + psi_M - tot / (double)M;
+                    const double mi = psi_k - (A.variant == 2 ? 1.0 / A.k : 0.0) + psi_M - tot / (double)M;
                     const int64_t v = vt0 + p;
                     A.out[(int64_t)(r0 + g) * A.out_stride + (v - A.v_begin)] = (float)mi;
                     if (A.dbg_mi && r0 + g == 0 && p == 0 && tile == 0) *A.dbg_mi = mi;
@@ -469,13 +482,23 @@ __global__ void __launch_bounds__(32 * kGroupWarps * kMaxGroupsPerCta, 1)
         for (int s = gt; s < M; s += GT) {
             const float e = epsw[s];
             const float2 ps = S[s];
-            const int self = e > 0.0f ? 1 : 0;
-            const int cx = count_within_x(S, M, ps.x, e) - self;
-            const int cy = count_within(ys, M, ps.y, e) - self;
-            acc += A.psi[cx + 1] + A.psi[cy + 1];
+            int cx, cy;
+            float ex = e, ey = e;
+            if (A.variant == 2) {
+                alg2_extents([&](int j) { return S[j]; }, M, s, ps, e, ex, ey);
+                cx = count_le([&](int j) { return S[j].x; }, M, ps.x, ex) - 1;
+                cy = count_le([&](int j) { return ys[j]; }, M, ps.y, ey) - 1;
+                acc += A.psi[cx] + A.psi[cy];
+            } else {
+                const int self = e > 0.0f ? 1 : 0;
+                cx = count_within_x(S, M, ps.x, e) - self;
+                cy = count_within(ys, M, ps.y, e) - self;
+                acc += A.psi[cx + 1] + A.psi[cy + 1];
+            }
             if (dbg) {
                 const int mi = perm[s];
-                A.dbg_eps[mi] = e;
+                A.dbg_eps[mi] = ex;
+                if (A.dbg_ey) A.dbg_ey[mi] = ey;
                 A.dbg_nx[mi] = cx;
                 A.dbg_ny[mi] = cy;
             }
@@ -488,7 +511,7 @@ __global__ void __launch_bounds__(32 * kGroupWarps * kMaxGroupsPerCta, 1)
             double tot = 0.0;
 #pragma unroll
             for (int w = 0; w < kGroupWarps; ++w) tot += ctl->part[w];
-            const double mi = psi_k + psi_M - tot / (double)M;
+            const double mi = psi_k - (A.variant == 2 ? 1.0 / A.k : 0.0) + psi_M - tot / (double)M;
             A.out[(int64_t)r * A.out_stride + (v - A.v_begin)] = (float)mi;
             if (dbg && A.dbg_mi) *A.dbg_mi = mi;
         }
@@ -564,7 +587,7 @@ cudaError_t launch_ksg(ndf_ctx* ctx, const Field& rf, const Field& qf, const int
                        int64_t ref0, int R, int k, int64_t v_begin, int64_t v_end, float* out,
                        int64_t out_stride, bool prune, int G, int VT, double* dbg_mi,
                        float* dbg_eps, int32_t* dbg_nx, int32_t* dbg_ny,
-                       unsigned long long* evals) {
+                       unsigned long long* evals, int variant, float* dbg_ey) {
     const int M = (int)rf.M;
     if (!qf.sorted || R < 1 || v_end <= v_begin) return cudaErrorInvalidValue;
     if (!d_refs && R != 1) return cudaErrorInvalidValue;
@@ -596,6 +619,8 @@ cudaError_t launch_ksg(ndf_ctx* ctx, const Field& rf, const Field& qf, const int
     A.dbg_eps = dbg_eps;
     A.dbg_nx = dbg_nx;
     A.dbg_ny = dbg_ny;
+    A.dbg_ey = dbg_ey;
+    A.variant = variant;
     A.evals = evals;
     switch (k + 1) {
         case 2: return launch_ksg_k<2>(ctx, A, prune);

@@ -40,6 +40,56 @@ __device__ __forceinline__ int count_within(const float* a, int n, float c, floa
     return hi > lo ? hi - lo : 0;
 }
 
+// #{p : |fl(a[p] - c)| <= e} in the ascending sequence at(0..n) (non-strict, as
+// KSG algorithm 2 counts), by two binary searches on monotone predicates.
+template <class Get>
+__device__ __forceinline__ int count_le(Get at, int n, float c, float e) {
+    int lo = 0, len = n;
+    while (len > 0) {  // first p with fl(c - a[p]) <= e
+        const int h = len >> 1;
+        if (!((c - at(lo + h)) <= e)) { lo += h + 1; len -= h + 1; }
+        else len = h;
+    }
+    int hi = 0;
+    len = n;
+    while (len > 0) {  // first p with fl(a[p] - c) > e
+        const int h = len >> 1;
+        if (!((at(hi + h) - c) > e)) { hi += h + 1; len -= h + 1; }
+        else len = h;
+    }
+    return hi > lo ? hi - lo : 0;
+}
+
+// KSG algorithm 2: the largest |dx| and |dy| over the members j != s whose joint
+// max-norm distance to the x-sorted point s is <= e (they lie in the x-window
+// |dx| <= e around position s, scanned outward).  pt(j) returns the x-sorted point.
+template <class Get>
+__device__ __forceinline__ void alg2_extents(Get pt, int M, int s, float2 ps, float e, float& ex,
+                                             float& ey) {
+    ex = 0.0f;
+    ey = 0.0f;
+    for (int j = s + 1; j < M; ++j) {
+        const float2 c = pt(j);
+        const float dx = c.x - ps.x;
+        if (dx > e) break;
+        const float dy = fabsf(ps.y - c.y);
+        if (fmaxf(dx, dy) <= e) {
+            ex = fmaxf(ex, dx);
+            ey = fmaxf(ey, dy);
+        }
+    }
+    for (int j = s - 1; j >= 0; --j) {
+        const float2 c = pt(j);
+        const float dx = ps.x - c.x;
+        if (dx > e) break;
+        const float dy = fabsf(ps.y - c.y);
+        if (fmaxf(dx, dy) <= e) {
+            ex = fmaxf(ex, dx);
+            ey = fmaxf(ey, dy);
+        }
+    }
+}
+
 __device__ __forceinline__ double block_sum(double v, double* red) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);

@@ -440,15 +440,17 @@ static ndf_status check_ksg_args(ndf_ctx* ctx, const Field* rf, int k) {
 // one reference over [v_begin, v_end) with the context's algorithm
 static cudaError_t run_ksg_one(ndf_ctx* ctx, const Field& rf, const Field& qf, int64_t ref_idx,
                                int k, int64_t v_begin, int64_t v_end, float* out, double* dbg_mi,
-                               float* dbg_eps, int32_t* dbg_nx, int32_t* dbg_ny) {
+                               float* dbg_eps, int32_t* dbg_nx, int32_t* dbg_ny, int variant = 1,
+                               float* dbg_ey = nullptr) {
     return launch_ksg(ctx, rf, qf, nullptr, ref_idx, 1, k, v_begin, v_end, out, 0,
                       ctx->ksg_algorithm == NDF_KSG_PRUNED, 1, ctx->ksg_tile, dbg_mi, dbg_eps,
                       dbg_nx, dbg_ny,
-                      ctx->count_evals ? ctx->evals.as<unsigned long long>() : nullptr);
+                      ctx->count_evals ? ctx->evals.as<unsigned long long>() : nullptr, variant,
+                      dbg_ey);
 }
 
-ndf_status ndf_mi_ksg(ndf_ctx* ctx, int ref_field, int query_field, int64_t ref_idx, int k,
-                      float* out) {
+static ndf_status mi_ksg_variant(ndf_ctx* ctx, int ref_field, int query_field, int64_t ref_idx,
+                                 int k, float* out, int variant) {
     if (!ctx) return NDF_ERR_ARG;
     const Field *rf, *qf;
     ndf_status st = check_pair(ctx, ref_field, query_field, ref_idx, &rf, &qf);
@@ -463,14 +465,24 @@ ndf_status ndf_mi_ksg(ndf_ctx* ctx, int ref_field, int query_field, int64_t ref_
     bool is_host;
     if ((st = resolve_out(ctx, out, bytes, &dev_out, &is_host)) != NDF_OK) return st;
     cudaError_t e = run_ksg_one(ctx, *rf, *qf, ref_idx, k, 0, qf->N, (float*)dev_out, nullptr,
-                                nullptr, nullptr, nullptr);
+                                nullptr, nullptr, nullptr, variant);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "ksg launch");
     return finish_out(ctx, out, dev_out, bytes, is_host);
 }
 
-ndf_status ndf_ksg_debug_pair(ndf_ctx* ctx, int ref_field, int query_field, int64_t ref_idx,
-                              int64_t query_idx, int k, float* eps, int32_t* nx, int32_t* ny,
-                              double* mi) {
+ndf_status ndf_mi_ksg(ndf_ctx* ctx, int ref_field, int query_field, int64_t ref_idx, int k,
+                      float* out) {
+    return mi_ksg_variant(ctx, ref_field, query_field, ref_idx, k, out, 1);
+}
+
+ndf_status ndf_mi_ksg2(ndf_ctx* ctx, int ref_field, int query_field, int64_t ref_idx, int k,
+                       float* out) {
+    return mi_ksg_variant(ctx, ref_field, query_field, ref_idx, k, out, 2);
+}
+
+static ndf_status ksg_debug_variant(ndf_ctx* ctx, int ref_field, int query_field, int64_t ref_idx,
+                                    int64_t query_idx, int k, float* eps, float* ey, int32_t* nx,
+                                    int32_t* ny, double* mi, int variant) {
     if (!ctx) return NDF_ERR_ARG;
     const Field *rf, *qf;
     ndf_status st = check_pair(ctx, ref_field, query_field, ref_idx, &rf, &qf);
@@ -482,8 +494,8 @@ ndf_status ndf_ksg_debug_pair(ndf_ctx* ctx, int ref_field, int query_field, int6
     cudaError_t es = ensure_sorted_columns(ctx, ctx->fields[query_field]);
     if (es != cudaSuccess) return cuda_fail(ctx, es, "sorted columns");
     int64_t M = rf->M;
-    // layout of the debug block: mi (double) | out (float) | eps[M] | nx[M] | ny[M]
-    size_t need = 16 + sizeof(float) * (size_t)M * 3 + 64;
+    // layout of the debug block: mi (double) | out (float) | eps[M] | nx[M] | ny[M] | ey[M]
+    size_t need = 16 + sizeof(float) * (size_t)M * 4 + 64;
     cudaError_t e = ctx->dbg.reserve(need);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "debug buffer");
     char* base = ctx->dbg.as<char>();
@@ -492,8 +504,9 @@ ndf_status ndf_ksg_debug_pair(ndf_ctx* ctx, int ref_field, int query_field, int6
     float* d_eps = (float*)(base + 16);
     int32_t* d_nx = (int32_t*)(d_eps + M);
     int32_t* d_ny = d_nx + M;
+    float* d_ey = (float*)(d_ny + M);
     e = run_ksg_one(ctx, *rf, *qf, ref_idx, k, query_idx, query_idx + 1, d_out, d_mi, d_eps, d_nx,
-                    d_ny);
+                    d_ny, variant, d_ey);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "ksg debug launch");
     std::vector<char> h(need);
     e = cudaMemcpyAsync(h.data(), base, need, cudaMemcpyDeviceToHost, ctx->stream);
@@ -504,7 +517,22 @@ ndf_status ndf_ksg_debug_pair(ndf_ctx* ctx, int ref_field, int query_field, int6
     if (eps) memcpy(eps, hb + 16, sizeof(float) * (size_t)M);
     if (nx) memcpy(nx, hb + 16 + 4 * M, sizeof(int32_t) * (size_t)M);
     if (ny) memcpy(ny, hb + 16 + 8 * M, sizeof(int32_t) * (size_t)M);
+    if (ey) memcpy(ey, hb + 16 + 12 * M, sizeof(float) * (size_t)M);
     return NDF_OK;
+}
+
+ndf_status ndf_ksg_debug_pair(ndf_ctx* ctx, int ref_field, int query_field, int64_t ref_idx,
+                              int64_t query_idx, int k, float* eps, int32_t* nx, int32_t* ny,
+                              double* mi) {
+    return ksg_debug_variant(ctx, ref_field, query_field, ref_idx, query_idx, k, eps, nullptr, nx,
+                             ny, mi, 1);
+}
+
+ndf_status ndf_ksg2_debug_pair(ndf_ctx* ctx, int ref_field, int query_field, int64_t ref_idx,
+                               int64_t query_idx, int k, float* ex, float* ey, int32_t* nx,
+                               int32_t* ny, double* mi) {
+    return ksg_debug_variant(ctx, ref_field, query_field, ref_idx, query_idx, k, ex, ey, nx, ny,
+                             mi, 2);
 }
 
 ndf_status ndf_set_ksg_algorithm(ndf_ctx* ctx, int algorithm, int count_evals) {

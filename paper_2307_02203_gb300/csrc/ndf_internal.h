@@ -120,7 +120,7 @@ cudaError_t launch_ksg(ndf_ctx* ctx, const Field& rf, const Field& qf, const int
                        int64_t ref0, int R, int k, int64_t v_begin, int64_t v_end, float* out,
                        int64_t out_stride, bool prune, int G, int VT, double* dbg_mi,
                        float* dbg_eps, int32_t* dbg_nx, int32_t* dbg_ny,
-                       unsigned long long* evals);
+                       unsigned long long* evals, int variant = 1, float* dbg_ey = nullptr);
 
 // Builds Field::sorted (one sort per vertex column, kept with the field).
 cudaError_t ensure_sorted_columns(ndf_ctx* ctx, Field& f);

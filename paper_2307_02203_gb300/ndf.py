@@ -61,6 +61,7 @@ _sig("ndf_field_shape", ctypes.c_int, [_vp, ctypes.c_int] + [ctypes.POINTER(_i64
 _sig("ndf_field_stats", ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp])
 _sig("ndf_pearson", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, _vp])
 _sig("ndf_mi_ksg", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, ctypes.c_int, _vp])
+_sig("ndf_mi_ksg2", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, ctypes.c_int, _vp])
 _sig("ndf_pearson_batch", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int,
                                          ctypes.c_int, _vp])
 _sig("ndf_set_ksg_algorithm", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int])
@@ -72,6 +73,8 @@ _sig("ndf_ksg_autotune", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.
 _sig("ndf_pearson_noalloc", ctypes.c_int, [_vp, _vp, _i64, _i64, _i64, _vp, _vp])
 _sig("ndf_ksg_debug_pair", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, _i64,
                                           ctypes.c_int, _vp, _vp, _vp, _vp])
+_sig("ndf_ksg2_debug_pair", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, _i64,
+                                           ctypes.c_int, _vp, _vp, _vp, _vp, _vp])
 
 
 class TrainCfg(ctypes.Structure):
@@ -224,6 +227,11 @@ def ndf_mi_ksg(ctx, ref_field: int, query_field: int, ref_idx: int, k: int, out)
            "ndf_mi_ksg")
 
 
+def ndf_mi_ksg2(ctx, ref_field: int, query_field: int, ref_idx: int, k: int, out) -> None:
+    _check(ctx, _lib.ndf_mi_ksg2(ctx, ref_field, query_field, ref_idx, k, _addr(out)),
+           "ndf_mi_ksg2")
+
+
 def ndf_set_ksg_algorithm(ctx, algorithm: int, count_evals: bool = False) -> None:
     _check(ctx, _lib.ndf_set_ksg_algorithm(ctx, int(algorithm), int(bool(count_evals))),
            "ndf_set_ksg_algorithm")
@@ -255,6 +263,13 @@ def ndf_ksg_debug_pair(ctx, ref_field, query_field, ref_idx, query_idx, k, eps, 
     _check(ctx, _lib.ndf_ksg_debug_pair(ctx, ref_field, query_field, ref_idx, query_idx, k,
                                         _addr(eps), _addr(nx), _addr(ny), _addr(mi)),
            "ndf_ksg_debug_pair")
+
+
+def ndf_ksg2_debug_pair(ctx, ref_field, query_field, ref_idx, query_idx, k, ex, ey, nx, ny,
+                        mi) -> None:
+    _check(ctx, _lib.ndf_ksg2_debug_pair(ctx, ref_field, query_field, ref_idx, query_idx, k,
+                                         _addr(ex), _addr(ey), _addr(nx), _addr(ny), _addr(mi)),
+           "ndf_ksg2_debug_pair")
 
 
 def ndf_pearson_noalloc(ref_field, query_field, M, N, ref_idx, out, cuda_stream=None) -> None:

@@ -25,6 +25,16 @@ def ksg_hand_cases():
     return out
 
 
+def ksg2_hand_cases():
+    out = []
+    for name, k, x, y, ex, ey, nx, ny, mi in _rows("ksg2_hand.txt"):
+        f = lambda t: [float(u) for u in t.split()]
+        i = lambda t: [int(u) for u in t.split()]
+        out.append(dict(name=name, k=int(k), x=f(x), y=f(y), ex=f(ex), ey=f(ey), nx=i(nx),
+                        ny=i(ny), mi=Fraction(mi)))
+    return out
+
+
 def pearson_hand_cases():
     out = []
     for x, y, num, den_sq in _rows("pearson_hand.txt"):

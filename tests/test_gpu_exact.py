@@ -11,6 +11,7 @@ import pytest
 import torch
 
 import oracle
+from golden_io import ksg2_hand_cases
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -212,9 +213,8 @@ def test_ksg_tiny_volume(ndf_mod, ctx, algo, tiny_field, tiny_ref):
     ((1000, 2, 8, 25), 8, "normal"),   # paper-scale M, several tiles + ragged tail
     ((1000, 1, 3, 7), 8, "ties"),      # heavy ties: eps = 0 and equal distances
     ((2500, 1, 2, 9), 8, "normal"),    # M > 2048: threads own two point blocks
-    ((4096, 1, 1, 3), 16, "normal"),   # largest M and k (the pruned search's per-point
-                                       # lists do not fit in shared memory: brute force)
-    ((3000, 1, 1, 4), 8, "normal"),    # M > 2048 with the pruned search in shared memory
+    ((4096, 1, 1, 3), 16, "normal"),   # largest M and k
+    ((3000, 1, 1, 4), 8, "normal"),    # M > 2048, not a power of two
     ((2, 1, 2, 2), 1, "normal"),       # smallest M
     ((17, 1, 3, 3), 16, "normal"),     # k = M - 1 = 16 (largest supported k)
     ((100, 2, 3, 5), 3, "ties"),
@@ -248,6 +248,68 @@ def test_ksg_cross_field(ndf_mod, ctx, algo):
     check_pairs_bit_exact(ndf_mod, ctx, fa, fb, a, b, 5, [0, 5, N - 1], 8)
     ndf_mod.ndf_free_ensemble(ctx, fa)
     ndf_mod.ndf_free_ensemble(ctx, fb)
+
+
+# ---------------------------------------------------------------- KSG algorithm 2
+def ksg2_debug(ndf, ctx, fa, fb, r, v, k, M):
+    ex = np.empty(M, dtype=np.float32)
+    ey = np.empty(M, dtype=np.float32)
+    nx = np.empty(M, dtype=np.int32)
+    ny = np.empty(M, dtype=np.int32)
+    mi = np.empty(1, dtype=np.float64)
+    ndf.ndf_ksg2_debug_pair(ctx, fa, fb, r, v, k, ex, ey, nx, ny, mi)
+    return float(mi[0]), ex, ey, nx, ny
+
+
+def check_pairs2_bit_exact(ndf, ctx, fa, fb, a, b, r, verts, k):
+    M = a.shape[0]
+    a2 = a.reshape(M, -1)
+    b2 = b.reshape(M, -1)
+    for v in verts:
+        g = ksg2_debug(ndf, ctx, fa, fb, r, int(v), k, M)
+        o = oracle.ksg2_pair(a2[:, r], b2[:, v], k)
+        for idx, name in ((1, "ex"), (2, "ey"), (3, "nx"), (4, "ny")):
+            np.testing.assert_array_equal(g[idx], o[idx], err_msg=f"{name} v={v}")
+        assert abs(g[0] - o[0]) <= 1e-6 * abs(o[0]) + 1e-9, (v, g[0], o[0])
+
+
+@pytest.mark.parametrize("case", ksg2_hand_cases(), ids=lambda c: c["name"])
+def test_ksg2_hand_cases(ndf_mod, ctx, algo, case):
+    """The hand-enumerated algorithm-2 cases as a two-vertex field (x at vertex 0,
+    y at vertex 1): extents, counts and the exact rational MI."""
+    f = np.stack([case["x"], case["y"]], axis=1).astype(np.float32).reshape(-1, 1, 1, 2)
+    fid = load(ndf_mod, ctx, f)
+    M = f.shape[0]
+    mi, ex, ey, nx, ny = ksg2_debug(ndf_mod, ctx, fid, fid, 0, 1, case["k"], M)
+    np.testing.assert_array_equal(ex, np.array(case["ex"], dtype=np.float32))
+    np.testing.assert_array_equal(ey, np.array(case["ey"], dtype=np.float32))
+    np.testing.assert_array_equal(nx, case["nx"])
+    np.testing.assert_array_equal(ny, case["ny"])
+    assert mi == pytest.approx(float(case["mi"]), abs=1e-12)
+    out = np.empty(2, dtype=np.float32)
+    ndf_mod.ndf_mi_ksg2(ctx, fid, fid, 0, case["k"], out)
+    assert out[1] == np.float32(float(case["mi"]))
+    ndf_mod.ndf_free_ensemble(ctx, fid)
+
+
+@pytest.mark.parametrize("shape,k,kind", [
+    ((1000, 2, 4, 9), 8, "normal"),
+    ((300, 1, 3, 7), 4, "ties"),
+    ((17, 1, 3, 3), 16, "normal"),     # k = M - 1
+    ((2, 1, 2, 2), 1, "normal"),
+    ((3000, 1, 1, 3), 8, "normal"),
+])
+def test_ksg2_volume_and_pairs(ndf_mod, ctx, algo, shape, k, kind):
+    f = rand_field(shape, seed=7 * shape[0] + k, kind=kind)
+    fid = load(ndf_mod, ctx, f)
+    N = f[0].size
+    r = N // 2
+    out = np.empty(N, dtype=np.float32)
+    ndf_mod.ndf_mi_ksg2(ctx, fid, fid, r, k, out)
+    ok, where = mi_close(out, oracle.ksg2_volume(f, f, r, k))
+    assert ok, (where, out[where])
+    check_pairs2_bit_exact(ndf_mod, ctx, fid, fid, f, f, r, sorted({0, r, N - 1}), k)
+    ndf_mod.ndf_free_ensemble(ctx, fid)
 
 
 # ---------------------------------------------------------------- batched KSG

@@ -72,6 +72,38 @@ def test_csens_ksg_sampled(ndf_mod, ctx, csens, algorithm):
     ndf_mod.ndf_set_ksg_algorithm(ctx, ndf_mod.NDF_KSG_PRUNED)
 
 
+def test_csens_ksg2_sampled(ndf_mod, ctx, csens):
+    """KSG algorithm 2 on the full-size ensemble (the default, pruned search)
+    against the oracle on sampled vertices; per-member extents and counts
+    bit-exact on a smaller sample."""
+    f, fid = csens
+    N = synth.CSENS.N
+    M = synth.CSENS.M
+    r = synth.vertex_index(*REF, synth.CSENS)
+    out = torch.empty(N, dtype=torch.float32, device="cuda")
+    ndf_mod.ndf_mi_ksg2(ctx, fid, fid, r, 8, out)
+    ndf_mod.ndf_synchronize(ctx)
+    vol = out.cpu().numpy()
+    assert np.isfinite(vol).all()
+    verts = np.concatenate([synth.sample_vertices(synth.CSENS, 2048, seed=16),
+                            [0, r, N - 1]]).astype(np.int64)
+    ref = oracle.ksg2_volume(f, f, r, 8, verts=verts)
+    got = vol[verts].astype(np.float64)
+    bad = np.abs(got - ref) > 1e-6 * np.abs(ref) + 1e-9
+    assert not bad.any(), (verts[bad][:5], got[bad][:5], ref[bad][:5])
+    f2 = f.reshape(M, N)
+    for v in synth.sample_vertices(synth.CSENS, 16, seed=17):
+        ex, ey = np.empty(M, np.float32), np.empty(M, np.float32)
+        nx, ny = np.empty(M, np.int32), np.empty(M, np.int32)
+        mi = np.empty(1, np.float64)
+        ndf_mod.ndf_ksg2_debug_pair(ctx, fid, fid, r, int(v), 8, ex, ey, nx, ny, mi)
+        o = oracle.ksg2_pair(f2[:, r], f2[:, v], 8)
+        np.testing.assert_array_equal(ex, o[1])
+        np.testing.assert_array_equal(ey, o[2])
+        np.testing.assert_array_equal(nx, o[3])
+        np.testing.assert_array_equal(ny, o[4])
+
+
 def test_csens_ksg_batch_sampled(ndf_mod, ctx, csens):
     """Four references in one batched launch against the oracle on sampled vertices."""
     f, fid = csens
