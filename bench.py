@@ -233,6 +233,48 @@ def measure_ksg_batch(ndf, ctx, fid, recipe, stream, args, R=16):
     return {"refs": R, "ms": ms, "ms_per_volume": ms / R, "mi_pairs_per_s": R * N / (ms * 1e-3)}
 
 
+def measure_render(ndf, ctx, model, refs, recipe, stream, W=1024, H=1024):
+    """Decode one reference volume and ray-march it (DVR, iso-surface, and the
+    difference of two reference fields) into a 1024x1024 RGBA buffer on the
+    device; CUDA-event times per image, and decode + render together."""
+    import torch
+
+    N = recipe.N
+    vol = torch.empty(N, dtype=torch.float32, device="cuda")
+    vol2 = torch.empty(N, dtype=torch.float32, device="cuda")
+    img = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+    tf = [[0.0, 0.0, 0.5, 0.0], [0.1, 0.3, 0.9, 0.5], [0.9, 0.9, 0.9, 0.2], [1.0, 0.5, 0.0, 3.0],
+          [0.8, 0.0, 0.0, 12.0]]
+    cam = dict(eye=(2.2, 1.6, 2.6), target=(0.0, 0.0, 0.0), up=(0.0, 1.0, 0.0), fov_y_deg=32.0,
+               width=W, height=H, step=2.0 / 512, tf=tf)
+    X, Y, Z = recipe.X, recipe.Y, recipe.Z
+    modes = {"dvr": dict(mode=ndf.NDF_RENDER_DVR, vmin=-1.0, vmax=1.0),
+             "iso": dict(mode=ndf.NDF_RENDER_ISO, vmin=-1.0, vmax=1.0, iso=0.5)}
+    ndf.ndf_infer(model, refs[0], vol)
+    ndf.ndf_infer(model, refs[1], vol2)
+    for kw in modes.values():  # warm-up
+        ndf.ndf_render_volume(ctx, vol, None, X, Y, Z, img, **cam, **kw)
+    ndf.ndf_synchronize(ctx)
+    res = {"width": W, "height": H, "step": cam["step"]}
+    for name, kw in modes.items():
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        ndf.ndf_infer(model, refs[2], vol)
+        e1.record(stream)
+        ndf.ndf_render_volume(ctx, vol, None, X, Y, Z, img, **cam, **kw)
+        e2.record(stream)
+        ndf.ndf_synchronize(ctx)
+        res[f"{name}_render_ms"] = e1.elapsed_time(e2)
+        res[f"{name}_decode_plus_render_ms"] = e0.elapsed_time(e2)
+    e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+    e0.record(stream)
+    ndf.ndf_render_volume(ctx, vol, vol2, X, Y, Z, img, **cam, **modes["dvr"])
+    e1.record(stream)
+    ndf.ndf_synchronize(ctx)
+    res["difference_dvr_render_ms"] = e0.elapsed_time(e1)
+    return res
+
+
 def measure_ndf(ndf, ctx, fid, recipe, stream, args, exact_ms, fid_b=None):
     """Learned part: trains a Pearson and a KSG-MI network on the loaded field
     (targets from the GPU estimators), then times volume decoding (1 reference
@@ -277,6 +319,7 @@ def measure_ndf(ndf, ctx, fid, recipe, stream, args, exact_ms, fid_b=None):
         ndf.ndf_synchronize(ctx)
         ms_one = e0.elapsed_time(e1) / len(refs)
         ms_batch = e1.elapsed_time(e2) / len(refs)
+        render = measure_render(ndf, ctx, model, refs, recipe, stream) if name == "pearson" else None
         # exact volumes of the same references for the error statement
         n_err = 16 if measure == ndf.NDF_MEASURE_PEARSON else args.ndf_mi_err_refs
         exact = torch.empty((n_err, N), dtype=torch.float32, device="cuda")
@@ -302,6 +345,8 @@ def measure_ndf(ndf, ctx, fid, recipe, stream, args, exact_ms, fid_b=None):
             "max_err": float(err.max()), "error_refs": n_err,
             "exact_mean_abs_value": float(exact.abs().mean()),
         }
+        if render is not None:
+            out[name]["render"] = render
         ndf.ndf_model_free(model)
     return out
 

@@ -288,6 +288,39 @@ ndf_status ndf_model_step(ndf_model* model, const float* p_ref, const float* p_q
 ndf_status ndf_model_forward(ndf_model* model, const float* p_ref, const float* p_query,
                              int64_t B, float* out);
 
+/* ---- headless volume rendering (Sec. 5, Sec. 6.5) -------------------------- */
+
+/* Direct volume rendering with a transfer function, or an iso-surface. */
+typedef enum { NDF_RENDER_DVR = 0, NDF_RENDER_ISO = 1 } ndf_render_mode;
+
+typedef struct {
+    float eye[3], target[3], up[3]; /* pinhole camera in the volume's [-1,1]^3 frame */
+    float fov_y_deg;                /* vertical field of view, (0, 180) degrees */
+    int32_t width, height;          /* image size in pixels */
+    float step;                     /* ray-march step, > 0 (box units) */
+    int32_t mode;                   /* ndf_render_mode */
+    float iso;                      /* iso value (NDF_RENDER_ISO) */
+    float vmin, vmax;               /* transfer-function domain, vmax > vmin */
+    float background[4];            /* RGBA behind the volume */
+    float ambient;                  /* iso-surface ambient term in [0, 1] */
+    int32_t n_tf;                   /* transfer-function entries, >= 1 */
+    const float* tf;                /* host [n_tf][4] RGBA; A = opacity per unit length */
+} ndf_render_cfg;
+
+/* Ray-marches the dependence volume vol_a[Z][Y][X] (host or device; vertex i of
+ * an axis of n vertices sits at -1 + 2 i / (n - 1), as ndf_infer decodes), or
+ * the difference vol_a - vol_b of two reference fields when vol_b is not NULL
+ * (Sec. 6.5), into out_rgba[height][width][4] (FP32, host or device).
+ * Samples: trilinear, at t0 + (k + 1/2) step along each ray inside [-1,1]^3.
+ * DVR: alpha = 1 - exp(-A step), front-to-back compositing over the background.
+ * ISO: first sign change of (value - iso), linear refinement, central-difference
+ * normal (h = step) turned to the viewer, colour tf(iso) * (ambient +
+ * (1 - ambient) max(0, n . -dir)).  Requires X, Y, Z >= 2 (NDF_ERR_ARG
+ * otherwise, and for a bad configuration).  Host volumes are copied to context
+ * scratch; synchronous only when out_rgba is a host pointer. */
+ndf_status ndf_render_volume(ndf_ctx* ctx, const float* vol_a, const float* vol_b, int64_t X,
+                             int64_t Y, int64_t Z, const ndf_render_cfg* cfg, float* out_rgba);
+
 /* ---- allocation-free variant --------------------------------------------- */
 
 /* Largest member count ndf_pearson_noalloc accepts. */

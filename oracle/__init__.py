@@ -15,6 +15,9 @@ Functions and the passages they follow:
   digamma_int              -- psi(1) = -gamma, psi(n+1) = psi(n) + 1/n
   ndf_*, adam_step         -- Sec. 4: dense-grid NDF forward, L1 loss (Eq. 3), hand-written
                               backward, Adam update, all FP64
+  render                   -- Sec. 5 / Sec. 6.5: headless ray-march of a dependence volume
+                              (DVR with a transfer function, iso-surface, difference of two
+                              fields), FP64 per pixel (render_oracle.h has the definitions)
 """
 from __future__ import annotations
 
@@ -28,8 +31,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libndf_oracle.so")
-_SOURCES = ["ndf_oracle.cpp", "ndf_net_oracle.cpp"]
-_HEADERS = ["ndf_oracle.h", "ndf_net_oracle.h"]
+_SOURCES = ["ndf_oracle.cpp", "ndf_net_oracle.cpp", "render_oracle.cpp"]
+_HEADERS = ["ndf_oracle.h", "ndf_net_oracle.h", "render_oracle.h"]
 _lock = threading.Lock()
 _lib = None
 
@@ -60,6 +63,18 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+class RenderCfg(ctypes.Structure):
+    """Camera, ray step, mode and transfer function of the ray-march oracle."""
+
+    _fields_ = [("eye", ctypes.c_double * 3), ("target", ctypes.c_double * 3),
+                ("up", ctypes.c_double * 3), ("fov_y_deg", ctypes.c_double),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("step", ctypes.c_double),
+                ("mode", ctypes.c_int32), ("iso", ctypes.c_double), ("vmin", ctypes.c_double),
+                ("vmax", ctypes.c_double), ("background", ctypes.c_double * 4),
+                ("ambient", ctypes.c_double), ("n_tf", ctypes.c_int32),
+                ("tf", ctypes.POINTER(ctypes.c_double))]
+
+
 def _load():
     global _lib
     with _lock:
@@ -88,6 +103,10 @@ def _load():
             lib.oracle_ksg2_volume.argtypes = lib.oracle_ksg_volume.argtypes
             lib.oracle_threads.restype = ctypes.c_int
             lib.oracle_threads.argtypes = [ctypes.c_int]
+            lib.oracle_render.restype = ctypes.c_int
+            lib.oracle_render.argtypes = [_f32p, _f32p, ctypes.c_int64, ctypes.c_int64,
+                                          ctypes.c_int64, ctypes.POINTER(RenderCfg), _f64p,
+                                          ctypes.c_int]
             _lib = lib
     return _lib
 
@@ -220,6 +239,36 @@ def ksg2_volume(ref_field, q_field, ref_idx: int, k: int, verts=None, nthreads: 
                                     int(nthreads))
     if rc != 0:
         raise ValueError("oracle_ksg2_volume: bad arguments")
+    return out
+
+
+def render(vol_a, vol_b, *, eye, target, up, fov_y_deg, width, height, step, mode, tf,
+           vmin, vmax, iso=0.0, background=(0.0, 0.0, 0.0, 0.0), ambient=0.2, nthreads=0):
+    """Ray-march the volume(s) float[Z][Y][X] (vol_b may be None: the difference
+    vol_a - vol_b is rendered otherwise).  mode 0 = DVR, 1 = iso-surface.  tf is
+    an [n][4] RGBA table over [vmin, vmax] (A = opacity per unit length).
+    Returns float64 [height][width][4]."""
+    a = np.ascontiguousarray(vol_a, dtype=np.float32)
+    if a.ndim != 3:
+        raise ValueError("volume must be [Z][Y][X]")
+    b = None if vol_b is None else np.ascontiguousarray(vol_b, dtype=np.float32)
+    if b is not None and b.shape != a.shape:
+        raise ValueError("volumes differ in shape")
+    tfa = np.ascontiguousarray(tf, dtype=np.float64)
+    c = RenderCfg()
+    c.eye[:], c.target[:], c.up[:] = list(eye), list(target), list(up)
+    c.fov_y_deg, c.width, c.height, c.step = fov_y_deg, width, height, step
+    c.mode, c.iso, c.vmin, c.vmax = mode, iso, vmin, vmax
+    c.background[:] = list(background)
+    c.ambient, c.n_tf = ambient, tfa.shape[0]
+    c.tf = tfa.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    out = np.empty((height, width, 4), dtype=np.float64)
+    Z, Y, X = a.shape
+    rc = _load().oracle_render(a.ctypes.data_as(_f32p),
+                               None if b is None else b.ctypes.data_as(_f32p), X, Y, Z,
+                               ctypes.byref(c), out.ctypes.data_as(_f64p), int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle_render: bad arguments")
     return out
 
 

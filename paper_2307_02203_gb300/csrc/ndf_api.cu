@@ -269,6 +269,7 @@ void ndf_destroy(ndf_ctx* ctx) {
     ctx->refidx.release();
     ctx->evals.release();
     ctx->ksg_work.release();
+    ctx->render_buf.release();
     if (ctx->copy_stream) {
         cudaStreamSynchronize(ctx->copy_stream);
         cudaStreamDestroy(ctx->copy_stream);

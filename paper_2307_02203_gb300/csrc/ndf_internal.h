@@ -69,6 +69,7 @@ struct ndf_ctx {
     bool count_evals = false;
     ndf::DevBuf evals;       // KSG distance evaluations (when counting is on)
     ndf::DevBuf ksg_work;    // pruned KSG: work-item counter
+    ndf::DevBuf render_buf;  // ray-march: transfer function and uploaded host volumes
     std::vector<CachedBuf> cache;  // device buffers of freed fields, reused by later loads
     ndf::DevBuf zr;          // batched Pearson: standardised reference rows
     ndf::DevBuf refidx;      // batched calls: reference indices on the device

@@ -27,6 +27,19 @@ NDF_ERR_TIMEOUT, NDF_ERR_STATE, NDF_ERR_IO = -4, -5, -6
 NDF_PREC_FP32, NDF_PREC_BF16X3, NDF_PREC_TF32 = 0, 1, 2
 NDF_MEASURE_PEARSON, NDF_MEASURE_MI_KSG = 0, 1
 NDF_KSG_BRUTE, NDF_KSG_PRUNED = 0, 1
+NDF_RENDER_DVR, NDF_RENDER_ISO = 0, 1
+
+
+class RenderCfg(ctypes.Structure):
+    """ndf_render_cfg (include/ndf.h)."""
+
+    _fields_ = [("eye", ctypes.c_float * 3), ("target", ctypes.c_float * 3),
+                ("up", ctypes.c_float * 3), ("fov_y_deg", ctypes.c_float),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("step", ctypes.c_float),
+                ("mode", ctypes.c_int32), ("iso", ctypes.c_float), ("vmin", ctypes.c_float),
+                ("vmax", ctypes.c_float), ("background", ctypes.c_float * 4),
+                ("ambient", ctypes.c_float), ("n_tf", ctypes.c_int32),
+                ("tf", ctypes.POINTER(ctypes.c_float))]
 
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -62,6 +75,7 @@ _sig("ndf_field_stats", ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp])
 _sig("ndf_pearson", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, _vp])
 _sig("ndf_mi_ksg", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, ctypes.c_int, _vp])
 _sig("ndf_mi_ksg2", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, ctypes.c_int, _vp])
+_sig("ndf_render_volume", ctypes.c_int, [_vp, _vp, _vp, _i64, _i64, _i64, _vp, _vp])
 _sig("ndf_pearson_batch", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int,
                                          ctypes.c_int, _vp])
 _sig("ndf_set_ksg_algorithm", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int])
@@ -270,6 +284,25 @@ def ndf_ksg2_debug_pair(ctx, ref_field, query_field, ref_idx, query_idx, k, ex, 
     _check(ctx, _lib.ndf_ksg2_debug_pair(ctx, ref_field, query_field, ref_idx, query_idx, k,
                                          _addr(ex), _addr(ey), _addr(nx), _addr(ny), _addr(mi)),
            "ndf_ksg2_debug_pair")
+
+
+def ndf_render_volume(ctx, vol_a, vol_b, X: int, Y: int, Z: int, out, *, eye, target, up,
+                      fov_y_deg, width, height, step, mode, tf, vmin, vmax, iso=0.0,
+                      background=(0.0, 0.0, 0.0, 0.0), ambient=0.2) -> None:
+    """Ray-march vol_a (or vol_a - vol_b) into out [height][width][4] (host or device)."""
+    import numpy as _np
+
+    tfa = _np.ascontiguousarray(tf, dtype=_np.float32).reshape(-1, 4)
+    c = RenderCfg()
+    c.eye[:], c.target[:], c.up[:] = list(eye), list(target), list(up)
+    c.fov_y_deg, c.width, c.height, c.step = fov_y_deg, width, height, step
+    c.mode, c.iso, c.vmin, c.vmax = mode, iso, vmin, vmax
+    c.background[:] = list(background)
+    c.ambient, c.n_tf = ambient, tfa.shape[0]
+    c.tf = tfa.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    _check(ctx, _lib.ndf_render_volume(ctx, _addr(vol_a), None if vol_b is None else _addr(vol_b),
+                                       X, Y, Z, ctypes.byref(c), _addr(out)),
+           "ndf_render_volume")
 
 
 def ndf_pearson_noalloc(ref_field, query_field, M, N, ref_idx, out, cuda_stream=None) -> None:
