@@ -275,6 +275,28 @@ def measure_render(ndf, ctx, model, refs, recipe, stream, W=1024, H=1024):
     return res
 
 
+def measure_sampler(ndf, ctx, fid, stream):
+    """Continuous-position training samples (uniform random positions, trilinear
+    member columns, paired estimators): triples per second for each measure."""
+    import torch
+
+    res = {}
+    for name, measure, k, n in (("pearson", ndf.NDF_MEASURE_PEARSON, 0, 1 << 20),
+                                ("mi", ndf.NDF_MEASURE_MI_KSG, K_NN, 1 << 17)):
+        pr = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+        pq = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+        t = torch.empty(n, dtype=torch.float32, device="cuda")
+        ndf.ndf_sample_triples(ctx, fid, fid, measure, k, 4096, 1, pr, pq, t)  # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ndf.ndf_sample_triples(ctx, fid, fid, measure, k, n, 2, pr, pq, t)
+        e1.record(stream)
+        ndf.ndf_synchronize(ctx)
+        ms = e0.elapsed_time(e1)
+        res[name] = {"triples": n, "ms": ms, "triples_per_s": n / (ms * 1e-3)}
+    return res
+
+
 def measure_ndf(ndf, ctx, fid, recipe, stream, args, exact_ms, fid_b=None):
     """Learned part: trains a Pearson and a KSG-MI network on the loaded field
     (targets from the GPU estimators), then times volume decoding (1 reference
@@ -533,6 +555,8 @@ def main():
     if fid_b is not None:
         ndf.ndf_free_ensemble(ctx, fid_b)
         ndf.ndf_trim_cache(ctx)
+    if ndf_res is not None:
+        ndf_res["continuous_sampler"] = measure_sampler(ndf, ctx, fid, stream)
 
     # ---- end to end through the ABI with host buffers (upload + stats + both volumes + D2H)
     host_r = torch.empty(N, dtype=torch.float32, pin_memory=True)

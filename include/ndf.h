@@ -226,6 +226,9 @@ typedef struct {
     float lr, beta1, beta2, eps; /* Adam [3e-4, 0.9, 0.999, 1e-8] */
     uint64_t seed;            /* triples, pass orders, initial weights [20230705] */
     double time_budget_s;     /* stop training after this many seconds (0: none) [0] */
+    int32_t continuous;       /* 0: grid-vertex pairs, generated once; 1: uniform random
+                                 positions with trilinear samples (ndf_sample_triples),
+                                 n_triples fresh pairs every pass (Sec. 4.3) [0] */
 } ndf_train_cfg;
 
 /* What a model is and how it was trained. */
@@ -244,6 +247,18 @@ typedef struct {
 } ndf_model_info_t;
 
 void ndf_train_cfg_default(ndf_train_cfg* cfg);
+
+/* Training samples at continuous positions (Sec. 4.3): n independent pairs of
+ * uniform random positions p_ref, p_q in [-1,1]^3 (a 2^-23 grid; seeded), the
+ * member columns of ref_field at p_ref and of query_field at p_q by trilinear
+ * interpolation (vertex i of an axis of n at -1 + 2 i / (n - 1); FP32 in a fixed
+ * order: u = ((p + 1) * 0.5) * (n - 1) clamped, i0 = min(floor(u), n - 2),
+ * w = u - i0, a * (1 - w) + b * w along x, y, z), and the target R(p_ref, p_q):
+ * Pearson r (Eq. 1, FP64 sums) or KSG MI (algorithm 1, k; the pruned search).
+ * Writes pref[n][3], pq[n][3], target[n] (host or device; host outputs
+ * synchronize).  Errors: NDF_ERR_ARG for bad ids, measure, k or n. */
+ndf_status ndf_sample_triples(ndf_ctx* ctx, int ref_field, int query_field, int measure, int k,
+                              int64_t n, uint64_t seed, float* pref, float* pq, float* target);
 
 /* Learn Phi(p_ref, p_q) ~ R(p_ref, p_q) (Eq. 3, L1 loss, Adam) for the
  * reference field / query field pair (the self-correlation field when they

@@ -101,6 +101,9 @@ def _load():
                                              _f32p, _i32p, _i32p]
             lib.oracle_ksg2_volume.restype = ctypes.c_int
             lib.oracle_ksg2_volume.argtypes = lib.oracle_ksg_volume.argtypes
+            lib.oracle_interp_column.restype = ctypes.c_int
+            lib.oracle_interp_column.argtypes = [_f32p, ctypes.c_int64, ctypes.c_int64,
+                                                 ctypes.c_int64, ctypes.c_int64, _f32p, _f32p]
             lib.oracle_threads.restype = ctypes.c_int
             lib.oracle_threads.argtypes = [ctypes.c_int]
             lib.oracle_render.restype = ctypes.c_int
@@ -239,6 +242,20 @@ def ksg2_volume(ref_field, q_field, ref_idx: int, k: int, verts=None, nthreads: 
                                     int(nthreads))
     if rc != 0:
         raise ValueError("oracle_ksg2_volume: bad arguments")
+    return out
+
+
+def interp_column(field, p):
+    """Member column of field[M][Z][Y][X] at the continuous position p (FP32 trilinear,
+    see oracle_interp_column)."""
+    f = np.ascontiguousarray(field, dtype=np.float32)
+    M, Z, Y, X = f.shape
+    pp = np.ascontiguousarray(p, dtype=np.float32).reshape(3)
+    out = np.empty(M, dtype=np.float32)
+    rc = _load().oracle_interp_column(f.ctypes.data_as(_f32p), M, X, Y, Z,
+                                      pp.ctypes.data_as(_f32p), out.ctypes.data_as(_f32p))
+    if rc != 0:
+        raise ValueError("oracle_interp_column: bad arguments")
     return out
 
 

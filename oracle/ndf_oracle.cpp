@@ -249,4 +249,33 @@ int oracle_ksg2_volume(const float* ref_field, const float* q_field, int64_t M, 
     return bad ? -1 : 0;
 }
 
+int oracle_interp_column(const float* field, int64_t M, int64_t X, int64_t Y, int64_t Z,
+                         const float p[3], float* out) {
+    if (!field || !p || !out || M < 1 || X < 1 || Y < 1 || Z < 1) return -1;
+    const int64_t n[3] = {X, Y, Z};
+    int64_t i0[3], i1[3];
+    float w[3];
+    for (int a = 0; a < 3; ++a) {
+        float u = ((p[a] + 1.0f) * 0.5f) * (float)(n[a] - 1);
+        u = std::min(std::max(u, 0.0f), (float)(n[a] - 1));
+        int64_t f = (int64_t)std::floor(u);
+        i0[a] = n[a] > 1 ? std::min(f, n[a] - 2) : 0;
+        w[a] = u - (float)i0[a];
+        i1[a] = std::min(i0[a] + 1, n[a] - 1);
+    }
+    const int64_t N = X * Y * Z;
+    auto at = [&](int64_t m, int64_t x, int64_t y, int64_t z) { return field[m * N + (z * Y + y) * X + x]; };
+    auto lerp = [](float a, float b, float t) { return a * (1.0f - t) + b * t; };
+    for (int64_t m = 0; m < M; ++m) {
+        const float c00 = lerp(at(m, i0[0], i0[1], i0[2]), at(m, i1[0], i0[1], i0[2]), w[0]);
+        const float c10 = lerp(at(m, i0[0], i1[1], i0[2]), at(m, i1[0], i1[1], i0[2]), w[0]);
+        const float c01 = lerp(at(m, i0[0], i0[1], i1[2]), at(m, i1[0], i0[1], i1[2]), w[0]);
+        const float c11 = lerp(at(m, i0[0], i1[1], i1[2]), at(m, i1[0], i1[1], i1[2]), w[0]);
+        const float c0 = lerp(c00, c10, w[1]);
+        const float c1 = lerp(c01, c11, w[1]);
+        out[m] = lerp(c0, c1, w[2]);
+    }
+    return 0;
+}
+
 }  // extern "C"

@@ -57,6 +57,17 @@ int oracle_ksg2_volume(const float* ref_field, const float* q_field, int64_t M, 
                        int64_t ref_idx, int k, const int64_t* verts, int64_t nverts, double* out,
                        int nthreads);
 
+/* Member column at a continuous position p in [-1,1]^3 (Sec. 4.3: training
+ * samples are read from the ensemble by trilinear interpolation).  field is
+ * float[M][Z][Y][X], vertex i of an axis of n vertices at -1 + 2 i / (n - 1)
+ * (an axis of one vertex is constant).  FP32, in this order per axis:
+ *   u  = ((p + 1) * 0.5) * (n - 1), clamped to [0, n - 1]
+ *   i0 = min(floor(u), n - 2) (0 when n = 1), w = u - i0, i1 = min(i0 + 1, n - 1)
+ *   lerp(a, b, w) = a * (1 - w) + b * w, first along x, then y, then z.
+ * out receives M floats.  Returns 0, or -1 on bad arguments. */
+int oracle_interp_column(const float* field, int64_t M, int64_t X, int64_t Y, int64_t Z,
+                         const float p[3], float* out);
+
 /* number of OpenMP threads a parallel region gets with the given request */
 int oracle_threads(int nthreads);
 

@@ -52,14 +52,14 @@ __host__ __device__ __forceinline__ int padi(int i) { return i + (i >> 2); }  //
 
 // ---------------------------------------------------------------- stage
 // one CTA per reference: sorted reference values and their member ids
-// (refs == nullptr: the single reference ref0)
+// (refs == nullptr: references ref0, ref0 + 1, ...)
 __global__ void __launch_bounds__(1024)
     ksg_stage_kernel(const float* __restrict__ field, int M, int64_t N,
                      const int64_t* __restrict__ refs, int64_t ref0, float* __restrict__ xs_all,
                      int* __restrict__ perm_all) {
     __shared__ float key[kKsgMaxM];
     __shared__ int val[kKsgMaxM];
-    const int64_t ref = refs ? refs[blockIdx.x] : ref0;
+    const int64_t ref = refs ? refs[blockIdx.x] : ref0 + blockIdx.x;
     int n2 = 1;
     while (n2 < M) n2 <<= 1;
     for (int i = threadIdx.x; i < n2; i += blockDim.x) {
@@ -116,6 +116,7 @@ struct KsgArgs {
     float* out;           // out[r * out_stride + (v - v_begin)]
     int64_t out_stride;
     int variant;          // KSG algorithm 1 or 2
+    int paired;           // pairs (reference i, vertex v_begin + i) only, R = v_end - v_begin
     double* dbg_mi;       // debug outputs for (reference 0, vertex v_begin), may be null
     float* dbg_eps;       // eps (algorithm 1) or the x extent (algorithm 2)
     float* dbg_ey;        // the y extent (algorithm 2)
@@ -372,7 +373,8 @@ __global__ void __launch_bounds__(32 * kGroupWarps * kMaxGroupsPerCta, 1)
                 (size_t)group * 2 * M;
     float* epsw = ys + M;
     const int64_t N = A.N, nv = A.v_end - A.v_begin;
-    const unsigned long long items = (unsigned long long)A.R * (unsigned long long)nv;
+    const unsigned long long items =
+        A.paired ? (unsigned long long)nv : (unsigned long long)A.R * (unsigned long long)nv;
     const double psi_k = A.psi[A.k], psi_M = A.psi[M];
     const unsigned lt_mask = (1u << lane) - 1u;
     if (gt < kPad) {
@@ -391,8 +393,8 @@ __global__ void __launch_bounds__(32 * kGroupWarps * kMaxGroupsPerCta, 1)
         group_sync(group);
         const unsigned long long item = ctl->item;
         if (item >= items) break;
-        const int r = (int)(item / (unsigned long long)nv);
-        const int64_t v = A.v_begin + (int64_t)(item - (unsigned long long)r * nv);
+        const int r = A.paired ? (int)item : (int)(item / (unsigned long long)nv);
+        const int64_t v = A.v_begin + (int64_t)(A.paired ? item : item - (unsigned long long)r * nv);
         const float* xs = A.xs_all + (int64_t)r * M;
         const int* perm = A.perm_all + (int64_t)r * M;
         for (int s = gt; s < M; s += GT) {
@@ -512,7 +514,7 @@ __global__ void __launch_bounds__(32 * kGroupWarps * kMaxGroupsPerCta, 1)
 #pragma unroll
             for (int w = 0; w < kGroupWarps; ++w) tot += ctl->part[w];
             const double mi = psi_k - (A.variant == 2 ? 1.0 / A.k : 0.0) + psi_M - tot / (double)M;
-            A.out[(int64_t)r * A.out_stride + (v - A.v_begin)] = (float)mi;
+            A.out[A.paired ? (v - A.v_begin) : (int64_t)r * A.out_stride + (v - A.v_begin)] = (float)mi;
             if (dbg && A.dbg_mi) *A.dbg_mi = mi;
         }
         evals_total += my_evals;
@@ -563,7 +565,7 @@ static cudaError_t launch_ksg_k(ndf_ctx* ctx, KsgArgs A, bool prune) {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
-        const int64_t pairs = (int64_t)A.R * (A.v_end - A.v_begin);
+        const int64_t pairs = A.paired ? (A.v_end - A.v_begin) : (int64_t)A.R * (A.v_end - A.v_begin);
         int64_t grid = (int64_t)ctx->sm_count * per_sm;
         if (grid * gpc > pairs) grid = (pairs + gpc - 1) / gpc;
         kern<<<(unsigned)grid, threads, smem, ctx->stream>>>(
@@ -587,10 +589,13 @@ cudaError_t launch_ksg(ndf_ctx* ctx, const Field& rf, const Field& qf, const int
                        int64_t ref0, int R, int k, int64_t v_begin, int64_t v_end, float* out,
                        int64_t out_stride, bool prune, int G, int VT, double* dbg_mi,
                        float* dbg_eps, int32_t* dbg_nx, int32_t* dbg_ny,
-                       unsigned long long* evals, int variant, float* dbg_ey) {
+                       unsigned long long* evals, int variant, float* dbg_ey, bool paired) {
     const int M = (int)rf.M;
     if (!qf.sorted || R < 1 || v_end <= v_begin) return cudaErrorInvalidValue;
-    if (!d_refs && R != 1) return cudaErrorInvalidValue;
+    if (paired) {
+        if (R != v_end - v_begin) return cudaErrorInvalidValue;
+        prune = true;  // the pair list runs on the pruned kernel's work counter
+    }
     cudaError_t e = ctx->stage_x.reserve(sizeof(float) * (size_t)M * (size_t)R);
     if (e == cudaSuccess) e = ctx->stage_perm.reserve(sizeof(int) * (size_t)M * (size_t)R);
     if (e != cudaSuccess) return e;
@@ -621,6 +626,7 @@ cudaError_t launch_ksg(ndf_ctx* ctx, const Field& rf, const Field& qf, const int
     A.dbg_ny = dbg_ny;
     A.dbg_ey = dbg_ey;
     A.variant = variant;
+    A.paired = paired ? 1 : 0;
     A.evals = evals;
     switch (k + 1) {
         case 2: return launch_ksg_k<2>(ctx, A, prune);

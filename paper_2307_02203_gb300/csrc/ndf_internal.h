@@ -113,15 +113,17 @@ cudaError_t launch_field_stats(ndf_ctx* ctx, const Field& f, int64_t v_begin, in
                                int* d_nonfinite);
 cudaError_t launch_pearson(ndf_ctx* ctx, const Field& rf, const Field& qf, int64_t ref_idx,
                            float* out);
-// KSG MI for R references (d_refs on the device, or the single reference ref0
+// KSG MI for R references (d_refs on the device, or references ref0, ref0 + 1, ...
 // when d_refs is null) against query vertices [v_begin, v_end):
 // out[r * out_stride + (v - v_begin)].  prune selects the exact pruned scan over
-// brute force; G references share a CTA's query tile of VT vertices.
+// brute force; G references share a CTA's query tile of VT vertices.  paired:
+// only the pairs (reference i, vertex v_begin + i), out[i], R = v_end - v_begin.
 cudaError_t launch_ksg(ndf_ctx* ctx, const Field& rf, const Field& qf, const int64_t* d_refs,
                        int64_t ref0, int R, int k, int64_t v_begin, int64_t v_end, float* out,
                        int64_t out_stride, bool prune, int G, int VT, double* dbg_mi,
                        float* dbg_eps, int32_t* dbg_nx, int32_t* dbg_ny,
-                       unsigned long long* evals, int variant = 1, float* dbg_ey = nullptr);
+                       unsigned long long* evals, int variant = 1, float* dbg_ey = nullptr,
+                       bool paired = false);
 
 // Builds Field::sorted (one sort per vertex column, kept with the field).
 cudaError_t ensure_sorted_columns(ndf_ctx* ctx, Field& f);

@@ -78,6 +78,183 @@ __global__ void make_batch_kernel(const int32_t* __restrict__ vref, const int32_
     target[i] = tgt[j];
 }
 
+// ---------------------------------------------------------------- continuous samples (Sec. 4.3)
+// Member columns at continuous positions: out[m][i] = trilinear sample of member m
+// at pos[i].  FP32 with the rounding of every step fixed (no contraction), so
+// that the CPU oracle reproduces the columns bit for bit:
+//   u = ((p + 1) * 0.5) * (n - 1) clamped to [0, n - 1], i0 = min(floor(u), n - 2)
+//   (0 for n = 1), w = u - i0, lerp(a, b, w) = a * (1 - w) + b * w along x, y, z.
+__device__ __forceinline__ void interp_axis(float p, int64_t n, int64_t& i0, int64_t& i1, float& w) {
+    float u = __fmul_rn(__fmul_rn(__fadd_rn(p, 1.0f), 0.5f), (float)(n - 1));
+    u = fminf(fmaxf(u, 0.0f), (float)(n - 1));
+    const int64_t f = (int64_t)floorf(u);
+    i0 = n > 1 ? (f < n - 2 ? f : n - 2) : 0;
+    w = __fsub_rn(u, (float)i0);
+    i1 = i0 + 1 < n - 1 ? i0 + 1 : n - 1;
+}
+
+__device__ __forceinline__ float lerp_rn(float a, float b, float t) {
+    return __fadd_rn(__fmul_rn(a, __fsub_rn(1.0f, t)), __fmul_rn(b, t));
+}
+
+__global__ void interp_columns_kernel(const float* __restrict__ field, int64_t M, int64_t X,
+                                      int64_t Y, int64_t Z, const float* __restrict__ pos,
+                                      int64_t n, float* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t x0, x1, y0, y1, z0, z1;
+    float wx, wy, wz;
+    interp_axis(pos[3 * i + 0], X, x0, x1, wx);
+    interp_axis(pos[3 * i + 1], Y, y0, y1, wy);
+    interp_axis(pos[3 * i + 2], Z, z0, z1, wz);
+    const int64_t N = X * Y * Z;
+    const int64_t o000 = (z0 * Y + y0) * X + x0, o100 = (z0 * Y + y0) * X + x1;
+    const int64_t o010 = (z0 * Y + y1) * X + x0, o110 = (z0 * Y + y1) * X + x1;
+    const int64_t o001 = (z1 * Y + y0) * X + x0, o101 = (z1 * Y + y0) * X + x1;
+    const int64_t o011 = (z1 * Y + y1) * X + x0, o111 = (z1 * Y + y1) * X + x1;
+    for (int64_t m = blockIdx.y; m < M; m += gridDim.y) {
+        const float* f = field + m * N;
+        const float c00 = lerp_rn(__ldg(f + o000), __ldg(f + o100), wx);
+        const float c10 = lerp_rn(__ldg(f + o010), __ldg(f + o110), wx);
+        const float c01 = lerp_rn(__ldg(f + o001), __ldg(f + o101), wx);
+        const float c11 = lerp_rn(__ldg(f + o011), __ldg(f + o111), wx);
+        out[m * n + i] = lerp_rn(lerp_rn(c00, c10, wy), lerp_rn(c01, c11, wy), wz);
+    }
+}
+
+// Pearson r of column i of a against column i of b (Eq. 1), both blocks [M][n]
+// with their FP64 means and 1/sqrt(S); FP64 accumulation, clamped to [-1, 1].
+__global__ void pearson_paired_kernel(const float* __restrict__ a, const double* __restrict__ ma,
+                                      const double* __restrict__ sa, const float* __restrict__ b,
+                                      const double* __restrict__ mb, const double* __restrict__ sb,
+                                      int64_t M, int64_t n, float* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double mua = ma[i], mub = mb[i];
+    double acc = 0.0;
+    for (int64_t m = 0; m < M; ++m)
+        acc = fma((double)__ldg(a + m * n + i) - mua, (double)__ldg(b + m * n + i) - mub, acc);
+    const double r = acc * sa[i] * sb[i];
+    out[i] = (float)fmin(1.0, fmax(-1.0, r));
+}
+
+// batch positions and targets from continuous triples through the bijection
+__global__ void make_batch_pos_kernel(const float* __restrict__ pref, const float* __restrict__ pq,
+                                      const float* __restrict__ tgt, int64_t T, uint64_t a,
+                                      uint64_t c, int64_t base, int64_t B, float* __restrict__ pr,
+                                      float* __restrict__ pqo, float* __restrict__ target) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B) return;
+    const uint64_t j = (a * (uint64_t)(base + i) + c) % (uint64_t)T;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        pr[3 * i + d] = pref[3 * j + d];
+        pqo[3 * i + d] = pq[3 * j + d];
+    }
+    target[i] = tgt[j];
+}
+
+// Scratch of the continuous sampler: position, column and statistics blocks for
+// up to `cap` pairs, reused across calls.
+struct SampleScratch {
+    float *ca = nullptr, *cb = nullptr, *cb_sorted = nullptr;
+    double *ma = nullptr, *sa = nullptr, *mb = nullptr, *sb = nullptr;
+    int64_t cap = 0, M = 0;
+    void release() {
+        void* ps[] = {ca, cb, cb_sorted, ma, sa, mb, sb};
+        for (void* q : ps)
+            if (q) cudaFree(q);
+        *this = SampleScratch();
+    }
+    cudaError_t reserve(int64_t M_, int64_t n) {
+        if (n <= cap && M_ == M) return cudaSuccess;
+        release();
+        cudaError_t e = cudaMalloc(&ca, sizeof(float) * (size_t)M_ * (size_t)n);
+        if (e == cudaSuccess) e = cudaMalloc(&cb, sizeof(float) * (size_t)M_ * (size_t)n);
+        if (e == cudaSuccess) e = cudaMalloc(&cb_sorted, sizeof(float) * (size_t)M_ * (size_t)n);
+        if (e == cudaSuccess) e = cudaMalloc(&ma, sizeof(double) * (size_t)n);
+        if (e == cudaSuccess) e = cudaMalloc(&sa, sizeof(double) * (size_t)n);
+        if (e == cudaSuccess) e = cudaMalloc(&mb, sizeof(double) * (size_t)n);
+        if (e == cudaSuccess) e = cudaMalloc(&sb, sizeof(double) * (size_t)n);
+        if (e != cudaSuccess) {
+            release();
+            return e;
+        }
+        cap = n;
+        M = M_;
+        return cudaSuccess;
+    }
+};
+
+// n triples (p_ref, p_q, R(p_ref, p_q)) at uniform random positions in [-1,1]^3
+// (Sec. 4.3), written to device arrays pref[n][3], pq[n][3], target[n].  Pairs
+// are independent; the estimators run on the interpolated columns, pair by pair.
+static cudaError_t sample_triples_dev(ndf_ctx* ctx, const Field& rf, const Field& qf, int measure,
+                                      int k, int64_t n, uint64_t seed, float* pref, float* pq,
+                                      float* target, SampleScratch& sc) {
+    const int64_t M = rf.M;
+    const int64_t chunk = std::min<int64_t>(n, 65536);
+    cudaError_t e = sc.reserve(M, chunk);
+    if (e != cudaSuccess) return e;
+    const uint64_t key = host_mix(seed ^ 0x434f4e54504f5353ULL);
+    std::vector<float> hp((size_t)chunk * 6);
+    int* d_flag = ctx->flag.as<int>();
+    for (int64_t c0 = 0; c0 < n && e == cudaSuccess; c0 += chunk) {
+        const int64_t nc = std::min(chunk, n - c0);
+        // 24-bit uniform grid on [-1, 1): exact in FP32
+        for (int64_t i = 0; i < nc * 6; ++i)
+            hp[(size_t)i] = (float)((double)(host_rand(key, (uint64_t)(c0 * 6 + i)) >> 40) *
+                                        (2.0 / 16777216.0) - 1.0);
+        std::vector<float> hr((size_t)nc * 3), hq((size_t)nc * 3);
+        for (int64_t i = 0; i < nc; ++i)
+            for (int d = 0; d < 3; ++d) {
+                hr[(size_t)(3 * i + d)] = hp[(size_t)(6 * i + d)];
+                hq[(size_t)(3 * i + d)] = hp[(size_t)(6 * i + 3 + d)];
+            }
+        e = cudaMemcpyAsync(pref + 3 * c0, hr.data(), (size_t)nc * 12, cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(pq + 3 * c0, hq.data(), (size_t)nc * 12, cudaMemcpyHostToDevice, ctx->stream);
+        if (e != cudaSuccess) break;
+        const dim3 grid((unsigned)((nc + 127) / 128), (unsigned)std::min<int64_t>(M, 64));
+        interp_columns_kernel<<<grid, 128, 0, ctx->stream>>>(rf.data, M, rf.X, rf.Y, rf.Z,
+                                                             pref + 3 * c0, nc, sc.ca);
+        interp_columns_kernel<<<grid, 128, 0, ctx->stream>>>(qf.data, M, qf.X, qf.Y, qf.Z,
+                                                             pq + 3 * c0, nc, sc.cb);
+        ctx->launches += 2;
+        Field fa, fb;
+        fa.live = fb.live = true;
+        fa.M = fb.M = M;
+        fa.Z = fb.Z = fa.Y = fb.Y = 1;
+        fa.X = fb.X = fa.N = fb.N = nc;
+        fa.data = sc.ca;
+        fb.data = sc.cb;
+        if (measure == NDF_MEASURE_PEARSON) {
+            fa.mean = sc.ma;
+            fa.inv_norm = sc.sa;
+            fb.mean = sc.mb;
+            fb.inv_norm = sc.sb;
+            e = cudaMemsetAsync(d_flag, 0, 4, ctx->stream);
+            if (e == cudaSuccess) e = launch_field_stats(ctx, fa, 0, nc, d_flag);
+            if (e == cudaSuccess) e = launch_field_stats(ctx, fb, 0, nc, d_flag);
+            if (e == cudaSuccess) {
+                pearson_paired_kernel<<<(unsigned)((nc + 255) / 256), 256, 0, ctx->stream>>>(
+                    sc.ca, sc.ma, sc.sa, sc.cb, sc.mb, sc.sb, M, nc, target + c0);
+                ctx->launches++;
+                e = cudaGetLastError();
+            }
+        } else {
+            fb.sorted = sc.cb_sorted;
+            e = launch_sort_columns(ctx, fb, 0, nc, ctx->stream);
+            if (e == cudaSuccess)
+                e = launch_ksg(ctx, fa, fb, nullptr, 0, (int)nc, k, 0, nc, target + c0, 0, true, 1, 1,
+                               nullptr, nullptr, nullptr, nullptr, nullptr, 1, nullptr, true);
+        }
+        // the host position buffers and the column blocks are reused by the next chunk
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    }
+    return e;
+}
+
 // ---------------------------------------------------------------- decoding (Sec. 5)
 
 struct GridArgs {
@@ -219,6 +396,7 @@ void ndf_train_cfg_default(ndf_train_cfg* c) {
     c->eps = 1e-8f;
     c->seed = 20230705ULL;
     c->time_budget_s = 0.0;
+    c->continuous = 0;
 }
 
 ndf_status ndf_model_create(ndf_ctx* ctx, const int res[4], int measure, uint64_t seed, int64_t X,
@@ -392,6 +570,50 @@ ndf_status ndf_model_info(const ndf_model* m, ndf_model_info_t* info) {
     return NDF_OK;
 }
 
+ndf_status ndf_sample_triples(ndf_ctx* ctx, int ref_field, int query_field, int measure, int k,
+                              int64_t n, uint64_t seed, float* pref, float* pq, float* target) {
+    if (!ctx) return NDF_ERR_ARG;
+    if (!pref || !pq || !target) return fail(ctx, NDF_ERR_ARG, "null pointer");
+    const Field *rf, *qf;
+    ndf_status st = check_pair(ctx, ref_field, query_field, 0, &rf, &qf);
+    if (st != NDF_OK) return st;
+    if (measure != NDF_MEASURE_PEARSON && measure != NDF_MEASURE_MI_KSG)
+        return fail(ctx, NDF_ERR_ARG, "unknown measure %d", measure);
+    if (measure == NDF_MEASURE_MI_KSG && (k < 1 || k >= rf->M || k > kKsgMaxK || rf->M > kKsgMaxM))
+        return fail(ctx, NDF_ERR_ARG, "bad k or M for the KSG targets");
+    if (n < 1 || n > (int64_t(1) << 31)) return fail(ctx, NDF_ERR_ARG, "need 1 <= n <= 2^31");
+    cudaSetDevice(ctx->device);
+    if (measure == NDF_MEASURE_MI_KSG && (st = ensure_psi_table(ctx, rf->M + 1)) != NDF_OK) return st;
+    void *dr, *dq, *dt;
+    bool hr, hq, ht;
+    // device staging for host outputs: three context buffers would alias, so use one
+    const size_t bp = sizeof(float) * 3 * (size_t)n, bt = sizeof(float) * (size_t)n;
+    const bool any_host = pointer_kind(pref) != PTR_DEVICE || pointer_kind(pq) != PTR_DEVICE ||
+                          pointer_kind(target) != PTR_DEVICE;
+    float* stage = nullptr;
+    if (any_host) {
+        cudaError_t e = cudaMalloc(&stage, 2 * bp + bt);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "sampler staging");
+    }
+    hr = pointer_kind(pref) != PTR_DEVICE;
+    hq = pointer_kind(pq) != PTR_DEVICE;
+    ht = pointer_kind(target) != PTR_DEVICE;
+    dr = hr ? (void*)stage : (void*)pref;
+    dq = hq ? (void*)(stage + 3 * n) : (void*)pq;
+    dt = ht ? (void*)(stage + 6 * n) : (void*)target;
+    SampleScratch sc;
+    cudaError_t e = sample_triples_dev(ctx, *rf, *qf, measure, k, n, seed, (float*)dr, (float*)dq,
+                                       (float*)dt, sc);
+    if (e == cudaSuccess && hr) e = cudaMemcpyAsync(pref, dr, bp, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && hq) e = cudaMemcpyAsync(pq, dq, bp, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && ht) e = cudaMemcpyAsync(target, dt, bt, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    sc.release();
+    if (stage) cudaFree(stage);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "continuous sampling");
+    return check_device_status(ctx);
+}
+
 // ---- training (Sec. 4.3)
 ndf_status ndf_train(ndf_ctx* ctx, int ref_field, int query_field, int measure, int k,
                      const ndf_train_cfg* cfg_in, ndf_model** out) {
@@ -428,14 +650,23 @@ ndf_status ndf_train(ndf_ctx* ctx, int ref_field, int query_field, int measure, 
         if (es != cudaSuccess) return bail(cuda_fail(ctx, es, "sorted columns"));
     }
 
-    // ---- training triples
+    // ---- training triples: grid vertex pairs, or (continuous) uniform random
+    // positions with trilinear samples, renewed every pass (Sec. 4.3)
+    const bool cont = cfg.continuous != 0;
     auto t0 = std::chrono::steady_clock::now();
     int32_t *vref = nullptr, *vq = nullptr;
+    float *cpref = nullptr, *cpq = nullptr;
+    SampleScratch sc;
     float *tgt = nullptr, *block = nullptr, *block_sorted = nullptr, *gtgt = nullptr;
     int64_t *dq = nullptr, *drefs = nullptr;
-    cudaError_t e = cudaMalloc(&vref, (size_t)T * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&vq, (size_t)T * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&tgt, (size_t)T * 4);
+    cudaError_t e = cudaMalloc(&tgt, (size_t)T * 4);
+    if (cont) {
+        if (e == cudaSuccess) e = cudaMalloc(&cpref, (size_t)T * 12);
+        if (e == cudaSuccess) e = cudaMalloc(&cpq, (size_t)T * 12);
+    } else {
+        if (e == cudaSuccess) e = cudaMalloc(&vref, (size_t)T * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&vq, (size_t)T * 4);
+    }
     if (e == cudaSuccess) e = cudaMalloc(&block, (size_t)M * Qg * 4);
     if (e == cudaSuccess) e = cudaMalloc(&dq, (size_t)Qg * 8);
     if (e == cudaSuccess) e = cudaMalloc(&gtgt, (size_t)Rg * Qg * 4);
@@ -456,20 +687,22 @@ ndf_status ndf_train(ndf_ctx* ctx, int ref_field, int query_field, int measure, 
         if (e == cudaSuccess) e = cudaMalloc(&blk.inv_norm, (size_t)Qg * 8);
     }
     auto cleanup_data = [&]() {
-        void* ps[] = {vref, vq, tgt, block, block_sorted, dq, gtgt, drefs, blk.mean, blk.inv_norm};
+        void* ps[] = {vref, vq, tgt, block, block_sorted, dq, gtgt, drefs, blk.mean, blk.inv_norm,
+                      cpref, cpq};
         for (void* q : ps)
             if (q) cudaFree(q);
+        sc.release();
     };
     if (e != cudaSuccess) {
         cleanup_data();
         return bail(cuda_fail(ctx, e, "training-set buffers"));
     }
     std::vector<int64_t> hq((size_t)Qg), hrefs((size_t)Rg);
-    std::vector<int32_t> hr((size_t)T), hqv((size_t)T);
+    std::vector<int32_t> hr((size_t)(cont ? 0 : T)), hqv((size_t)(cont ? 0 : T));
     const uint64_t key = host_mix(cfg.seed ^ 0x4e44465452414e53ULL);
     int64_t filled = 0, group = 0;
     int* d_flag = ctx->flag.as<int>();
-    while (filled < T && e == cudaSuccess) {
+    while (!cont && filled < T && e == cudaSuccess) {
         // queries of this group: Qg distinct-ish uniform vertices, sorted for locality
         for (int64_t q = 0; q < Qg; ++q)
             hq[(size_t)q] = (int64_t)(host_rand(key, (uint64_t)(group * 2 * Qg + q)) % (uint64_t)N);
@@ -517,10 +750,12 @@ ndf_status ndf_train(ndf_ctx* ctx, int ref_field, int query_field, int measure, 
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         ++group;
     }
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && !cont)
         e = cudaMemcpyAsync(vref, hr.data(), (size_t)T * 4, cudaMemcpyHostToDevice, ctx->stream);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && !cont)
         e = cudaMemcpyAsync(vq, hqv.data(), (size_t)T * 4, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess && cont)
+        e = sample_triples_dev(ctx, *rf, *qf, measure, k, T, cfg.seed, cpref, cpq, tgt, sc);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {
         cleanup_data();
@@ -539,7 +774,15 @@ ndf_status ndf_train(ndf_ctx* ctx, int ref_field, int query_field, int measure, 
     float lr = cfg.lr;
     double best = 1e300;
     int bad = 0, decays = 0;
+    double extra_gen = 0.0;
     for (int pass = 0; pass < cfg.max_passes && e == cudaSuccess; ++pass) {
+        if (cont && pass > 0) {  // fresh samples every pass
+            const auto g0 = std::chrono::steady_clock::now();
+            e = sample_triples_dev(ctx, *rf, *qf, measure, k, T, cfg.seed + (uint64_t)pass, cpref,
+                                   cpq, tgt, sc);
+            extra_gen += std::chrono::duration<double>(std::chrono::steady_clock::now() - g0).count();
+            if (e != cudaSuccess) break;
+        }
         // a new affine bijection j = a*i + c (mod T) every pass
         uint64_t a = host_rand(key ^ 0x5bd1e995ULL, (uint64_t)pass) % (uint64_t)T;
         if (a == 0) a = 1;
@@ -548,9 +791,14 @@ ndf_status ndf_train(ndf_ctx* ctx, int ref_field, int query_field, int measure, 
         e = cudaMemsetAsync(m->work.loss, 0, 8, ctx->stream);
         for (int64_t base = 0; base < T && e == cudaSuccess; base += B) {
             const int64_t b = T - base < B ? T - base : B;
-            make_batch_kernel<<<(unsigned)((b + 255) / 256), 256, 0, ctx->stream>>>(
-                vref, vq, tgt, T, a, c, base, b, m->X, m->Y, m->Z, m->work.pos,
-                m->work.pos + 3 * B, m->work.target);
+            if (cont)
+                make_batch_pos_kernel<<<(unsigned)((b + 255) / 256), 256, 0, ctx->stream>>>(
+                    cpref, cpq, tgt, T, a, c, base, b, m->work.pos, m->work.pos + 3 * B,
+                    m->work.target);
+            else
+                make_batch_kernel<<<(unsigned)((b + 255) / 256), 256, 0, ctx->stream>>>(
+                    vref, vq, tgt, T, a, c, base, b, m->X, m->Y, m->Z, m->work.pos,
+                    m->work.pos + 3 * B, m->work.target);
             ctx->launches++;
             e = model_step(m, m->work.pos, m->work.pos + 3 * B, m->work.target, b, lr, cfg.beta1,
                            cfg.beta2, cfg.eps, true);
@@ -575,7 +823,9 @@ ndf_status ndf_train(ndf_ctx* ctx, int ref_field, int query_field, int measure, 
         const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t1).count();
         if (cfg.time_budget_s > 0.0 && el > cfg.time_budget_s) break;
     }
-    m->train_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t1).count();
+    m->train_seconds =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t1).count() - extra_gen;
+    m->gen_seconds += extra_gen;
     cleanup_data();
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "training"));
     *out = m;

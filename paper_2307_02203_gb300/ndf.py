@@ -75,6 +75,8 @@ _sig("ndf_field_stats", ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp])
 _sig("ndf_pearson", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, _vp])
 _sig("ndf_mi_ksg", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, ctypes.c_int, _vp])
 _sig("ndf_mi_ksg2", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, ctypes.c_int, _vp])
+_sig("ndf_sample_triples", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, _i64, ctypes.c_uint64, _vp, _vp, _vp])
 _sig("ndf_render_volume", ctypes.c_int, [_vp, _vp, _vp, _i64, _i64, _i64, _vp, _vp])
 _sig("ndf_pearson_batch", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int,
                                          ctypes.c_int, _vp])
@@ -98,7 +100,8 @@ class TrainCfg(ctypes.Structure):
                 ("refs_per_group", _i64), ("queries_per_group", _i64), ("max_passes", ctypes.c_int),
                 ("patience", ctypes.c_int), ("max_decays", ctypes.c_int), ("lr", ctypes.c_float),
                 ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
-                ("seed", ctypes.c_uint64), ("time_budget_s", ctypes.c_double)]
+                ("seed", ctypes.c_uint64), ("time_budget_s", ctypes.c_double),
+                ("continuous", ctypes.c_int32)]
 
 
 class ModelInfo(ctypes.Structure):
@@ -311,6 +314,14 @@ def ndf_pearson_noalloc(ref_field, query_field, M, N, ref_idx, out, cuda_stream=
                                   _addr(out), cuda_stream)
     if st != NDF_OK:
         raise NdfError(st, "ndf_pearson_noalloc", "see include/ndf.h for the argument limits")
+
+
+def ndf_sample_triples(ctx, ref_field: int, query_field: int, measure: int, k: int, n: int,
+                       seed: int, pref, pq, target) -> None:
+    """n continuous-position training triples: pref/pq [n][3], target [n]."""
+    _check(ctx, _lib.ndf_sample_triples(ctx, ref_field, query_field, measure, k, n, seed,
+                                        _addr(pref), _addr(pq), _addr(target)),
+           "ndf_sample_triples")
 
 
 def ndf_train_cfg_default() -> TrainCfg:
