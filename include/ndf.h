@@ -303,6 +303,68 @@ ndf_status ndf_model_step(ndf_model* model, const float* p_ref, const float* p_q
 ndf_status ndf_model_forward(ndf_model* model, const float* p_ref, const float* p_query,
                              int64_t B, float* out);
 
+/* ---- the paper's NDF architecture (Sec. 4.1-4.2, Fig. 2; row f2) ---------- */
+
+/* Hidden-layer activations: ReLU, Snake x + sin^2 x, SnakeAlt x / 2 + sin^2 x. */
+typedef enum { NDF_ACT_RELU = 0, NDF_ACT_SNAKE = 1, NDF_ACT_SNAKEALT = 2 } ndf_activation;
+
+/* Input embedding [p, Fourier features (Eq. 4: sin / cos(2^i pi p_j), i < n_freq),
+ * hash-grid features] -> encoder MLP (enc_layers linear layers of `width`,
+ * activation between them) -> element-wise product of the two positions'
+ * latents -> decoder MLP (dec_layers, last to 1) -> tanh (Pearson) or softplus
+ * (MI).  Hash grid: `levels` levels of base_res * 2^l points per axis
+ * (corner-aligned on [-1,1]^3), min(2^log2_table, R^3) entries of `feat`
+ * features each (dense index when the level fits, else the spatial hash
+ * x*1 ^ y*2654435761 ^ z*805459861 mod 2^T).  ndf_hash_arch_default gives the
+ * paper's 6 levels from 16^3, L = 12, 6 + 6 layers of 128, SnakeAlt; the
+ * table size defaults to 2^22 per level (the paper's 2^30 would need 51 GB of
+ * FP32 training state). */
+typedef struct {
+    int32_t levels, base_res, log2_table, feat, n_freq, width, enc_layers, dec_layers, act;
+} ndf_hash_arch;
+void ndf_hash_arch_default(ndf_hash_arch* arch);
+
+typedef struct ndf_hash_model ndf_hash_model;
+
+/* A model decoding grids of X x Y x Z vertices.  cross = 0: one encoder and
+ * grid for both positions (self fields, Phi(p1, p2) = Phi(p2, p1) exactly);
+ * cross = 1: separate encoders (0 reference, 1 query).  Parameters follow the
+ * layout of the oracle (per encoder: level tables, then W[out][in], b per layer;
+ * then the decoder layers), FP32, with Adam moments.  Initialisation: tables
+ * U(-1e-4, 1e-4), weights U(+-sqrt(6 / fan_in)), biases 0 (seeded). */
+ndf_status ndf_hash_model_create(ndf_ctx* ctx, const ndf_hash_arch* arch, int measure, int cross,
+                                 uint64_t seed, int64_t X, int64_t Y, int64_t Z,
+                                 ndf_hash_model** out);
+void ndf_hash_model_free(ndf_hash_model* m);
+int64_t ndf_hash_model_param_count(const ndf_hash_model* m);
+ndf_status ndf_hash_model_get_params(ndf_hash_model* m, float* out);      /* host or device */
+ndf_status ndf_hash_model_set_params(ndf_hash_model* m, const float* in); /* host or device */
+
+/* out[B] = network(pr[b], pq[b]); pr, pq [B][3] positions in [-1,1]^3. */
+ndf_status ndf_hash_model_forward(ndf_hash_model* m, const float* pr, const float* pq, int64_t B,
+                                  float* out);
+
+/* One step of the mean L1 loss (Eq. 3): gradient of every parameter (copied to
+ * grad_out when not NULL), the loss in *loss_out, and with apply != 0 an Adam
+ * update (beta 0.9 / 0.999, eps 1e-8) with learning rate lr. */
+ndf_status ndf_hash_model_step(ndf_hash_model* m, const float* pr, const float* pq,
+                               const float* target, int64_t B, float lr, int apply,
+                               float* grad_out, double* loss_out);
+
+/* Training on continuous-position samples (ndf_sample_triples), n_triples fresh
+ * pairs every pass, Adam and the plateau schedule of cfg (Sec. 4.3). */
+ndf_status ndf_hash_train(ndf_ctx* ctx, int ref_field, int query_field, int measure, int k,
+                          const ndf_hash_arch* arch, const ndf_train_cfg* cfg,
+                          ndf_hash_model** out);
+
+/* Passes, last pass loss, sampling and training seconds, Adam steps. */
+ndf_status ndf_hash_model_info(const ndf_hash_model* m, int* passes, double* last_loss,
+                               double* gen_seconds, double* train_seconds, int64_t* adam_steps);
+
+/* The dependence volume of one reference vertex (vertex-aligned positions):
+ * the reference is encoded once, the N query vertices in chunks of 65536. */
+ndf_status ndf_hash_infer(ndf_hash_model* m, int64_t ref_idx, float* out);
+
 /* ---- headless volume rendering (Sec. 5, Sec. 6.5) -------------------------- */
 
 /* Direct volume rendering with a transfer function, or an iso-surface. */

@@ -15,6 +15,9 @@ Functions and the passages they follow:
   digamma_int              -- psi(1) = -gamma, psi(n+1) = psi(n) + 1/n
   ndf_*, adam_step         -- Sec. 4: dense-grid NDF forward, L1 loss (Eq. 3), hand-written
                               backward, Adam update, all FP64
+  hash_*                   -- Sec. 4.1-4.2: the paper's NDF architecture (hash grid, Fourier
+                              features, Snake/SnakeAlt MLP encoders, product merge, decoder),
+                              forward and hand-written backward in FP64 (hash_net_oracle.h)
   render                   -- Sec. 5 / Sec. 6.5: headless ray-march of a dependence volume
                               (DVR with a transfer function, iso-surface, difference of two
                               fields), FP64 per pixel (render_oracle.h has the definitions)
@@ -31,8 +34,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libndf_oracle.so")
-_SOURCES = ["ndf_oracle.cpp", "ndf_net_oracle.cpp", "render_oracle.cpp"]
-_HEADERS = ["ndf_oracle.h", "ndf_net_oracle.h", "render_oracle.h"]
+_SOURCES = ["ndf_oracle.cpp", "ndf_net_oracle.cpp", "render_oracle.cpp", "hash_net_oracle.cpp"]
+_HEADERS = ["ndf_oracle.h", "ndf_net_oracle.h", "render_oracle.h", "hash_net_oracle.h"]
 _lock = threading.Lock()
 _lib = None
 
@@ -75,6 +78,21 @@ class RenderCfg(ctypes.Structure):
                 ("tf", ctypes.POINTER(ctypes.c_double))]
 
 
+class HashShape(ctypes.Structure):
+    """Shape of the paper's NDF architecture (see hash_net_oracle.h)."""
+
+    _fields_ = [(n, ctypes.c_int32) for n in ("levels", "base_res", "log2_table", "feat", "n_freq",
+                                               "width", "enc_layers", "dec_layers", "n_enc",
+                                               "measure", "act")]
+
+
+def hash_shape(**kw):
+    s = HashShape()
+    for n, _ in HashShape._fields_:
+        setattr(s, n, int(kw[n]))
+    return s
+
+
 def _load():
     global _lib
     with _lock:
@@ -104,6 +122,14 @@ def _load():
             lib.oracle_interp_column.restype = ctypes.c_int
             lib.oracle_interp_column.argtypes = [_f32p, ctypes.c_int64, ctypes.c_int64,
                                                  ctypes.c_int64, ctypes.c_int64, _f32p, _f32p]
+            lib.oracle_hash_param_count.restype = ctypes.c_int64
+            lib.oracle_hash_param_count.argtypes = [ctypes.POINTER(HashShape)]
+            lib.oracle_hash_forward.restype = ctypes.c_int
+            lib.oracle_hash_forward.argtypes = [ctypes.POINTER(HashShape), _f64p, ctypes.c_int64,
+                                                _f64p, _f64p, _f64p]
+            lib.oracle_hash_loss_grad.restype = ctypes.c_int
+            lib.oracle_hash_loss_grad.argtypes = [ctypes.POINTER(HashShape), _f64p, ctypes.c_int64,
+                                                  _f64p, _f64p, _f64p, _f64p, _f64p]
             lib.oracle_threads.restype = ctypes.c_int
             lib.oracle_threads.argtypes = [ctypes.c_int]
             lib.oracle_render.restype = ctypes.c_int
@@ -257,6 +283,42 @@ def interp_column(field, p):
     if rc != 0:
         raise ValueError("oracle_interp_column: bad arguments")
     return out
+
+
+def hash_param_count(shape) -> int:
+    n = _load().oracle_hash_param_count(ctypes.byref(shape))
+    if n < 0:
+        raise ValueError("bad hash-network shape")
+    return int(n)
+
+
+def hash_forward(shape, params, pr, pq):
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    a = np.ascontiguousarray(pr, dtype=np.float64).reshape(-1, 3)
+    b = np.ascontiguousarray(pq, dtype=np.float64).reshape(-1, 3)
+    out = np.empty(a.shape[0], dtype=np.float64)
+    rc = _load().oracle_hash_forward(ctypes.byref(shape), p.ctypes.data_as(_f64p), a.shape[0],
+                                     a.ctypes.data_as(_f64p), b.ctypes.data_as(_f64p),
+                                     out.ctypes.data_as(_f64p))
+    if rc != 0:
+        raise ValueError("oracle_hash_forward: bad arguments")
+    return out
+
+
+def hash_loss_grad(shape, params, pr, pq, target):
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    a = np.ascontiguousarray(pr, dtype=np.float64).reshape(-1, 3)
+    b = np.ascontiguousarray(pq, dtype=np.float64).reshape(-1, 3)
+    t = np.ascontiguousarray(target, dtype=np.float64)
+    loss = ctypes.c_double(0.0)
+    grad = np.empty(p.shape[0], dtype=np.float64)
+    rc = _load().oracle_hash_loss_grad(ctypes.byref(shape), p.ctypes.data_as(_f64p), a.shape[0],
+                                       a.ctypes.data_as(_f64p), b.ctypes.data_as(_f64p),
+                                       t.ctypes.data_as(_f64p), ctypes.byref(loss),
+                                       grad.ctypes.data_as(_f64p))
+    if rc != 0:
+        raise ValueError("oracle_hash_loss_grad: bad arguments")
+    return loss.value, grad
 
 
 def render(vol_a, vol_b, *, eye, target, up, fov_y_deg, width, height, step, mode, tf,

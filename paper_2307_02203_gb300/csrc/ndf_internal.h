@@ -131,6 +131,44 @@ cudaError_t ensure_sorted_columns(ndf_ctx* ctx, Field& f);
 cudaError_t launch_sort_columns(ndf_ctx* ctx, const Field& f, int64_t v_begin, int64_t v_end,
                                 cudaStream_t stream);
 
+// Scratch of the continuous sampler: position, column and statistics blocks for
+// up to `cap` pairs, reused across calls.
+struct SampleScratch {
+    float *ca = nullptr, *cb = nullptr, *cb_sorted = nullptr;
+    double *ma = nullptr, *sa = nullptr, *mb = nullptr, *sb = nullptr;
+    int64_t cap = 0, M = 0;
+    void release() {
+        void* ps[] = {ca, cb, cb_sorted, ma, sa, mb, sb};
+        for (void* q : ps)
+            if (q) cudaFree(q);
+        *this = SampleScratch();
+    }
+    cudaError_t reserve(int64_t M_, int64_t n) {
+        if (n <= cap && M_ == M) return cudaSuccess;
+        release();
+        cudaError_t e = cudaMalloc(&ca, sizeof(float) * (size_t)M_ * (size_t)n);
+        if (e == cudaSuccess) e = cudaMalloc(&cb, sizeof(float) * (size_t)M_ * (size_t)n);
+        if (e == cudaSuccess) e = cudaMalloc(&cb_sorted, sizeof(float) * (size_t)M_ * (size_t)n);
+        if (e == cudaSuccess) e = cudaMalloc(&ma, sizeof(double) * (size_t)n);
+        if (e == cudaSuccess) e = cudaMalloc(&sa, sizeof(double) * (size_t)n);
+        if (e == cudaSuccess) e = cudaMalloc(&mb, sizeof(double) * (size_t)n);
+        if (e == cudaSuccess) e = cudaMalloc(&sb, sizeof(double) * (size_t)n);
+        if (e != cudaSuccess) {
+            release();
+            return e;
+        }
+        cap = n;
+        M = M_;
+        return cudaSuccess;
+    }
+};
+
+// n continuous-position training triples (Sec. 4.3) into device arrays
+// pref[n][3], pq[n][3], target[n] (ndf_sample_triples without the host side).
+cudaError_t sample_triples_dev(ndf_ctx* ctx, const Field& rf, const Field& qf, int measure, int k,
+                               int64_t n, uint64_t seed, float* pref, float* pq, float* target,
+                               SampleScratch& sc);
+
 constexpr int kKsgMaxM = 4096;
 constexpr int kKsgMaxK = 16;
 

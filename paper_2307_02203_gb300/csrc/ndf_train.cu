@@ -154,44 +154,12 @@ __global__ void make_batch_pos_kernel(const float* __restrict__ pref, const floa
     target[i] = tgt[j];
 }
 
-// Scratch of the continuous sampler: position, column and statistics blocks for
-// up to `cap` pairs, reused across calls.
-struct SampleScratch {
-    float *ca = nullptr, *cb = nullptr, *cb_sorted = nullptr;
-    double *ma = nullptr, *sa = nullptr, *mb = nullptr, *sb = nullptr;
-    int64_t cap = 0, M = 0;
-    void release() {
-        void* ps[] = {ca, cb, cb_sorted, ma, sa, mb, sb};
-        for (void* q : ps)
-            if (q) cudaFree(q);
-        *this = SampleScratch();
-    }
-    cudaError_t reserve(int64_t M_, int64_t n) {
-        if (n <= cap && M_ == M) return cudaSuccess;
-        release();
-        cudaError_t e = cudaMalloc(&ca, sizeof(float) * (size_t)M_ * (size_t)n);
-        if (e == cudaSuccess) e = cudaMalloc(&cb, sizeof(float) * (size_t)M_ * (size_t)n);
-        if (e == cudaSuccess) e = cudaMalloc(&cb_sorted, sizeof(float) * (size_t)M_ * (size_t)n);
-        if (e == cudaSuccess) e = cudaMalloc(&ma, sizeof(double) * (size_t)n);
-        if (e == cudaSuccess) e = cudaMalloc(&sa, sizeof(double) * (size_t)n);
-        if (e == cudaSuccess) e = cudaMalloc(&mb, sizeof(double) * (size_t)n);
-        if (e == cudaSuccess) e = cudaMalloc(&sb, sizeof(double) * (size_t)n);
-        if (e != cudaSuccess) {
-            release();
-            return e;
-        }
-        cap = n;
-        M = M_;
-        return cudaSuccess;
-    }
-};
-
 // n triples (p_ref, p_q, R(p_ref, p_q)) at uniform random positions in [-1,1]^3
 // (Sec. 4.3), written to device arrays pref[n][3], pq[n][3], target[n].  Pairs
 // are independent; the estimators run on the interpolated columns, pair by pair.
-static cudaError_t sample_triples_dev(ndf_ctx* ctx, const Field& rf, const Field& qf, int measure,
-                                      int k, int64_t n, uint64_t seed, float* pref, float* pq,
-                                      float* target, SampleScratch& sc) {
+cudaError_t sample_triples_dev(ndf_ctx* ctx, const Field& rf, const Field& qf, int measure, int k,
+                               int64_t n, uint64_t seed, float* pref, float* pq, float* target,
+                               SampleScratch& sc) {
     const int64_t M = rf.M;
     const int64_t chunk = std::min<int64_t>(n, 65536);
     cudaError_t e = sc.reserve(M, chunk);

@@ -28,6 +28,14 @@ NDF_PREC_FP32, NDF_PREC_BF16X3, NDF_PREC_TF32 = 0, 1, 2
 NDF_MEASURE_PEARSON, NDF_MEASURE_MI_KSG = 0, 1
 NDF_KSG_BRUTE, NDF_KSG_PRUNED = 0, 1
 NDF_RENDER_DVR, NDF_RENDER_ISO = 0, 1
+NDF_ACT_RELU, NDF_ACT_SNAKE, NDF_ACT_SNAKEALT = 0, 1, 2
+
+
+class HashArch(ctypes.Structure):
+    """ndf_hash_arch (include/ndf.h); fill with ndf_hash_arch_default()."""
+
+    _fields_ = [(n, ctypes.c_int32) for n in ("levels", "base_res", "log2_table", "feat", "n_freq",
+                                               "width", "enc_layers", "dec_layers", "act")]
 
 
 class RenderCfg(ctypes.Structure):
@@ -78,6 +86,24 @@ _sig("ndf_mi_ksg2", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, ctypes
 _sig("ndf_sample_triples", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_int, _i64, ctypes.c_uint64, _vp, _vp, _vp])
 _sig("ndf_render_volume", ctypes.c_int, [_vp, _vp, _vp, _i64, _i64, _i64, _vp, _vp])
+_sig("ndf_hash_arch_default", None, [_vp])
+_sig("ndf_hash_model_create", ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                             _i64, _i64, _i64, ctypes.POINTER(_vp)])
+_sig("ndf_hash_model_free", None, [_vp])
+_sig("ndf_hash_model_param_count", _i64, [_vp])
+_sig("ndf_hash_model_get_params", ctypes.c_int, [_vp, _vp])
+_sig("ndf_hash_model_set_params", ctypes.c_int, [_vp, _vp])
+_sig("ndf_hash_model_forward", ctypes.c_int, [_vp, _vp, _vp, _i64, _vp])
+_sig("ndf_hash_model_step", ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, ctypes.c_float, ctypes.c_int,
+                                           _vp, ctypes.POINTER(ctypes.c_double)])
+_sig("ndf_hash_train", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      _vp, _vp, ctypes.POINTER(_vp)])
+_sig("ndf_hash_model_info", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(_i64)])
+_sig("ndf_hash_infer", ctypes.c_int, [_vp, _i64, _vp])
 _sig("ndf_pearson_batch", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int,
                                          ctypes.c_int, _vp])
 _sig("ndf_set_ksg_algorithm", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int])
@@ -306,6 +332,83 @@ def ndf_render_volume(ctx, vol_a, vol_b, X: int, Y: int, Z: int, out, *, eye, ta
     _check(ctx, _lib.ndf_render_volume(ctx, _addr(vol_a), None if vol_b is None else _addr(vol_b),
                                        X, Y, Z, ctypes.byref(c), _addr(out)),
            "ndf_render_volume")
+
+
+class _HashModel:
+    """A hash-grid NDF handle; holds its context for error strings."""
+
+    def __init__(self, ctx, ptr):
+        self.ctx, self.ptr = ctx, ptr
+
+    @property
+    def _as_parameter_(self):
+        return self.ptr
+
+
+def ndf_hash_arch_default() -> HashArch:
+    a = HashArch()
+    _lib.ndf_hash_arch_default(ctypes.byref(a))
+    return a
+
+
+def ndf_hash_model_create(ctx, arch: HashArch, measure: int, cross: bool, seed: int, X: int, Y: int,
+                          Z: int):
+    out = _vp()
+    _check(ctx, _lib.ndf_hash_model_create(ctx, ctypes.byref(arch), measure, int(bool(cross)), seed,
+                                           X, Y, Z, ctypes.byref(out)), "ndf_hash_model_create")
+    return _HashModel(ctx, out)
+
+
+def ndf_hash_model_free(m) -> None:
+    _lib.ndf_hash_model_free(m)
+
+
+def ndf_hash_model_param_count(m) -> int:
+    return int(_lib.ndf_hash_model_param_count(m))
+
+
+def ndf_hash_model_get_params(m, out) -> None:
+    _check(m.ctx, _lib.ndf_hash_model_get_params(m, _addr(out)), "ndf_hash_model_get_params")
+
+
+def ndf_hash_model_set_params(m, params) -> None:
+    _check(m.ctx, _lib.ndf_hash_model_set_params(m, _addr(params)), "ndf_hash_model_set_params")
+
+
+def ndf_hash_model_forward(m, pr, pq, out) -> None:
+    B = len(out)
+    _check(m.ctx, _lib.ndf_hash_model_forward(m, _addr(pr), _addr(pq), B, _addr(out)),
+           "ndf_hash_model_forward")
+
+
+def ndf_hash_model_step(m, pr, pq, target, lr: float, apply: bool, grad_out=None) -> float:
+    loss = ctypes.c_double(0.0)
+    _check(m.ctx, _lib.ndf_hash_model_step(m, _addr(pr), _addr(pq), _addr(target), len(target),
+                                           lr, int(bool(apply)),
+                                           None if grad_out is None else _addr(grad_out),
+                                           ctypes.byref(loss)), "ndf_hash_model_step")
+    return loss.value
+
+
+def ndf_hash_train(ctx, ref_field: int, query_field: int, measure: int, k: int, arch: HashArch,
+                   cfg=None):
+    out = _vp()
+    _check(ctx, _lib.ndf_hash_train(ctx, ref_field, query_field, measure, k, ctypes.byref(arch),
+                                    None if cfg is None else ctypes.byref(cfg), ctypes.byref(out)),
+           "ndf_hash_train")
+    return _HashModel(ctx, out)
+
+
+def ndf_hash_model_info(m) -> dict:
+    p, ls, g, t, a = ctypes.c_int(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), _i64()
+    _check(m.ctx, _lib.ndf_hash_model_info(m, ctypes.byref(p), ctypes.byref(ls), ctypes.byref(g),
+                                           ctypes.byref(t), ctypes.byref(a)), "ndf_hash_model_info")
+    return {"passes": p.value, "last_loss": ls.value, "gen_seconds": g.value,
+            "train_seconds": t.value, "adam_steps": a.value}
+
+
+def ndf_hash_infer(m, ref_idx: int, out) -> None:
+    _check(m.ctx, _lib.ndf_hash_infer(m, ref_idx, _addr(out)), "ndf_hash_infer")
 
 
 def ndf_pearson_noalloc(ref_field, query_field, M, N, ref_idx, out, cuda_stream=None) -> None:
