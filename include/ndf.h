@@ -308,6 +308,15 @@ ndf_status ndf_model_forward(ndf_model* model, const float* p_ref, const float* 
 /* Hidden-layer activations: ReLU, Snake x + sin^2 x, SnakeAlt x / 2 + sin^2 x. */
 typedef enum { NDF_ACT_RELU = 0, NDF_ACT_SNAKE = 1, NDF_ACT_SNAKEALT = 2 } ndf_activation;
 
+/* Feature merge (Sec. 4.1): the paper's element-wise product, and the
+ * alternatives it compares against (sum, absolute difference, concatenation). */
+typedef enum {
+    NDF_MERGE_PRODUCT = 0,
+    NDF_MERGE_SUM = 1,
+    NDF_MERGE_ABSDIFF = 2,
+    NDF_MERGE_CONCAT = 3
+} ndf_merge;
+
 /* Input embedding [p, Fourier features (Eq. 4: sin / cos(2^i pi p_j), i < n_freq),
  * hash-grid features] -> encoder MLP (enc_layers linear layers of `width`,
  * activation between them) -> element-wise product of the two positions'
@@ -316,11 +325,13 @@ typedef enum { NDF_ACT_RELU = 0, NDF_ACT_SNAKE = 1, NDF_ACT_SNAKEALT = 2 } ndf_a
  * (corner-aligned on [-1,1]^3), min(2^log2_table, R^3) entries of `feat`
  * features each (dense index when the level fits, else the spatial hash
  * x*1 ^ y*2654435761 ^ z*805459861 mod 2^T).  ndf_hash_arch_default gives the
- * paper's 6 levels from 16^3, L = 12, 6 + 6 layers of 128, SnakeAlt; the
- * table size defaults to 2^22 per level (the paper's 2^30 would need 51 GB of
- * FP32 training state). */
+ * paper's 6 levels from 16^3, L = 12, 6 + 6 layers of 128, SnakeAlt, product
+ * merge; the table size defaults to 2^22 per level (the paper's 2^30 would
+ * need 51 GB of FP32 training state).  enc_layers = 0 is the grid-only ablation
+ * (Sec. 6.4: the latent is the embedding itself). */
 typedef struct {
     int32_t levels, base_res, log2_table, feat, n_freq, width, enc_layers, dec_layers, act;
+    int32_t merge; /* ndf_merge */
 } ndf_hash_arch;
 void ndf_hash_arch_default(ndf_hash_arch* arch);
 

@@ -83,13 +83,14 @@ class HashShape(ctypes.Structure):
 
     _fields_ = [(n, ctypes.c_int32) for n in ("levels", "base_res", "log2_table", "feat", "n_freq",
                                                "width", "enc_layers", "dec_layers", "n_enc",
-                                               "measure", "act")]
+                                               "measure", "act", "merge")]
 
 
 def hash_shape(**kw):
+    """Fields of HashShape by name; merge defaults to 0 (product)."""
     s = HashShape()
     for n, _ in HashShape._fields_:
-        setattr(s, n, int(kw[n]))
+        setattr(s, n, int(kw.get(n, 0) if n == "merge" else kw[n]))
     return s
 
 

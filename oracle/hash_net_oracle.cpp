@@ -12,7 +12,7 @@ namespace {
 const double kPi = 3.14159265358979323846;
 
 struct Layout {
-    int levels, F, L, c, le, ld, n_enc, din;
+    int levels, F, L, c, le, ld, n_enc, din, merge, dlat, ddec;
     std::vector<int64_t> res, entries;
     int64_t enc_size = 0, total = 0;
     std::vector<int64_t> table_off;      // within an encoder
@@ -21,8 +21,8 @@ struct Layout {
     bool ok = false;
     explicit Layout(const oracle_hash_shape& s) {
         if (s.levels < 1 || s.base_res < 2 || s.log2_table < 1 || s.log2_table > 30 || s.feat < 1 ||
-            s.n_freq < 0 || s.width < 1 || s.enc_layers < 1 || s.dec_layers < 1 ||
-            (s.n_enc != 1 && s.n_enc != 2) || s.act < 0 || s.act > 2)
+            s.n_freq < 0 || s.width < 1 || s.enc_layers < 0 || s.dec_layers < 1 ||
+            (s.n_enc != 1 && s.n_enc != 2) || s.act < 0 || s.act > 2 || s.merge < 0 || s.merge > 3)
             return;
         levels = s.levels;
         F = s.feat;
@@ -31,7 +31,10 @@ struct Layout {
         le = s.enc_layers;
         ld = s.dec_layers;
         n_enc = s.n_enc;
+        merge = s.merge;
         din = 3 + 6 * L + levels * F;
+        dlat = le > 0 ? c : din;
+        ddec = merge == 3 ? 2 * dlat : dlat;
         int64_t o = 0;
         for (int l = 0; l < levels; ++l) {
             const int64_t R = (int64_t)s.base_res << l;
@@ -52,9 +55,9 @@ struct Layout {
         enc_size = o;
         o = enc_size * n_enc;
         for (int k = 0; k < ld; ++k) {
-            const int64_t out = k == ld - 1 ? 1 : c;
+            const int64_t out = k == ld - 1 ? 1 : c, in = k == 0 ? ddec : c;
             dec_w.push_back(o);
-            o += out * c;
+            o += out * in;
             dec_b.push_back(o);
             o += out;
         }
@@ -108,6 +111,7 @@ struct EncCache {
     std::vector<std::vector<double>> pre;   // pre-activations per layer
     std::vector<std::vector<double>> post;  // layer outputs (after activation when any)
     std::vector<Corners> cs;                // per level
+    std::vector<double> lat;                // the latent (last layer output or x0)
 };
 
 void encode(const Layout& Ly, const oracle_hash_shape& s, const double* P, int e, const double p[3],
@@ -137,6 +141,7 @@ void encode(const Layout& Ly, const oracle_hash_shape& s, const double* P, int e
     }
     C.pre.assign(Ly.le, {});
     C.post.assign(Ly.le, {});
+    C.lat = C.x0;
     const std::vector<double>* in = &C.x0;
     for (int k = 0; k < Ly.le; ++k) {
         const int64_t nin = k == 0 ? Ly.din : Ly.c;
@@ -151,6 +156,7 @@ void encode(const Layout& Ly, const oracle_hash_shape& s, const double* P, int e
             C.post[k][o] = k < Ly.le - 1 ? act(s.act, a) : a;
         }
         in = &C.post[k];
+        C.lat = C.post[k];
     }
 }
 
@@ -199,19 +205,54 @@ double decode(const Layout& Ly, const oracle_hash_shape& s, const double* P, con
     pres.assign(Ly.ld, {});
     std::vector<double> h = z;
     for (int k = 0; k < Ly.ld; ++k) {
-        const int nout = k == Ly.ld - 1 ? 1 : Ly.c;
+        const int nout = k == Ly.ld - 1 ? 1 : Ly.c, nin = k == 0 ? Ly.ddec : Ly.c;
         ins[k] = h;
         pres[k].assign(nout, 0.0);
         std::vector<double> nh(nout);
         for (int o = 0; o < nout; ++o) {
             double a = P[Ly.dec_b[k] + o];
-            for (int i = 0; i < Ly.c; ++i) a += P[Ly.dec_w[k] + (int64_t)o * Ly.c + i] * h[i];
+            for (int i = 0; i < nin; ++i) a += P[Ly.dec_w[k] + (int64_t)o * nin + i] * h[i];
             pres[k][o] = a;
             nh[o] = k < Ly.ld - 1 ? act(s.act, a) : a;
         }
         h = nh;
     }
     return h[0];
+}
+
+std::vector<double> merge_fwd(const Layout& Ly, const std::vector<double>& a, const std::vector<double>& b) {
+    std::vector<double> z(Ly.ddec);
+    for (int i = 0; i < Ly.dlat; ++i) {
+        if (Ly.merge == 0) z[i] = a[i] * b[i];
+        else if (Ly.merge == 1) z[i] = a[i] + b[i];
+        else if (Ly.merge == 2) z[i] = std::fabs(a[i] - b[i]);
+        else {
+            z[i] = a[i];
+            z[Ly.dlat + i] = b[i];
+        }
+    }
+    return z;
+}
+
+void merge_bwd(const Layout& Ly, const std::vector<double>& g, const std::vector<double>& a,
+               const std::vector<double>& b, std::vector<double>& ga, std::vector<double>& gb) {
+    ga.assign(Ly.dlat, 0.0);
+    gb.assign(Ly.dlat, 0.0);
+    for (int i = 0; i < Ly.dlat; ++i) {
+        if (Ly.merge == 0) {
+            ga[i] = g[i] * b[i];
+            gb[i] = g[i] * a[i];
+        } else if (Ly.merge == 1) {
+            ga[i] = gb[i] = g[i];
+        } else if (Ly.merge == 2) {
+            const double sg = a[i] > b[i] ? 1.0 : (a[i] < b[i] ? -1.0 : 0.0);
+            ga[i] = g[i] * sg;
+            gb[i] = -g[i] * sg;
+        } else {
+            ga[i] = g[i];
+            gb[i] = g[Ly.dlat + i];
+        }
+    }
 }
 
 }  // namespace
@@ -233,8 +274,7 @@ int oracle_hash_forward(const oracle_hash_shape* s, const double* params, int64_
         EncCache cr, cq;
         encode(Ly, *s, params, 0, pr + 3 * b, cr);
         encode(Ly, *s, params, Ly.n_enc - 1, pq + 3 * b, cq);
-        std::vector<double> z(Ly.c);
-        for (int i = 0; i < Ly.c; ++i) z[i] = cr.post[Ly.le - 1][i] * cq.post[Ly.le - 1][i];
+        const std::vector<double> z = merge_fwd(Ly, cr.lat, cq.lat);
         std::vector<std::vector<double>> ins, pres;
         out[b] = out_act(s->measure, decode(Ly, *s, params, z, ins, pres));
     }
@@ -253,10 +293,7 @@ int oracle_hash_loss_grad(const oracle_hash_shape* s, const double* params, int6
         EncCache cr, cq;
         encode(Ly, *s, params, 0, pr + 3 * b, cr);
         encode(Ly, *s, params, Ly.n_enc - 1, pq + 3 * b, cq);
-        const std::vector<double>& zr = cr.post[Ly.le - 1];
-        const std::vector<double>& zq = cq.post[Ly.le - 1];
-        std::vector<double> z(Ly.c);
-        for (int i = 0; i < Ly.c; ++i) z[i] = zr[i] * zq[i];
+        const std::vector<double> z = merge_fwd(Ly, cr.lat, cq.lat);
         std::vector<std::vector<double>> ins, pres;
         const double raw = decode(Ly, *s, params, z, ins, pres);
         const double y = out_act(s->measure, raw);
@@ -265,24 +302,21 @@ int oracle_hash_loss_grad(const oracle_hash_shape* s, const double* params, int6
         const double sg = d > 0.0 ? 1.0 : (d < 0.0 ? -1.0 : 0.0);
         std::vector<double> g{sg / (double)B * dout_act(s->measure, raw)};
         for (int k = Ly.ld - 1; k >= 0; --k) {
-            const int nout = k == Ly.ld - 1 ? 1 : Ly.c;
+            const int nout = k == Ly.ld - 1 ? 1 : Ly.c, nin = k == 0 ? Ly.ddec : Ly.c;
             if (k < Ly.ld - 1)
                 for (int o = 0; o < nout; ++o) g[o] *= dact(s->act, pres[k][o]);
-            std::vector<double> gin(Ly.c, 0.0);
+            std::vector<double> gin(nin, 0.0);
             for (int o = 0; o < nout; ++o) {
                 grad[Ly.dec_b[k] + o] += g[o];
-                for (int i = 0; i < Ly.c; ++i) {
-                    grad[Ly.dec_w[k] + (int64_t)o * Ly.c + i] += g[o] * ins[k][i];
-                    gin[i] += params[Ly.dec_w[k] + (int64_t)o * Ly.c + i] * g[o];
+                for (int i = 0; i < nin; ++i) {
+                    grad[Ly.dec_w[k] + (int64_t)o * nin + i] += g[o] * ins[k][i];
+                    gin[i] += params[Ly.dec_w[k] + (int64_t)o * nin + i] * g[o];
                 }
             }
             g = gin;
         }
-        std::vector<double> gr(Ly.c), gq(Ly.c);
-        for (int i = 0; i < Ly.c; ++i) {
-            gr[i] = g[i] * zq[i];
-            gq[i] = g[i] * zr[i];
-        }
+        std::vector<double> gr, gq;
+        merge_bwd(Ly, g, cr.lat, cq.lat, gr, gq);
         encode_backward(Ly, *s, params, 0, cr, gr, grad);
         encode_backward(Ly, *s, params, Ly.n_enc - 1, cq, gq, grad);
     }

@@ -10,12 +10,16 @@
  *             entries E_l = min(2^T, R_l^3): dense index x + R y + R^2 z when R^3 <= 2^T,
  *             else (x * 1 XOR y * 2654435761 XOR z * 805459861) mod 2^T in uint32
  *   encoder   enc_layers linear layers (first D_in -> width, then width -> width),
- *             activation after every layer but the last
- *   merge     z = enc(p_ref) (elementwise *) enc(p_q); one shared encoder and grid
- *             (n_enc = 1, self fields) or one per variable (n_enc = 2, cross fields:
- *             encoder 0 for the reference, 1 for the query)
- *   decoder   dec_layers linear layers (width -> width, last width -> 1), activation
- *             after every layer but the last, then tanh (Pearson) or softplus (MI)
+ *             activation after every layer but the last; enc_layers = 0 is the
+ *             grid-only ablation (Sec. 6.4): the latent is the embedding itself
+ *   merge     0: z = enc(p_ref) * enc(p_q) elementwise (the paper's choice), and the
+ *             ablations of Sec. 4.1: 1 sum, 2 absolute difference, 3 concatenation
+ *             [enc(p_ref); enc(p_q)]; one shared encoder and grid (n_enc = 1, self
+ *             fields) or one per variable (n_enc = 2, cross fields: encoder 0 for
+ *             the reference, 1 for the query)
+ *   decoder   dec_layers linear layers (first |z| -> width, then width -> width,
+ *             last -> 1), activation after every layer but the last, then tanh
+ *             (Pearson) or softplus (MI)
  *   act       0 ReLU, 1 Snake x + sin^2 x, 2 SnakeAlt x / 2 + sin^2 x
  *   loss      mean |y - target| (L1, Eq. 3)
  * Parameters (flat, in this order): per encoder e: level tables [E_l][F] for
@@ -32,7 +36,7 @@ extern "C" {
 
 typedef struct {
     int32_t levels, base_res, log2_table, feat, n_freq, width, enc_layers, dec_layers;
-    int32_t n_enc, measure, act;
+    int32_t n_enc, measure, act, merge;
 } oracle_hash_shape;
 
 int64_t oracle_hash_param_count(const oracle_hash_shape* s);

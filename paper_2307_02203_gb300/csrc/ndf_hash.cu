@@ -36,6 +36,7 @@ constexpr int kHashMaxLayers = 8;
 
 struct HashLayout {
     int levels = 0, F = 0, L = 0, c = 0, le = 0, ld = 0, n_enc = 0, din = 0, act = 0, logT = 0;
+    int merge = 0, dlat = 0, ddec = 0;  // latent width, decoder input width
     int64_t res[kHashMaxLevels] = {}, entries[kHashMaxLevels] = {}, toff[kHashMaxLevels] = {};
     int64_t ew[kHashMaxLayers] = {}, eb[kHashMaxLayers] = {};  // within an encoder
     int64_t dw[kHashMaxLayers] = {}, db[kHashMaxLayers] = {};  // absolute
@@ -43,8 +44,9 @@ struct HashLayout {
     bool init(const ndf_hash_arch& a, int n_enc_) {
         if (a.levels < 1 || a.levels > kHashMaxLevels || a.base_res < 2 || a.log2_table < 1 ||
             a.log2_table > 30 || a.feat < 1 || a.feat > 8 || a.n_freq < 0 || a.n_freq > 20 ||
-            a.width < 1 || a.width > 1024 || a.enc_layers < 1 || a.enc_layers > kHashMaxLayers ||
-            a.dec_layers < 1 || a.dec_layers > kHashMaxLayers || a.act < 0 || a.act > 2)
+            a.width < 1 || a.width > 1024 || a.enc_layers < 0 || a.enc_layers > kHashMaxLayers ||
+            a.dec_layers < 1 || a.dec_layers > kHashMaxLayers || a.act < 0 || a.act > 2 ||
+            a.merge < 0 || a.merge > 3)
             return false;
         if ((int64_t)a.base_res << (a.levels - 1) > (int64_t(1) << 20)) return false;
         levels = a.levels;
@@ -56,7 +58,10 @@ struct HashLayout {
         n_enc = n_enc_;
         act = a.act;
         logT = a.log2_table;
+        merge = a.merge;
         din = 3 + 6 * L + levels * F;
+        dlat = le > 0 ? c : din;
+        ddec = merge == NDF_MERGE_CONCAT ? 2 * dlat : dlat;
         int64_t o = 0;
         for (int l = 0; l < levels; ++l) {
             res[l] = (int64_t)a.base_res << l;
@@ -76,9 +81,9 @@ struct HashLayout {
         enc_size = o;
         o = enc_size * n_enc;
         for (int k = 0; k < ld; ++k) {
-            const int64_t out = k == ld - 1 ? 1 : c;
+            const int64_t out = k == ld - 1 ? 1 : c, in = k == 0 ? ddec : c;
             dw[k] = o;
-            o += out * c;
+            o += out * in;
             db[k] = o;
             o += out;
         }
@@ -218,23 +223,43 @@ __global__ void dact_mul_kernel(float* __restrict__ g, const float* __restrict__
     if (i < n) g[i] *= dact_f(act, pre[i]);
 }
 
-// z = zr * zq; zr broadcast over the batch when zr_stride == 0
+// z from the two latents (d features each, zr broadcast when zr_stride == 0):
+// product (the paper's merge), sum, |difference|, or concatenation [zr; zq]
 __global__ void merge_kernel(const float* __restrict__ zr, int64_t zr_stride,
-                             const float* __restrict__ zq, int c, int64_t B,
+                             const float* __restrict__ zq, int d, int64_t B, int mode,
                              float* __restrict__ z) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)c * B) return;
-    const int64_t b = i / c, o = i - b * c;
-    z[i] = zr[b * zr_stride + o] * zq[i];
+    if (i >= (int64_t)d * B) return;
+    const int64_t b = i / d, o = i - b * d;
+    const float a = zr[b * zr_stride + o], q = zq[i];
+    if (mode == NDF_MERGE_CONCAT) {
+        z[b * 2 * d + o] = a;
+        z[b * 2 * d + d + o] = q;
+    } else {
+        z[i] = mode == NDF_MERGE_PRODUCT ? a * q : mode == NDF_MERGE_SUM ? a + q : fabsf(a - q);
+    }
 }
 
 __global__ void merge_backward_kernel(const float* __restrict__ g, const float* __restrict__ zr,
-                                      const float* __restrict__ zq, int64_t n,
+                                      const float* __restrict__ zq, int d, int64_t B, int mode,
                                       float* __restrict__ gr, float* __restrict__ gq) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    gr[i] = g[i] * zq[i];
-    gq[i] = g[i] * zr[i];
+    if (i >= (int64_t)d * B) return;
+    const int64_t b = i / d, o = i - b * d;
+    if (mode == NDF_MERGE_CONCAT) {
+        gr[i] = g[b * 2 * d + o];
+        gq[i] = g[b * 2 * d + d + o];
+    } else if (mode == NDF_MERGE_PRODUCT) {
+        gr[i] = g[i] * zq[i];
+        gq[i] = g[i] * zr[i];
+    } else if (mode == NDF_MERGE_SUM) {
+        gr[i] = g[i];
+        gq[i] = g[i];
+    } else {
+        const float sg = zr[i] > zq[i] ? 1.0f : (zr[i] < zq[i] ? -1.0f : 0.0f);
+        gr[i] = g[i] * sg;
+        gq[i] = -g[i] * sg;
+    }
 }
 
 __device__ __forceinline__ float out_act(int measure, float x) {
@@ -337,11 +362,11 @@ static cudaError_t hash_workspace(ndf_hash_model* m, int64_t B) {
     m->ws = nullptr;
     m->cap = 0;
     const HashLayout& L = m->Ly;
-    const int64_t c = L.c, wmax = std::max<int64_t>(L.din, c);
+    const int64_t c = L.c, wmax = std::max<int64_t>(std::max<int64_t>(L.din, c), L.ddec);
     // loss (2 doubles), x0 x2, encoder pre/post x2 sides, z, decoder pre/post,
     // ga, gb (ping-pong), gr, gq (merge gradients), ones, graw, tgt, positions
-    const int64_t floats = 4 + 2 * B * L.din + 2 * 2 * L.le * B * c + B * c + 2 * L.ld * B * c +
-                           2 * B * wmax + 2 * B * c + 3 * B + 6 * B;
+    const int64_t floats = 4 + 2 * B * L.din + 2 * 2 * L.le * B * c + B * L.ddec +
+                           2 * L.ld * B * c + 2 * B * wmax + 2 * B * L.dlat + 3 * B + 6 * B;
     cudaError_t e = cudaMalloc(&m->ws, sizeof(float) * (size_t)floats);
     if (e != cudaSuccess) return e;
     float* o = m->ws;
@@ -357,15 +382,15 @@ static cudaError_t hash_workspace(ndf_hash_model* m, int64_t B) {
             m->pre_e[s][k] = take(B * c);
             m->post_e[s][k] = take(B * c);
         }
-    m->z = take(B * c);
+    m->z = take(B * L.ddec);
     for (int k = 0; k < L.ld; ++k) {
         m->pre_d[k] = take(B * c);
         m->post_d[k] = take(B * c);
     }
     m->ga = take(B * wmax);
     m->gb = take(B * wmax);
-    m->gr = take(B * c);
-    m->gq = take(B * c);
+    m->gr = take(B * L.dlat);
+    m->gq = take(B * L.dlat);
     m->ones = take(B);
     m->graw = take(B);
     m->tgt = take(B);
@@ -419,14 +444,19 @@ static cudaError_t encode_side(ndf_hash_model* m, int e, int s, const float* pos
     return cudaGetLastError();
 }
 
+// the latent of side s: the last encoder layer, or the embedding (grid-only)
+static const float* latent(const ndf_hash_model* m, int s) {
+    return m->Ly.le > 0 ? m->post_e[s][m->Ly.le - 1] : m->x0[s];
+}
+
 // decoder over m->z; raw outputs in pre_d[ld-1]
 static cudaError_t decode_z(ndf_hash_model* m, int64_t B) {
     const HashLayout& L = m->Ly;
     ndf_ctx* ctx = m->ctx;
     const float* in = m->z;
     for (int k = 0; k < L.ld; ++k) {
-        const int cout = k == L.ld - 1 ? 1 : L.c;
-        if (!gemm_fwd(m->blas, m->params + L.dw[k], in, m->pre_d[k], cout, L.c, B))
+        const int cout = k == L.ld - 1 ? 1 : L.c, cin = k == 0 ? L.ddec : L.c;
+        if (!gemm_fwd(m->blas, m->params + L.dw[k], in, m->pre_d[k], cout, cin, B))
             return cudaErrorUnknown;
         bias_act_kernel<<<blocks_for((int64_t)cout * B), 256, 0, ctx->stream>>>(
             m->pre_d[k], m->params + L.db[k], cout, B, k < L.ld - 1 ? L.act : -1, m->post_d[k]);
@@ -445,9 +475,10 @@ static cudaError_t hash_forward_backward(ndf_hash_model* m, const float* pr, con
     cudaError_t e = encode_side(m, 0, 0, pr, B);
     if (e == cudaSuccess) e = encode_side(m, eq, 1, pq, B);
     if (e != cudaSuccess) return e;
-    const float* zr = m->post_e[0][L.le - 1];
-    const float* zq = m->post_e[1][L.le - 1];
-    merge_kernel<<<blocks_for((int64_t)L.c * B), 256, 0, ctx->stream>>>(zr, L.c, zq, L.c, B, m->z);
+    const float* zr = latent(m, 0);
+    const float* zq = latent(m, 1);
+    merge_kernel<<<blocks_for((int64_t)L.dlat * B), 256, 0, ctx->stream>>>(zr, L.dlat, zq, L.dlat, B,
+                                                                           L.merge, m->z);
     ctx->launches++;
     if ((e = decode_z(m, B)) != cudaSuccess) return e;
     out_loss_kernel<<<blocks_for(B), 256, 0, ctx->stream>>>(m->pre_d[L.ld - 1], target, B,
@@ -459,11 +490,11 @@ static cudaError_t hash_forward_backward(ndf_hash_model* m, const float* pr, con
     float* pp[2] = {m->ga, m->gb};
     int cur = 0;
     for (int k = L.ld - 1; k >= 0; --k) {
-        const int cout = k == L.ld - 1 ? 1 : L.c;
+        const int cout = k == L.ld - 1 ? 1 : L.c, cin = k == 0 ? L.ddec : L.c;
         const float* in = k == 0 ? m->z : m->post_d[k - 1];
         float* gin = pp[cur];
         if (!gemm_bwd(m->blas, m->params + L.dw[k], in, g, gin, m->grad + L.dw[k], m->grad + L.db[k],
-                      m->ones, cout, L.c, B))
+                      m->ones, cout, cin, B))
             return cudaErrorUnknown;
         if (k > 0) {
             dact_mul_kernel<<<blocks_for((int64_t)L.c * B), 256, 0, ctx->stream>>>(
@@ -473,8 +504,8 @@ static cudaError_t hash_forward_backward(ndf_hash_model* m, const float* pr, con
         g = gin;
         cur ^= 1;
     }
-    merge_backward_kernel<<<blocks_for((int64_t)L.c * B), 256, 0, ctx->stream>>>(
-        g, zr, zq, (int64_t)L.c * B, m->gr, m->gq);
+    merge_backward_kernel<<<blocks_for((int64_t)L.dlat * B), 256, 0, ctx->stream>>>(
+        g, zr, zq, L.dlat, B, L.merge, m->gr, m->gq);
     ctx->launches++;
     for (int s = 0; s < 2; ++s) {
         const int enc_i = s == 0 ? 0 : eq;  // a shared encoder accumulates both sides
@@ -519,6 +550,7 @@ void ndf_hash_arch_default(ndf_hash_arch* a) {
     a->enc_layers = 6;
     a->dec_layers = 6;
     a->act = NDF_ACT_SNAKEALT;
+    a->merge = NDF_MERGE_PRODUCT;
 }
 
 ndf_status ndf_hash_model_create(ndf_ctx* ctx, const ndf_hash_arch* arch, int measure, int cross,
@@ -691,7 +723,7 @@ ndf_status ndf_hash_infer(ndf_hash_model* m, int64_t ref_idx, float* out) {
     vertex_positions_kernel<<<1, 32, 0, ctx->stream>>>(ref_idx, 1, m->X, m->Y, m->Z, m->pos);
     ctx->launches++;
     e = encode_side(m, 0, 0, m->pos, 1);
-    const float* zr = m->post_e[0][L.le - 1];
+    const float* zr = latent(m, 0);
     for (int64_t v0 = 0; v0 < N && e == cudaSuccess; v0 += chunk) {
         const int64_t n = std::min(chunk, N - v0);
         vertex_positions_kernel<<<blocks_for(n), 256, 0, ctx->stream>>>(v0, n, m->X, m->Y, m->Z,
@@ -699,8 +731,8 @@ ndf_status ndf_hash_infer(ndf_hash_model* m, int64_t ref_idx, float* out) {
         ctx->launches++;
         e = encode_side(m, L.n_enc - 1, 1, m->pos + 3, n);
         if (e != cudaSuccess) break;
-        merge_kernel<<<blocks_for((int64_t)L.c * n), 256, 0, ctx->stream>>>(
-            zr, 0, m->post_e[1][L.le - 1], L.c, n, m->z);
+        merge_kernel<<<blocks_for((int64_t)L.dlat * n), 256, 0, ctx->stream>>>(
+            zr, 0, latent(m, 1), L.dlat, n, L.merge, m->z);
         ctx->launches++;
         if ((e = decode_z(m, n)) != cudaSuccess) break;
         out_loss_kernel<<<blocks_for(n), 256, 0, ctx->stream>>>(

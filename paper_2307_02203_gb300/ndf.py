@@ -29,13 +29,14 @@ NDF_MEASURE_PEARSON, NDF_MEASURE_MI_KSG = 0, 1
 NDF_KSG_BRUTE, NDF_KSG_PRUNED = 0, 1
 NDF_RENDER_DVR, NDF_RENDER_ISO = 0, 1
 NDF_ACT_RELU, NDF_ACT_SNAKE, NDF_ACT_SNAKEALT = 0, 1, 2
+NDF_MERGE_PRODUCT, NDF_MERGE_SUM, NDF_MERGE_ABSDIFF, NDF_MERGE_CONCAT = 0, 1, 2, 3
 
 
 class HashArch(ctypes.Structure):
     """ndf_hash_arch (include/ndf.h); fill with ndf_hash_arch_default()."""
 
     _fields_ = [(n, ctypes.c_int32) for n in ("levels", "base_res", "log2_table", "feat", "n_freq",
-                                               "width", "enc_layers", "dec_layers", "act")]
+                                               "width", "enc_layers", "dec_layers", "act", "merge")]
 
 
 class RenderCfg(ctypes.Structure):

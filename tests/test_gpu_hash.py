@@ -26,7 +26,7 @@ def oshape(a, cross, measure):
     return oracle.hash_shape(levels=a.levels, base_res=a.base_res, log2_table=a.log2_table,
                              feat=a.feat, n_freq=a.n_freq, width=a.width, enc_layers=a.enc_layers,
                              dec_layers=a.dec_layers, n_enc=2 if cross else 1, measure=measure,
-                             act=a.act)
+                             act=a.act, merge=a.merge)
 
 
 def rand_params(n, seed, scale=0.4):
@@ -62,6 +62,33 @@ def test_forward_and_gradients_vs_oracle(ndf_mod, ctx, cross, measure, act):
     assert loss == pytest.approx(lref, rel=1e-5)
     err = np.abs(g - gref)
     assert np.linalg.norm(err) <= 1e-3 * np.linalg.norm(gref) + 1e-7
+    ndf_mod.ndf_hash_model_free(m)
+
+
+@pytest.mark.parametrize("merge,enc_layers", [(1, 3), (2, 3), (3, 3), (0, 0)])
+def test_ablations_vs_oracle(ndf_mod, ctx, merge, enc_layers):
+    """The merge alternatives of Sec. 4.1 and the grid-only model of Sec. 6.4."""
+    a = archs(ndf_mod, 2, merge=merge, enc_layers=enc_layers)
+    cross = merge == 3
+    m = ndf_mod.ndf_hash_model_create(ctx, a, 0, cross, 3, 8, 8, 8)
+    s = oshape(a, cross, 0)
+    n = oracle.hash_param_count(s)
+    assert ndf_mod.ndf_hash_model_param_count(m) == n
+    p = rand_params(n, 20 + merge)
+    ndf_mod.ndf_hash_model_set_params(m, p)
+    rng = np.random.default_rng(31)
+    B = 333
+    pr = rng.uniform(-1, 1, (B, 3)).astype(np.float32)
+    pq = rng.uniform(-1, 1, (B, 3)).astype(np.float32)
+    y = np.empty(B, np.float32)
+    ndf_mod.ndf_hash_model_forward(m, pr, pq, y)
+    ref = oracle.hash_forward(s, p.astype(np.float64), pr, pq)
+    assert (np.abs(y - ref) <= 2e-5 + 2e-5 * np.abs(ref)).all()
+    t = rng.uniform(-0.8, 0.8, B).astype(np.float32)
+    g = np.empty(n, np.float32)
+    ndf_mod.ndf_hash_model_step(m, pr, pq, t, 0.0, False, g)
+    _, gref = oracle.hash_loss_grad(s, p.astype(np.float64), pr, pq, t)
+    assert np.linalg.norm(g - gref) <= 1e-3 * np.linalg.norm(gref) + 1e-7
     ndf_mod.ndf_hash_model_free(m)
 
 

@@ -110,3 +110,46 @@ def test_dense_level_reads_its_vertex_entry():
         e2 = float(x + 4 * y + 16 * z) ** 2
         want = math.log1p(math.exp(-e2)) + e2
         assert oracle.hash_forward(s, p, pos, pos)[0] == pytest.approx(want, rel=1e-12)
+
+
+@pytest.mark.parametrize("merge,enc_layers", [(1, 2), (2, 2), (3, 2), (0, 0), (3, 0)])
+def test_ablations_gradient_vs_central_differences(merge, enc_layers):
+    # merge: 1 sum, 2 |difference|, 3 concatenation; enc_layers = 0: grid only
+    s = shape(merge=merge, enc_layers=enc_layers, n_enc=2 if merge == 3 else 1)
+    n = oracle.hash_param_count(s)
+    rng = np.random.default_rng(merge * 10 + enc_layers)
+    p = rng.normal(0, 0.6, n)
+    pr, pq = rng.uniform(-1, 1, (4, 3)), rng.uniform(-1, 1, (4, 3))
+    t = rng.uniform(-0.5, 0.5, 4)
+    _, g = oracle.hash_loss_grad(s, p, pr, pq, t)
+    h = 1e-6
+    for i in rng.choice(n, size=min(n, 100), replace=False):
+        d = np.zeros(n)
+        d[i] = h
+        num = (oracle.hash_loss_grad(s, p + d, pr, pq, t)[0] -
+               oracle.hash_loss_grad(s, p - d, pr, pq, t)[0]) / (2 * h)
+        assert abs(num - g[i]) <= 1e-7 + 1e-6 * abs(g[i]), (i, num, g[i])
+
+
+def test_merge_symmetry():
+    # with one shared encoder, sum and |difference| are symmetric, concatenation is not
+    rng = np.random.default_rng(8)
+    a, b = rng.uniform(-1, 1, (30, 3)), rng.uniform(-1, 1, (30, 3))
+    for merge, sym in ((1, True), (2, True), (3, False)):
+        s = shape(merge=merge)
+        p = rng.normal(0, 0.7, oracle.hash_param_count(s))
+        fa, fb = oracle.hash_forward(s, p, a, b), oracle.hash_forward(s, p, b, a)
+        assert np.array_equal(fa, fb) == sym
+
+
+def test_grid_only_latent_is_the_embedding():
+    # enc_layers = 0: with a one-layer linear decoder of weight e_j and product
+    # merge, y = tanh(x0_j(p_ref) * x0_j(p_q)); x0_0 is p_x
+    s = shape(enc_layers=0, dec_layers=1, n_freq=1)
+    p = np.zeros(oracle.hash_param_count(s))
+    tables = sum(min(2 ** 5, (2 << l) ** 3) * 2 for l in range(3))
+    p[tables + 0] = 1.0  # decoder W[0][0]: coordinate x
+    rng = np.random.default_rng(9)
+    a, b = rng.uniform(-1, 1, (10, 3)), rng.uniform(-1, 1, (10, 3))
+    np.testing.assert_allclose(oracle.hash_forward(s, p, a, b), np.tanh(a[:, 0] * b[:, 0]),
+                               atol=1e-15)
