@@ -297,6 +297,54 @@ def measure_sampler(ndf, ctx, fid, stream):
     return res
 
 
+def measure_hash_ndf(ndf, ctx, fid, recipe, stream, args, grid_only=False):
+    """The paper's architecture (hash grid, Fourier features, SnakeAlt MLPs, product
+    merge) trained on continuous samples renewed every pass (Pearson, self field);
+    decode time per volume and MAE against the exact estimator.  grid_only: the
+    ablation without encoder MLPs (Sec. 6.4)."""
+    import torch
+
+    N = recipe.N
+    arch = ndf.ndf_hash_arch_default()
+    if grid_only:
+        arch.enc_layers = 0
+    cfg = ndf.ndf_train_cfg_default()
+    cfg.n_triples = 1 << 20
+    cfg.batch = 1 << 14
+    cfg.lr = 1e-3
+    cfg.time_budget_s = float(args.ndf_seconds)
+    t0 = time.perf_counter()
+    model = ndf.ndf_hash_train(ctx, fid, fid, ndf.NDF_MEASURE_PEARSON, 0, arch, cfg)
+    ndf.ndf_synchronize(ctx)
+    wall = time.perf_counter() - t0
+    info = ndf.ndf_hash_model_info(model)
+    rng = np.random.default_rng(778)
+    refs = [int(r) for r in rng.integers(0, N, size=8)]
+    dec = torch.empty((len(refs), N), dtype=torch.float32, device="cuda")
+    ndf.ndf_hash_infer(model, refs[0], dec[0])  # warm-up
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i, r in enumerate(refs):
+        ndf.ndf_hash_infer(model, r, dec[i])
+    e1.record(stream)
+    ndf.ndf_synchronize(ctx)
+    exact = torch.empty((len(refs), N), dtype=torch.float32, device="cuda")
+    ndf.ndf_pearson_batch(ctx, fid, fid, refs, ndf.NDF_PREC_FP32, exact)
+    ndf.ndf_synchronize(ctx)
+    err = (dec - exact).abs()
+    res = {"arch": {n: getattr(arch, n) for n, _ in arch._fields_},
+           "params": ndf.ndf_hash_model_param_count(model), "triples_per_pass": int(cfg.n_triples),
+           "batch": int(cfg.batch), "passes": info["passes"], "adam_steps": info["adam_steps"],
+           "train_seconds": info["train_seconds"], "sample_seconds": info["gen_seconds"],
+           "train_steps_per_s": info["adam_steps"] / max(info["train_seconds"], 1e-9),
+           "train_wall_s": wall, "last_pass_l1": info["last_loss"],
+           "decode_ms_per_volume": e0.elapsed_time(e1) / len(refs),
+           "mae": float(err.mean()), "max_err_mean_over_refs": float(err.amax(dim=1).mean()),
+           "error_refs": len(refs)}
+    ndf.ndf_hash_model_free(model)
+    return res
+
+
 def measure_ndf(ndf, ctx, fid, recipe, stream, args, exact_ms, fid_b=None):
     """Learned part: trains a Pearson and a KSG-MI network on the loaded field
     (targets from the GPU estimators), then times volume decoding (1 reference
@@ -439,6 +487,10 @@ def main():
                     help="volumes timed with the brute-force KSG search (same results)")
     ap.add_argument("--ndf", type=int, default=1, help="also train and time the neural field")
     ap.add_argument("--ndf-seconds", type=float, default=25.0, help="training budget per network")
+    ap.add_argument("--ndf-hash", type=int, default=1,
+                    help="also train the paper's hash-grid architecture (continuous samples)")
+    ap.add_argument("--ndf-hash-variants", type=int, default=0,
+                    help="also train the grid-only ablation of the hash-grid architecture")
     ap.add_argument("--ndf-cross", type=int, default=1,
                     help="also train cross-field networks (reference in A, query in a second field B)")
     ap.add_argument("--ndf-triples", type=int, default=1 << 26, help="Pearson training triples")
@@ -557,6 +609,11 @@ def main():
         ndf.ndf_trim_cache(ctx)
     if ndf_res is not None:
         ndf_res["continuous_sampler"] = measure_sampler(ndf, ctx, fid, stream)
+        if args.ndf_hash:
+            ndf_res["hash_grid_pearson"] = measure_hash_ndf(ndf, ctx, fid, recipe, stream, args)
+        if args.ndf_hash_variants:
+            ndf_res["hash_grid_only_pearson"] = measure_hash_ndf(ndf, ctx, fid, recipe, stream,
+                                                                 args, grid_only=True)
 
     # ---- end to end through the ABI with host buffers (upload + stats + both volumes + D2H)
     host_r = torch.empty(N, dtype=torch.float32, pin_memory=True)
