@@ -297,7 +297,7 @@ def measure_sampler(ndf, ctx, fid, stream):
     return res
 
 
-def measure_hash_ndf(ndf, ctx, fid, recipe, stream, args, grid_only=False):
+def measure_hash_ndf(ndf, ctx, fid, recipe, stream, args, grid_only=False, n_freq=None):
     """The paper's architecture (hash grid, Fourier features, SnakeAlt MLPs, product
     merge) trained on continuous samples renewed every pass (Pearson, self field);
     decode time per volume and MAE against the exact estimator.  grid_only: the
@@ -308,10 +308,13 @@ def measure_hash_ndf(ndf, ctx, fid, recipe, stream, args, grid_only=False):
     arch = ndf.ndf_hash_arch_default()
     if grid_only:
         arch.enc_layers = 0
+    if n_freq is not None:
+        arch.n_freq = n_freq
     cfg = ndf.ndf_train_cfg_default()
-    cfg.n_triples = 1 << 20
-    cfg.batch = 1 << 14
+    cfg.n_triples = 1 << 19
+    cfg.batch = 1 << 13
     cfg.lr = 1e-3
+    cfg.max_decays = 100
     cfg.time_budget_s = float(args.ndf_seconds)
     t0 = time.perf_counter()
     model = ndf.ndf_hash_train(ctx, fid, fid, ndf.NDF_MEASURE_PEARSON, 0, arch, cfg)
@@ -611,6 +614,8 @@ def main():
         ndf_res["continuous_sampler"] = measure_sampler(ndf, ctx, fid, stream)
         if args.ndf_hash:
             ndf_res["hash_grid_pearson"] = measure_hash_ndf(ndf, ctx, fid, recipe, stream, args)
+            ndf_res["hash_grid_pearson_L4"] = measure_hash_ndf(ndf, ctx, fid, recipe, stream, args,
+                                                               n_freq=4)
         if args.ndf_hash_variants:
             ndf_res["hash_grid_only_pearson"] = measure_hash_ndf(ndf, ctx, fid, recipe, stream,
                                                                  args, grid_only=True)

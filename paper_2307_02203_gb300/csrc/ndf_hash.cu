@@ -588,7 +588,9 @@ ndf_status ndf_hash_model_create(ndf_ctx* ctx, const ndf_hash_arch* arch, int me
         return e != cudaSuccess ? cuda_fail(ctx, e, "hash model allocation")
                                 : fail(ctx, NDF_ERR_CUDA, "cuBLAS set-up failed");
     }
-    // initialisation: tables U(-1e-4, 1e-4), weights U(-sqrt(6/in), sqrt(6/in)), biases 0
+    // initialisation: tables U(-0.1, 0.1), weights U(-sqrt(6/in), sqrt(6/in)), biases 0, and a
+    // zero last decoder layer (the untrained field is constant: without it, the sin^2 term
+    // of Snake-family activations drifts the output and L1 training collapses it)
     std::vector<float> h((size_t)m->Ly.total, 0.0f);
     uint64_t st = seed * 0x9e3779b97f4a7c15ULL + 0x1234567ULL;
     auto unif = [&]() {
@@ -602,17 +604,17 @@ ndf_status ndf_hash_model_create(ndf_ctx* ctx, const ndf_hash_arch* arch, int me
     const HashLayout& L = m->Ly;
     for (int e_i = 0; e_i < L.n_enc; ++e_i) {
         const int64_t base = L.enc_size * e_i;
-        for (int64_t i = 0; i < L.tables; ++i) h[(size_t)(base + i)] = (float)(1e-4 * unif());
+        for (int64_t i = 0; i < L.tables; ++i) h[(size_t)(base + i)] = (float)(0.1 * unif());
         for (int k = 0; k < L.le; ++k) {
             const int64_t cin = k == 0 ? L.din : L.c;
             const double a = sqrt(6.0 / (double)cin);
             for (int64_t i = 0; i < cin * L.c; ++i) h[(size_t)(base + L.ew[k] + i)] = (float)(a * unif());
         }
     }
-    for (int k = 0; k < L.ld; ++k) {
-        const int64_t cout = k == L.ld - 1 ? 1 : L.c;
-        const double a = sqrt(6.0 / (double)L.c);
-        for (int64_t i = 0; i < cout * L.c; ++i) h[(size_t)(L.dw[k] + i)] = (float)(a * unif());
+    for (int k = 0; k < L.ld - 1; ++k) {
+        const int64_t cin = k == 0 ? L.ddec : L.c;
+        const double a = sqrt(6.0 / (double)cin);
+        for (int64_t i = 0; i < cin * L.c; ++i) h[(size_t)(L.dw[k] + i)] = (float)(a * unif());
     }
     e = cudaMemcpyAsync(m->params, h.data(), bytes, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
