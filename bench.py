@@ -36,7 +36,7 @@ K_NN = 8
 # one-level slab capture (ncu dram__bytes_read.sum + dram__bytes_write.sum for
 # 88,000 vertices) scaled by the vertices processed (x20): the kernels stream each
 # query column and its sorted copy once (algorithmic 14.08 GB + 7 MB output).
-KSG_PRUNED_TRAFFIC_PER_VOLUME = None  # recaptured after the kernel change
+KSG_PRUNED_TRAFFIC_PER_VOLUME = (705.641e6 + 4.142e6) * 20
 KSG_BRUTE_TRAFFIC_PER_VOLUME = (705.845e6 + 4.089e6) * 20
 METRIC = "ms per 1.76M-voxel dependence volume (Pearson + KSG MI k=8, M=1000)"
 
