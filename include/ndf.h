@@ -105,6 +105,13 @@ ndf_status ndf_free_ensemble(ndf_ctx* ctx, int field_id);
  * the context's stream first). */
 ndf_status ndf_trim_cache(ndf_ctx* ctx);
 
+/* Test hook for failure detection: runs one kernel whose mbarrier wait is never
+ * completed, so the library's bounded wait gives up (after about one second),
+ * sets the device status word and returns.  The call synchronizes and returns
+ * what the next host check reports: NDF_ERR_TIMEOUT when the path works.  The
+ * context stays usable; the status word is cleared by the check. */
+ndf_status ndf_selftest_timeout(ndf_ctx* ctx);
+
 /* Shape of a loaded field (any output pointer may be NULL). */
 ndf_status ndf_field_shape(const ndf_ctx* ctx, int field_id, int64_t* M, int64_t* Z, int64_t* Y,
                            int64_t* X);

@@ -10,10 +10,18 @@ namespace ndf {
 // Bit flags of the device status word (ctx->flag, word 1).
 enum : unsigned { kDevTimeout = 1u, kDevBadInput = 2u };
 
-// Upper bound on mbarrier polls before a wait gives up (each poll is a
-// hardware try_wait with its own short suspend window): far above any real
-// completion time, far below a hang.
+// Bounds of an mbarrier wait: at most kWaitPolls polls (each a hardware try_wait
+// with its own short suspend window) and at most kWaitNs nanoseconds of
+// %globaltimer, checked every 1024 polls; both far above any real completion
+// time, far below a hang.
 constexpr uint32_t kWaitPolls = 1u << 24;
+constexpr uint64_t kWaitNs = 1000000000ull;
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -35,6 +43,7 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
 // the poll budget ran out.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
     uint32_t addr = smem_u32(bar);
+    uint64_t t0 = 0;
     for (uint32_t i = 0; i < kWaitPolls; ++i) {
         uint32_t done;
         asm volatile(
@@ -45,6 +54,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
             : "r"(addr), "r"(phase)
             : "memory");
         if (done) return true;
+        if ((i & 1023u) == 1023u) {
+            const uint64_t t = global_ns();
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > kWaitNs) return false;
+        }
     }
     return false;
 }

@@ -34,6 +34,15 @@ void Field::free_all() {
     live = false;
 }
 
+// A wait that nothing completes: an mbarrier expecting one arrival that never
+// comes.  The bounded wait gives up (about a second) and reports kDevTimeout.
+__global__ void selftest_wait_kernel(unsigned* status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait(&bar, 0)) report(status, kDevTimeout);
+}
+
 cudaError_t ctx_alloc(ndf_ctx* ctx, void** p, size_t bytes) {
     *p = nullptr;
     for (size_t i = 0; i < ctx->cache.size(); ++i) {
@@ -377,6 +386,17 @@ ndf_status ndf_free_ensemble(ndf_ctx* ctx, int field_id) {
     cudaStreamSynchronize(ctx->stream);
     release_field(ctx, f);
     return NDF_OK;
+}
+
+ndf_status ndf_selftest_timeout(ndf_ctx* ctx) {
+    if (!ctx) return NDF_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    selftest_wait_kernel<<<1, 32, 0, ctx->stream>>>(ctx->flag.as<unsigned>() + 1);
+    ctx->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "self-test launch");
+    return check_device_status(ctx);
 }
 
 ndf_status ndf_trim_cache(ndf_ctx* ctx) {

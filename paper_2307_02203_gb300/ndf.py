@@ -79,6 +79,7 @@ _sig("ndf_load_ensemble", ctypes.c_int, [_vp, _vp, _i64, _i64, _i64, _i64,
                                          ctypes.POINTER(ctypes.c_int)])
 _sig("ndf_free_ensemble", ctypes.c_int, [_vp, ctypes.c_int])
 _sig("ndf_trim_cache", ctypes.c_int, [_vp])
+_sig("ndf_selftest_timeout", ctypes.c_int, [_vp])
 _sig("ndf_field_shape", ctypes.c_int, [_vp, ctypes.c_int] + [ctypes.POINTER(_i64)] * 4)
 _sig("ndf_field_stats", ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp])
 _sig("ndf_pearson", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, _vp])
@@ -234,6 +235,11 @@ def ndf_load_ensemble(ctx, field, M, Z, Y, X) -> int:
 
 def ndf_free_ensemble(ctx, field_id: int) -> None:
     _check(ctx, _lib.ndf_free_ensemble(ctx, field_id), "ndf_free_ensemble")
+
+
+def ndf_selftest_timeout(ctx) -> int:
+    """Status of the bounded-wait self-test (NDF_ERR_TIMEOUT when the path works)."""
+    return int(_lib.ndf_selftest_timeout(ctx))
 
 
 def ndf_trim_cache(ctx) -> None:
