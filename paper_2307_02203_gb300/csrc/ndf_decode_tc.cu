@@ -88,9 +88,15 @@ __device__ __forceinline__ bool try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 __device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    uint64_t t0 = 0;
     for (uint32_t i = 0; i < kWaitPolls; ++i) {
         if (try_wait(bar, parity)) return true;
         if ((i & 255) == 255 && *abort_flag) return false;
+        if ((i & 1023u) == 1023u) {  // and at most kWaitNs of wall time
+            const uint64_t t = global_ns();
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > kWaitNs) break;
+        }
     }
     *abort_flag = 1;
     return false;
@@ -254,6 +260,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) infer_tc_kernel(const TcInferAr
             const uint32_t sw1 = smem_u32(smem + kOffW1), sw2 = smem_u32(smem + kOffW2),
                            sw3 = smem_u32(smem + kOffW3);
             uint32_t polls = 0;
+            uint64_t t0 = 0;
             while ((tile[0] < tiles || tile[1] < tiles) && !*abort_flag) {
                 bool progressed = false;
                 for (int s = 0; s < 2; ++s) {
@@ -285,8 +292,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) infer_tc_kernel(const TcInferAr
                 }
                 if (progressed) {
                     polls = 0;
+                    t0 = 0;
                 } else if (++polls > kWaitPolls) {
                     *abort_flag = 1;
+                } else if ((polls & 1023u) == 0u) {  // and at most kWaitNs of wall time
+                    const uint64_t t = global_ns();
+                    if (t0 == 0) t0 = t;
+                    else if (t - t0 > kWaitNs) *abort_flag = 1;
                 }
             }
         }

@@ -158,6 +158,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity,
                                               volatile int* abort_flag) {
     uint32_t addr = smem_u32(bar);
+    uint64_t t0 = 0;
     for (uint32_t i = 0; i < kWaitPolls; ++i) {
         uint32_t done;
         asm volatile(
@@ -169,6 +170,11 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity,
             : "memory");
         if (done) return true;
         if ((i & 255) == 255 && *abort_flag) return false;
+        if ((i & 1023u) == 1023u) {  // and at most kWaitNs of wall time
+            const uint64_t t = global_ns();
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > kWaitNs) break;
+        }
     }
     *abort_flag = 1;
     return false;
