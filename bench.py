@@ -123,9 +123,9 @@ def load_peaks():
         with open(p) as fh:
             d = json.load(fh)
         return {"hbm_gbs": float(d["hbm_gbs"]), "sm_max_mhz": float(d.get("sm_max_mhz", 2070.0)),
-                "source": "measured"}
+                "bf16_tflops": float(d.get("bf16_tflops", 1900.0)), "source": "measured"}
     except (OSError, KeyError, ValueError):
-        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "bf16_tflops": 1900.0, "source": "fallback"}
 
 
 def make_field(recipe, pinned, nthreads):
@@ -324,25 +324,78 @@ def measure_hash_ndf(ndf, ctx, fid, recipe, stream, args, grid_only=False, n_fre
     rng = np.random.default_rng(778)
     refs = [int(r) for r in rng.integers(0, N, size=8)]
     dec = torch.empty((len(refs), N), dtype=torch.float32, device="cuda")
-    ndf.ndf_hash_infer(model, refs[0], dec[0])  # warm-up
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for i, r in enumerate(refs):
-        ndf.ndf_hash_infer(model, r, dec[i])
-    e1.record(stream)
-    ndf.ndf_synchronize(ctx)
+
+    def timed(fn):
+        ndf.ndf_synchronize(ctx)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        ndf.ndf_synchronize(ctx)
+        return e0.elapsed_time(e1)
+
+    def one_per_call():
+        for i, r in enumerate(refs):
+            ndf.ndf_hash_infer(model, r, dec[i])
+
+    def batched():
+        ndf.ndf_hash_infer_batch(model, refs, dec)
+
     exact = torch.empty((len(refs), N), dtype=torch.float32, device="cuda")
     ndf.ndf_pearson_batch(ctx, fid, fid, refs, ndf.NDF_PREC_FP32, exact)
-    ndf.ndf_synchronize(ctx)
-    err = (dec - exact).abs()
+    decode = {}
+    vols = {}
+    tc = ndf.ndf_hash_get_decode(model) == ndf.NDF_HASH_DECODE_TC
+    paths = [("fp32", ndf.NDF_HASH_DECODE_FP32, False)]
+    if tc:
+        paths += [("tc", ndf.NDF_HASH_DECODE_TC, False), ("tc_cached", ndf.NDF_HASH_DECODE_TC, True)]
+    for name, mode, cache in paths:
+        ndf.ndf_hash_set_decode(model, mode, cache)
+        first = timed(lambda: ndf.ndf_hash_infer(model, refs[0], dec[0]))  # warm-up (builds a cache)
+        d = {"ms_per_volume": timed(one_per_call) / len(refs)}
+        if mode == ndf.NDF_HASH_DECODE_TC:
+            d["ms_per_volume_batched"] = timed(batched) / len(refs)
+        if cache:
+            d["first_call_ms_with_query_encoding"] = first
+        err = (dec - exact).abs()
+        d["mae"] = float(err.mean())
+        d["max_err_mean_over_refs"] = float(err.amax(dim=1).mean())
+        vols[name] = dec.clone()
+        decode[name] = d
+    if tc:
+        diff = (vols["tc"] - vols["fp32"]).abs()
+        decode["tc"]["vs_fp32_mean_abs"] = float(diff.mean())
+        decode["tc"]["vs_fp32_max_abs"] = float(diff.max())
+        decode["tc_cached"]["equals_tc"] = bool(torch.equal(vols["tc_cached"], vols["tc"]))
+        # tensor-core roofline: algorithmic flops of the dense layers per volume
+        # multiply-adds per vertex: encoder (din -> c, then c -> c), decoder hidden
+        # layers (latent -> c, then c -> c), output layer (c -> 1)
+        din = 3 + 6 * arch.n_freq + arch.levels * arch.feat
+        c = arch.width
+        lat = c if arch.enc_layers else din
+        enc_mac = din * c + (arch.enc_layers - 1) * c * c if arch.enc_layers else 0
+        dec_mac = lat * c + (arch.dec_layers - 2) * c * c if arch.dec_layers >= 2 else 0
+        out_mac = c if arch.dec_layers >= 2 else lat
+        flop_full = 2.0 * N * (enc_mac + dec_mac + out_mac)
+        flop_cached = 2.0 * N * (dec_mac + out_mac)
+        peaks = load_peaks()
+        peak = peaks["bf16_tflops"]
+        for name, fl, key in (("tc", flop_full, "ms_per_volume_batched"),
+                              ("tc_cached", flop_cached, "ms_per_volume_batched")):
+            ach = fl / (decode[name][key] * 1e-3) / 1e12
+            decode[name]["tensor_tflops"] = ach
+            decode[name]["tensor_frac_of_bf16_peak"] = ach / peak
+            decode[name]["peak_source"] = peaks["source"]
+            decode[name]["algorithmic_gflop_per_volume"] = fl / 1e9
+    ndf.ndf_hash_set_decode(model, ndf.NDF_HASH_DECODE_TC if tc else ndf.NDF_HASH_DECODE_FP32)
     res = {"arch": {n: getattr(arch, n) for n, _ in arch._fields_},
            "params": ndf.ndf_hash_model_param_count(model), "triples_per_pass": int(cfg.n_triples),
            "batch": int(cfg.batch), "passes": info["passes"], "adam_steps": info["adam_steps"],
            "train_seconds": info["train_seconds"], "sample_seconds": info["gen_seconds"],
            "train_steps_per_s": info["adam_steps"] / max(info["train_seconds"], 1e-9),
            "train_wall_s": wall, "last_pass_l1": info["last_loss"],
-           "decode_ms_per_volume": e0.elapsed_time(e1) / len(refs),
-           "mae": float(err.mean()), "max_err_mean_over_refs": float(err.amax(dim=1).mean()),
+           "decode_ms_per_volume": decode["tc" if tc else "fp32"]["ms_per_volume"],
+           "mae": decode["tc" if tc else "fp32"]["mae"], "decode": decode,
            "error_refs": len(refs)}
     ndf.ndf_hash_model_free(model)
     return res
@@ -612,6 +665,8 @@ def main():
         ndf.ndf_trim_cache(ctx)
     if ndf_res is not None:
         ndf_res["continuous_sampler"] = measure_sampler(ndf, ctx, fid, stream)
+    if args.ndf_hash or args.ndf_hash_variants:
+        ndf_res = {} if ndf_res is None else ndf_res
         if args.ndf_hash:
             ndf_res["hash_grid_pearson"] = measure_hash_ndf(ndf, ctx, fid, recipe, stream, args)
             ndf_res["hash_grid_pearson_L4"] = measure_hash_ndf(ndf, ctx, fid, recipe, stream, args,

@@ -380,9 +380,33 @@ ndf_status ndf_hash_train(ndf_ctx* ctx, int ref_field, int query_field, int meas
 ndf_status ndf_hash_model_info(const ndf_hash_model* m, int* passes, double* last_loss,
                                double* gen_seconds, double* train_seconds, int64_t* adam_steps);
 
-/* The dependence volume of one reference vertex (vertex-aligned positions):
- * the reference is encoded once, the N query vertices in chunks of 65536. */
+/* The dependence volume of one reference vertex (vertex-aligned positions,
+ * Sec. 5): out[N] (host or device), N = X * Y * Z.  The reference latent is
+ * encoded once; the path is the one ndf_hash_set_decode selected. */
 ndf_status ndf_hash_infer(ndf_hash_model* m, int64_t ref_idx, float* out);
+
+/* R volumes, out[R][N] (host or device); ref_idx: R host indices in [0, N).
+ * The tensor-core path decodes up to 64 references per launch (one CTA row per
+ * reference).  NDF_ERR_ARG for an index out of range. */
+ndf_status ndf_hash_infer_batch(ndf_hash_model* m, const int64_t* ref_idx, int32_t R, float* out);
+
+/* Decoding path of ndf_hash_infer / ndf_hash_infer_batch.
+ *   NDF_HASH_DECODE_FP32: FP32 layers (cuBLAS SGEMM), the same arithmetic as
+ *     ndf_hash_model_forward; queries in chunks of 65536.
+ *   NDF_HASH_DECODE_TC: one persistent tcgen05 kernel per launch runs the whole
+ *     chain for 128-vertex tiles (BF16 operands, FP32 accumulation in TMEM;
+ *     embedding, biases, activations, merge and output layer in FP32).  Needs
+ *     width 128, at most 128 embedding inputs and a product / sum / |difference|
+ *     merge (NDF_ERR_ARG otherwise).
+ *   cache_queries != 0 (TC only; at least one encoder and two decoder layers):
+ *     the N query latents are encoded once per parameter change and kept on
+ *     the device (N x 128 FP32); each reference then runs only the merge and the
+ *     decoder.  The results equal the uncached TC path's.
+ * A new model starts in NDF_HASH_DECODE_TC when its architecture allows it,
+ * else in FP32, without the cache. */
+typedef enum { NDF_HASH_DECODE_FP32 = 0, NDF_HASH_DECODE_TC = 1 } ndf_hash_decode;
+ndf_status ndf_hash_set_decode(ndf_hash_model* m, int32_t mode, int32_t cache_queries);
+int32_t ndf_hash_get_decode(const ndf_hash_model* m); /* the mode, -1 for NULL */
 
 /* ---- headless volume rendering (Sec. 5, Sec. 6.5) -------------------------- */
 

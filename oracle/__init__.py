@@ -128,6 +128,10 @@ def _load():
             lib.oracle_hash_forward.restype = ctypes.c_int
             lib.oracle_hash_forward.argtypes = [ctypes.POINTER(HashShape), _f64p, ctypes.c_int64,
                                                 _f64p, _f64p, _f64p]
+            lib.oracle_hash_forward_bf16.restype = ctypes.c_int
+            lib.oracle_hash_forward_bf16.argtypes = lib.oracle_hash_forward.argtypes
+            lib.oracle_bf16_round.restype = ctypes.c_double
+            lib.oracle_bf16_round.argtypes = [ctypes.c_double]
             lib.oracle_hash_loss_grad.restype = ctypes.c_int
             lib.oracle_hash_loss_grad.argtypes = [ctypes.POINTER(HashShape), _f64p, ctypes.c_int64,
                                                   _f64p, _f64p, _f64p, _f64p, _f64p]
@@ -304,6 +308,24 @@ def hash_forward(shape, params, pr, pq):
     if rc != 0:
         raise ValueError("oracle_hash_forward: bad arguments")
     return out
+
+
+def hash_forward_bf16(shape, params, pr, pq):
+    """hash_forward with BF16 operands in every layer's product but the output layer's."""
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    a = np.ascontiguousarray(pr, dtype=np.float64).reshape(-1, 3)
+    b = np.ascontiguousarray(pq, dtype=np.float64).reshape(-1, 3)
+    out = np.empty(a.shape[0], dtype=np.float64)
+    rc = _load().oracle_hash_forward_bf16(ctypes.byref(shape), p.ctypes.data_as(_f64p), a.shape[0],
+                                          a.ctypes.data_as(_f64p), b.ctypes.data_as(_f64p),
+                                          out.ctypes.data_as(_f64p))
+    if rc != 0:
+        raise ValueError("oracle_hash_forward_bf16: bad arguments")
+    return out
+
+
+def bf16_round(x) -> float:
+    return float(_load().oracle_bf16_round(float(x)))
 
 
 def hash_loss_grad(shape, params, pr, pq, target):

@@ -66,6 +66,23 @@ struct Layout {
     }
 };
 
+// x rounded to BF16 (8 significant bits) by round-to-nearest-even, after a
+// round-to-nearest conversion to FP32 (the values a BF16 tensor-core operand is
+// made from are FP32)
+double bf16_round(double x) {
+    const float f = (float)x;
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7F800000u) == 0x7F800000u) return (double)f;  // Inf (also from overflow) / NaN
+    const uint32_t lsb = (u >> 16) & 1u;
+    u = (u + 0x7FFFu + lsb) & 0xFFFF0000u;
+    float r;
+    std::memcpy(&r, &u, 4);
+    return (double)r;
+}
+
+inline double opnd(bool rb, double x) { return rb ? bf16_round(x) : x; }
+
 double act(int a, double x) {
     if (a == 0) return x > 0.0 ? x : 0.0;
     const double s = std::sin(x);
@@ -114,8 +131,9 @@ struct EncCache {
     std::vector<double> lat;                // the latent (last layer output or x0)
 };
 
+// rb: every layer's product takes its operands rounded to BF16 (bf16_round)
 void encode(const Layout& Ly, const oracle_hash_shape& s, const double* P, int e, const double p[3],
-            EncCache& C) {
+            EncCache& C, bool rb = false) {
     const double* enc = P + Ly.enc_size * e;
     C.x0.assign(Ly.din, 0.0);
     C.x0[0] = p[0];
@@ -151,7 +169,7 @@ void encode(const Layout& Ly, const oracle_hash_shape& s, const double* P, int e
         C.post[k].assign(Ly.c, 0.0);
         for (int o = 0; o < Ly.c; ++o) {
             double a = b[o];
-            for (int64_t i = 0; i < nin; ++i) a += W[o * nin + i] * (*in)[i];
+            for (int64_t i = 0; i < nin; ++i) a += opnd(rb, W[o * nin + i]) * opnd(rb, (*in)[i]);
             C.pre[k][o] = a;
             C.post[k][o] = k < Ly.le - 1 ? act(s.act, a) : a;
         }
@@ -199,8 +217,10 @@ double dout_act(int measure, double x) {
 }
 
 // decoder forward; keeps pre-activations and inputs for the backward
+// rb: the hidden layers' products take BF16-rounded operands (the output layer's do not)
 double decode(const Layout& Ly, const oracle_hash_shape& s, const double* P, const std::vector<double>& z,
-              std::vector<std::vector<double>>& ins, std::vector<std::vector<double>>& pres) {
+              std::vector<std::vector<double>>& ins, std::vector<std::vector<double>>& pres,
+              bool rb = false) {
     ins.assign(Ly.ld, {});
     pres.assign(Ly.ld, {});
     std::vector<double> h = z;
@@ -211,7 +231,8 @@ double decode(const Layout& Ly, const oracle_hash_shape& s, const double* P, con
         std::vector<double> nh(nout);
         for (int o = 0; o < nout; ++o) {
             double a = P[Ly.dec_b[k] + o];
-            for (int i = 0; i < nin; ++i) a += P[Ly.dec_w[k] + (int64_t)o * nin + i] * h[i];
+            const bool r = rb && k < Ly.ld - 1;
+            for (int i = 0; i < nin; ++i) a += opnd(r, P[Ly.dec_w[k] + (int64_t)o * nin + i]) * opnd(r, h[i]);
             pres[k][o] = a;
             nh[o] = k < Ly.ld - 1 ? act(s.act, a) : a;
         }
@@ -265,21 +286,33 @@ int64_t oracle_hash_param_count(const oracle_hash_shape* s) {
     return Ly.ok ? Ly.total : -1;
 }
 
-int oracle_hash_forward(const oracle_hash_shape* s, const double* params, int64_t B,
-                        const double* pr, const double* pq, double* out) {
+static int forward_impl(const oracle_hash_shape* s, const double* params, int64_t B, const double* pr,
+                        const double* pq, double* out, bool rb) {
     if (!s || !params || !pr || !pq || !out || B < 0) return -1;
     Layout Ly(*s);
     if (!Ly.ok) return -1;
     for (int64_t b = 0; b < B; ++b) {
         EncCache cr, cq;
-        encode(Ly, *s, params, 0, pr + 3 * b, cr);
-        encode(Ly, *s, params, Ly.n_enc - 1, pq + 3 * b, cq);
+        encode(Ly, *s, params, 0, pr + 3 * b, cr, rb);
+        encode(Ly, *s, params, Ly.n_enc - 1, pq + 3 * b, cq, rb);
         const std::vector<double> z = merge_fwd(Ly, cr.lat, cq.lat);
         std::vector<std::vector<double>> ins, pres;
-        out[b] = out_act(s->measure, decode(Ly, *s, params, z, ins, pres));
+        out[b] = out_act(s->measure, decode(Ly, *s, params, z, ins, pres, rb));
     }
     return 0;
 }
+
+int oracle_hash_forward(const oracle_hash_shape* s, const double* params, int64_t B,
+                        const double* pr, const double* pq, double* out) {
+    return forward_impl(s, params, B, pr, pq, out, false);
+}
+
+int oracle_hash_forward_bf16(const oracle_hash_shape* s, const double* params, int64_t B,
+                             const double* pr, const double* pq, double* out) {
+    return forward_impl(s, params, B, pr, pq, out, true);
+}
+
+double oracle_bf16_round(double x) { return bf16_round(x); }
 
 int oracle_hash_loss_grad(const oracle_hash_shape* s, const double* params, int64_t B,
                           const double* pr, const double* pq, const double* target, double* loss,

@@ -45,6 +45,18 @@ int64_t oracle_hash_param_count(const oracle_hash_shape* s);
 int oracle_hash_forward(const oracle_hash_shape* s, const double* params, int64_t B,
                         const double* pr, const double* pq, double* out);
 
+/* The same network with BF16 operands: every product of an encoder layer and
+ * of a decoder hidden layer takes its weight and its input rounded to BF16
+ * (oracle_bf16_round); sums, biases, activations, the merge and the output layer
+ * stay FP64.  This is the arithmetic of a BF16 tensor-core decoder (BF16
+ * operands, wide accumulation).  Returns 0 or -1. */
+int oracle_hash_forward_bf16(const oracle_hash_shape* s, const double* params, int64_t B,
+                             const double* pr, const double* pq, double* out);
+
+/* x -> FP32 (round to nearest) -> BF16 (8 significant bits, round to nearest,
+ * ties to even); beyond the FP32 range Inf, NaN stays NaN. */
+double oracle_bf16_round(double x);
+
 /* Mean L1 loss and its gradient with respect to every parameter (hand-written
  * backward).  grad has oracle_hash_param_count entries.  Returns 0 or -1. */
 int oracle_hash_loss_grad(const oracle_hash_shape* s, const double* params, int64_t B,

@@ -27,125 +27,11 @@
 #include <numeric>
 #include <vector>
 
+#include "hash_common.cuh"
+#include "ndf_hash_tc.h"
 #include "ndf_internal.h"
 
 namespace ndf {
-
-constexpr int kHashMaxLevels = 8;
-constexpr int kHashMaxLayers = 8;
-
-struct HashLayout {
-    int levels = 0, F = 0, L = 0, c = 0, le = 0, ld = 0, n_enc = 0, din = 0, act = 0, logT = 0;
-    int merge = 0, dlat = 0, ddec = 0;  // latent width, decoder input width
-    int64_t res[kHashMaxLevels] = {}, entries[kHashMaxLevels] = {}, toff[kHashMaxLevels] = {};
-    int64_t ew[kHashMaxLayers] = {}, eb[kHashMaxLayers] = {};  // within an encoder
-    int64_t dw[kHashMaxLayers] = {}, db[kHashMaxLayers] = {};  // absolute
-    int64_t enc_size = 0, tables = 0, total = 0;
-    bool init(const ndf_hash_arch& a, int n_enc_) {
-        if (a.levels < 1 || a.levels > kHashMaxLevels || a.base_res < 2 || a.log2_table < 1 ||
-            a.log2_table > 30 || a.feat < 1 || a.feat > 8 || a.n_freq < 0 || a.n_freq > 20 ||
-            a.width < 1 || a.width > 1024 || a.enc_layers < 0 || a.enc_layers > kHashMaxLayers ||
-            a.dec_layers < 1 || a.dec_layers > kHashMaxLayers || a.act < 0 || a.act > 2 ||
-            a.merge < 0 || a.merge > 3)
-            return false;
-        if ((int64_t)a.base_res << (a.levels - 1) > (int64_t(1) << 20)) return false;
-        levels = a.levels;
-        F = a.feat;
-        L = a.n_freq;
-        c = a.width;
-        le = a.enc_layers;
-        ld = a.dec_layers;
-        n_enc = n_enc_;
-        act = a.act;
-        logT = a.log2_table;
-        merge = a.merge;
-        din = 3 + 6 * L + levels * F;
-        dlat = le > 0 ? c : din;
-        ddec = merge == NDF_MERGE_CONCAT ? 2 * dlat : dlat;
-        int64_t o = 0;
-        for (int l = 0; l < levels; ++l) {
-            res[l] = (int64_t)a.base_res << l;
-            const double dense = (double)res[l] * (double)res[l] * (double)res[l];
-            const int64_t cap = int64_t(1) << logT;
-            entries[l] = dense <= (double)cap ? res[l] * res[l] * res[l] : cap;
-            toff[l] = o;
-            o += entries[l] * F;
-        }
-        tables = o;
-        for (int k = 0; k < le; ++k) {
-            ew[k] = o;
-            o += (int64_t)(k == 0 ? din : c) * c;
-            eb[k] = o;
-            o += c;
-        }
-        enc_size = o;
-        o = enc_size * n_enc;
-        for (int k = 0; k < ld; ++k) {
-            const int64_t out = k == ld - 1 ? 1 : c, in = k == 0 ? ddec : c;
-            dw[k] = o;
-            o += out * in;
-            db[k] = o;
-            o += out;
-        }
-        total = o;
-        return true;
-    }
-};
-
-// kernel-side copy of what the embedding needs
-struct EmbedArgs {
-    int levels, F, L, din;
-    int res[kHashMaxLevels];
-    int64_t entries[kHashMaxLevels], toff[kHashMaxLevels];
-    unsigned char dense[kHashMaxLevels];
-};
-
-EmbedArgs embed_args(const HashLayout& Ly) {
-    EmbedArgs e;
-    e.levels = Ly.levels;
-    e.F = Ly.F;
-    e.L = Ly.L;
-    e.din = Ly.din;
-    for (int l = 0; l < Ly.levels; ++l) {
-        e.res[l] = (int)Ly.res[l];
-        e.entries[l] = Ly.entries[l];
-        e.toff[l] = Ly.toff[l];
-        e.dense[l] = (double)Ly.res[l] * Ly.res[l] * Ly.res[l] <= (double)(int64_t(1) << Ly.logT);
-    }
-    return e;
-}
-
-struct Cell {
-    int64_t idx[8];
-    float w[8];
-};
-
-__device__ __forceinline__ Cell level_cell(const EmbedArgs& E, int l, const float* p) {
-    const int R = E.res[l];
-    int i0[3];
-    float t[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        float u = (p[a] + 1.0f) * 0.5f * (float)(R - 1);
-        u = fminf(fmaxf(u, 0.0f), (float)(R - 1));
-        i0[a] = min((int)floorf(u), R - 2);
-        t[a] = u - (float)i0[a];
-    }
-    Cell c;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const int x = i0[0] + (q & 1), y = i0[1] + ((q >> 1) & 1), z = i0[2] + ((q >> 2) & 1);
-        if (E.dense[l]) {
-            c.idx[q] = (int64_t)x + (int64_t)R * y + (int64_t)R * R * z;
-        } else {
-            const uint32_t h = (uint32_t)x * 1u ^ (uint32_t)y * 2654435761u ^ (uint32_t)z * 805459861u;
-            c.idx[q] = (int64_t)(h % (uint32_t)E.entries[l]);
-        }
-        c.w[q] = ((q & 1) ? t[0] : 1.0f - t[0]) * (((q >> 1) & 1) ? t[1] : 1.0f - t[1]) *
-                 (((q >> 2) & 1) ? t[2] : 1.0f - t[2]);
-    }
-    return c;
-}
 
 // x0[b][din] = embed(pos[b]) with the tables of one encoder
 __global__ void hash_embed_kernel(const float* __restrict__ pos, int64_t B,
@@ -155,26 +41,7 @@ __global__ void hash_embed_kernel(const float* __restrict__ pos, int64_t B,
     if (b >= B) return;
     const float p[3] = {pos[3 * b], pos[3 * b + 1], pos[3 * b + 2]};
     float* x = x0 + b * E.din;
-    x[0] = p[0];
-    x[1] = p[1];
-    x[2] = p[2];
-    for (int j = 0; j < 3; ++j)
-        for (int i = 0; i < E.L; ++i) {
-            float s, c;
-            sincospif(ldexpf(p[j], i), &s, &c);  // sin / cos(2^i pi p_j)
-            x[3 + (j * E.L + i) * 2] = s;
-            x[3 + (j * E.L + i) * 2 + 1] = c;
-        }
-    for (int l = 0; l < E.levels; ++l) {
-        const Cell cl = level_cell(E, l, p);
-        const float* tab = enc + E.toff[l];
-        for (int f = 0; f < E.F; ++f) {
-            float v = 0.0f;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) v += cl.w[q] * __ldg(tab + cl.idx[q] * E.F + f);
-            x[3 + 6 * E.L + l * E.F + f] = v;
-        }
-    }
+    embed_point(E, enc, p, [&](int k, float v) { x[k] = v; });
 }
 
 // hash-table gradient: scatter dL/d(embedding) of the hash features
@@ -195,16 +62,6 @@ __global__ void hash_embed_backward_kernel(const float* __restrict__ pos, int64_
             for (int q = 0; q < 8; ++q) atomicAdd(tab + cl.idx[q] * E.F + f, cl.w[q] * gv);
         }
     }
-}
-
-__device__ __forceinline__ float act_f(int a, float x) {
-    if (a == 0) return fmaxf(x, 0.0f);
-    const float s = sinf(x);
-    return (a == 1 ? x : 0.5f * x) + s * s;
-}
-__device__ __forceinline__ float dact_f(int a, float x) {
-    if (a == 0) return x > 0.0f ? 1.0f : 0.0f;
-    return (a == 1 ? 1.0f : 0.5f) + sinf(2.0f * x);
 }
 
 // pre[b][o] += bias[o]; post = act(pre) (or a copy when act < 0)
@@ -262,10 +119,6 @@ __global__ void merge_backward_kernel(const float* __restrict__ g, const float* 
     }
 }
 
-__device__ __forceinline__ float out_act(int measure, float x) {
-    return measure == NDF_MEASURE_PEARSON ? tanhf(x) : log1pf(expf(-fabsf(x))) + fmaxf(x, 0.0f);
-}
-
 // y = out_act(raw) (and the L1 loss and its gradient when target != null)
 __global__ void out_loss_kernel(const float* __restrict__ raw, const float* __restrict__ target,
                                 int64_t B, int measure, float* __restrict__ y,
@@ -319,13 +172,24 @@ __global__ void vertex_positions_kernel(int64_t v0, int64_t n, int64_t X, int64_
                                         float* __restrict__ pos) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const int64_t v = v0 + i, x = v % X, y = (v / X) % Y, z = v / (X * Y);
-    pos[3 * i] = X > 1 ? -1.0f + 2.0f * (float)x / (float)(X - 1) : 0.0f;
-    pos[3 * i + 1] = Y > 1 ? -1.0f + 2.0f * (float)y / (float)(Y - 1) : 0.0f;
-    pos[3 * i + 2] = Z > 1 ? -1.0f + 2.0f * (float)z / (float)(Z - 1) : 0.0f;
+    vertex_position(v0 + i, X, Y, Z, pos + 3 * i);
 }
 
 inline unsigned blocks_for(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace ndf
+
+namespace ndf {
+
+// the tensor-core decoder covers width 128, an embedding of at most 128 inputs
+// and the element-wise merges (not concatenation)
+static bool hash_tc_eligible(const HashLayout& L) {
+    const int nL = L.le + L.ld - 1;
+    return L.c == 128 && L.din <= 128 && L.merge != NDF_MERGE_CONCAT && nL >= 1 && nL <= kHashTcMaxLayers;
+}
+
+// the query-latent cache needs a latent (an encoder layer) and a decoder layer after it
+static bool hash_tc_cache_ok(const HashLayout& L) { return hash_tc_eligible(L) && L.le >= 1 && L.ld >= 2; }
 
 }  // namespace ndf
 
@@ -348,6 +212,12 @@ struct ndf_hash_model {
     float *ga = nullptr, *gb = nullptr, *gr = nullptr, *gq = nullptr;
     float *ones = nullptr, *graw = nullptr, *tgt = nullptr, *pos = nullptr;
     double* loss = nullptr;
+    // tensor-core decoding: packed BF16 weight images and biases of the parameter
+    // version tc_ver, reference latents, optional cache of the query latents
+    int decode_tc = 0, cache_q = 0;
+    int64_t ver = 0, tc_ver = -1, lat_ver = -1;
+    unsigned char* tc_w = nullptr;
+    float *tc_bias = nullptr, *tc_zr = nullptr, *tc_lat = nullptr;
     // training record
     int passes = 0;
     double last_loss = 0.0, gen_seconds = 0.0, train_seconds = 0.0;
@@ -535,6 +405,160 @@ static cudaError_t hash_forward_backward(ndf_hash_model* m, const float* pr, con
     return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------- tensor-core decoding
+// Packed images: [encoder 0 layers][encoder 1 layers (cross)][decoder hidden layers],
+// so that a query-side chain (encoder eq, then the decoder) is contiguous.
+static cudaError_t hash_tc_prepare(ndf_hash_model* m) {
+    const HashLayout& L = m->Ly;
+    const int n = L.n_enc * L.le + L.ld - 1;
+    const size_t lb = hash_tc_layer_bytes();
+    cudaError_t e = cudaSuccess;
+    if (!m->tc_w) {
+        e = cudaMalloc(&m->tc_w, lb * (size_t)n);
+        if (e == cudaSuccess) e = cudaMalloc(&m->tc_bias, sizeof(float) * 128 * (size_t)n);
+        if (e == cudaSuccess) e = cudaMalloc(&m->tc_zr, sizeof(float) * 128 * (size_t)kHashTcMaxRefs);
+        if (e != cudaSuccess) return e;
+    }
+    if (m->tc_ver == m->ver) return cudaSuccess;
+    HashTcPack pk;
+    for (int en = 0; en < L.n_enc; ++en)
+        for (int k = 0; k < L.le; ++k) {
+            pk.cin[pk.n] = k == 0 ? L.din : L.c;
+            pk.w[pk.n] = L.enc_size * en + L.ew[k];
+            pk.b[pk.n] = L.enc_size * en + L.eb[k];
+            ++pk.n;
+        }
+    for (int k = 0; k < L.ld - 1; ++k) {
+        pk.cin[pk.n] = k == 0 ? L.ddec : L.c;
+        pk.w[pk.n] = L.dw[k];
+        pk.b[pk.n] = L.db[k];
+        ++pk.n;
+    }
+    e = launch_hash_tc_pack(m->params, pk, m->tc_w, m->tc_bias, m->ctx->stream);
+    m->ctx->launches++;
+    if (e == cudaSuccess) m->tc_ver = m->ver;
+    return e;
+}
+
+static HashTcArgs hash_tc_base(const ndf_hash_model* m) {
+    HashTcArgs a;
+    a.E = embed_args(m->Ly);
+    a.measure = m->measure;
+    a.X = m->X;
+    a.Y = m->Y;
+    a.Z = m->Z;
+    a.status = m->ctx->flag.as<unsigned>() + 1;
+    return a;
+}
+
+static int hash_tc_ctas(const ndf_hash_model* m, int64_t rows, int R) {
+    const int64_t groups = ((rows + 127) / 128 + 1) / 2;
+    int64_t c = (m->ctx->sm_count + R - 1) / R;
+    if (c > groups) c = groups;
+    return c < 1 ? 1 : (int)c;
+}
+
+// encode-only launch: the FP32 latents of encoder `en` for rows vertices
+// (vlist when given, else 0 .. rows-1) into lat[rows][128]
+static cudaError_t hash_tc_encode(ndf_hash_model* m, int en, const int64_t* vlist, int64_t rows, float* lat) {
+    const HashLayout& L = m->Ly;
+    HashTcArgs a = hash_tc_base(m);
+    a.tables = m->params + L.enc_size * en;
+    a.wimg = m->tc_w + hash_tc_layer_bytes() * (size_t)(en * L.le);
+    a.bias = m->tc_bias + (size_t)128 * (en * L.le);
+    a.nL = L.le;
+    a.n_enc = L.le;
+    a.merge = -1;
+    a.N = rows;
+    if (vlist) {
+        a.vlist_n = (int)rows;
+        for (int64_t i = 0; i < rows; ++i) a.vlist[i] = vlist[i];
+    }
+    a.lat = lat;
+    m->ctx->launches++;
+    return launch_hash_tc(a, L.act, hash_tc_ctas(m, rows, 1), 1, m->ctx->stream);
+}
+
+// volumes of R <= kHashTcMaxRefs references into out[R][N] (device)
+static cudaError_t hash_tc_decode(ndf_hash_model* m, const int64_t* refs, int R, float* out) {
+    const HashLayout& L = m->Ly;
+    ndf_ctx* ctx = m->ctx;
+    const int64_t N = m->X * m->Y * m->Z;
+    cudaError_t e = hash_tc_prepare(m);
+    if (e != cudaSuccess) return e;
+    // reference latents (encoder 0)
+    if (L.le == 0) {
+        HashTcArgs a = hash_tc_base(m);
+        a.tables = m->params;
+        a.vlist_n = R;
+        for (int i = 0; i < R; ++i) a.vlist[i] = refs[i];
+        e = launch_hash_tc_embed_refs(a, m->tc_zr, ctx->stream);
+        ctx->launches++;
+    } else {
+        e = hash_tc_encode(m, 0, refs, R, m->tc_zr);
+    }
+    if (e != cudaSuccess) return e;
+    const int eq = L.n_enc - 1;
+    const bool cached = m->cache_q && hash_tc_cache_ok(L);
+    if (cached && m->lat_ver != m->ver) {
+        if (!m->tc_lat && (e = cudaMalloc(&m->tc_lat, sizeof(float) * 128 * (size_t)N)) != cudaSuccess) return e;
+        if ((e = hash_tc_encode(m, eq, nullptr, N, m->tc_lat)) != cudaSuccess) return e;
+        m->lat_ver = m->ver;
+    }
+    HashTcArgs a = hash_tc_base(m);
+    a.merge = L.merge;
+    a.zr = m->tc_zr;
+    a.w_last = m->params + L.dw[L.ld - 1];
+    a.b_last = m->params + L.db[L.ld - 1];
+    a.N = N;
+    a.out = out;
+    const int first = cached ? L.n_enc * L.le : eq * L.le;
+    a.wimg = m->tc_w + hash_tc_layer_bytes() * (size_t)first;
+    a.bias = m->tc_bias + (size_t)128 * first;
+    if (cached) {
+        a.lat_in = m->tc_lat;
+        a.nL = L.ld - 1;
+        a.n_enc = 0;
+    } else {
+        a.tables = m->params + L.enc_size * eq;
+        a.nL = L.le + L.ld - 1;
+        a.n_enc = L.le;
+    }
+    ctx->launches++;
+    return launch_hash_tc(a, L.act, hash_tc_ctas(m, N, R), R, ctx->stream);
+}
+
+// the FP32 path for one reference: the reference encoded once, queries in chunks
+static cudaError_t hash_fp32_decode(ndf_hash_model* m, int64_t ref_idx, float* dev_out) {
+    ndf_ctx* ctx = m->ctx;
+    const HashLayout& L = m->Ly;
+    const int64_t N = m->X * m->Y * m->Z;
+    const int64_t chunk = std::min<int64_t>(N, 65536);
+    cudaError_t e = hash_workspace(m, chunk);
+    if (e != cudaSuccess) return e;
+    vertex_positions_kernel<<<1, 32, 0, ctx->stream>>>(ref_idx, 1, m->X, m->Y, m->Z, m->pos);
+    ctx->launches++;
+    e = encode_side(m, 0, 0, m->pos, 1);
+    const float* zr = latent(m, 0);
+    for (int64_t v0 = 0; v0 < N && e == cudaSuccess; v0 += chunk) {
+        const int64_t n = std::min(chunk, N - v0);
+        vertex_positions_kernel<<<blocks_for(n), 256, 0, ctx->stream>>>(v0, n, m->X, m->Y, m->Z,
+                                                                         m->pos + 3);
+        ctx->launches++;
+        e = encode_side(m, L.n_enc - 1, 1, m->pos + 3, n);
+        if (e != cudaSuccess) break;
+        merge_kernel<<<blocks_for((int64_t)L.dlat * n), 256, 0, ctx->stream>>>(
+            zr, 0, latent(m, 1), L.dlat, n, L.merge, m->z);
+        ctx->launches++;
+        if ((e = decode_z(m, n)) != cudaSuccess) break;
+        out_loss_kernel<<<blocks_for(n), 256, 0, ctx->stream>>>(m->pre_d[L.ld - 1], nullptr, n, m->measure,
+                                                                 dev_out + v0, nullptr, nullptr);
+        ctx->launches++;
+        e = cudaGetLastError();
+    }
+    return e;
+}
 }  // namespace ndf
 
 extern "C" {
@@ -622,6 +646,7 @@ ndf_status ndf_hash_model_create(ndf_ctx* ctx, const ndf_hash_arch* arch, int me
         ndf_hash_model_free(m);
         return cuda_fail(ctx, e, "hash model initialisation");
     }
+    m->decode_tc = hash_tc_eligible(m->Ly) ? 1 : 0;
     *out = m;
     return NDF_OK;
 }
@@ -629,7 +654,7 @@ ndf_status ndf_hash_model_create(ndf_ctx* ctx, const ndf_hash_arch* arch, int me
 void ndf_hash_model_free(ndf_hash_model* m) {
     if (!m) return;
     if (m->ctx) cudaStreamSynchronize(m->ctx->stream);
-    void* ps[] = {m->params, m->grad, m->m, m->v, m->ws};
+    void* ps[] = {m->params, m->grad, m->m, m->v, m->ws, m->tc_w, m->tc_bias, m->tc_zr, m->tc_lat};
     for (void* q : ps)
         if (q) cudaFree(q);
     if (m->blas) cublasDestroy(m->blas);
@@ -651,6 +676,7 @@ ndf_status ndf_hash_model_set_params(ndf_hash_model* m, const float* in) {
     const size_t bytes = sizeof(float) * (size_t)m->Ly.total;
     cudaError_t e = cudaMemcpyAsync(m->params, in, bytes, cudaMemcpyDefault, m->ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->ctx->stream);
+    ++m->ver;
     return e == cudaSuccess ? NDF_OK : cuda_fail(m->ctx, e, "hash params upload");
 }
 
@@ -673,6 +699,7 @@ ndf_status ndf_hash_model_step(ndf_hash_model* m, const float* pr, const float* 
     if (e == cudaSuccess) e = hash_forward_backward(m, m->pos, m->pos + 3 * B, m->tgt, B, nullptr);
     if (e == cudaSuccess && apply) {
         ++m->t;
+        ++m->ver;
         const float c1 = 1.0f - powf(0.9f, (float)m->t), c2 = 1.0f - powf(0.999f, (float)m->t);
         hash_adam_kernel<<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(
             m->params, m->grad, m->m, m->v, m->Ly.total, lr, 0.9f, 0.999f, 1e-8f, c1, c2);
@@ -706,46 +733,59 @@ ndf_status ndf_hash_model_forward(ndf_hash_model* m, const float* pr, const floa
     return e == cudaSuccess ? NDF_OK : cuda_fail(ctx, e, "hash forward");
 }
 
-// the volume of one reference vertex: the reference is encoded once, queries in chunks
+// the volume of one reference vertex (tensor-core decoder or the FP32 chain)
 ndf_status ndf_hash_infer(ndf_hash_model* m, int64_t ref_idx, float* out) {
-    if (!m || !out) return NDF_ERR_ARG;
+    return ndf_hash_infer_batch(m, &ref_idx, 1, out);
+}
+
+ndf_status ndf_hash_infer_batch(ndf_hash_model* m, const int64_t* refs, int32_t R, float* out) {
+    if (!m || !refs || !out || R < 1) return NDF_ERR_ARG;
     ndf_ctx* ctx = m->ctx;
     const int64_t N = m->X * m->Y * m->Z;
-    if (ref_idx < 0 || ref_idx >= N) return fail(ctx, NDF_ERR_ARG, "ref_idx out of range");
+    for (int32_t i = 0; i < R; ++i)
+        if (refs[i] < 0 || refs[i] >= N) return fail(ctx, NDF_ERR_ARG, "ref_idx out of range");
     cudaSetDevice(ctx->device);
-    const int64_t chunk = std::min<int64_t>(N, 65536);
-    cudaError_t e = hash_workspace(m, chunk);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "hash workspace");
     void* dev_out;
     bool is_host;
-    ndf_status st = resolve_out(ctx, out, sizeof(float) * (size_t)N, &dev_out, &is_host);
+    const size_t bytes = sizeof(float) * (size_t)N * (size_t)R;
+    ndf_status st = resolve_out(ctx, out, bytes, &dev_out, &is_host);
     if (st != NDF_OK) return st;
-    const HashLayout& L = m->Ly;
-    // the reference latent: side 0 with a batch of one
-    vertex_positions_kernel<<<1, 32, 0, ctx->stream>>>(ref_idx, 1, m->X, m->Y, m->Z, m->pos);
-    ctx->launches++;
-    e = encode_side(m, 0, 0, m->pos, 1);
-    const float* zr = latent(m, 0);
-    for (int64_t v0 = 0; v0 < N && e == cudaSuccess; v0 += chunk) {
-        const int64_t n = std::min(chunk, N - v0);
-        vertex_positions_kernel<<<blocks_for(n), 256, 0, ctx->stream>>>(v0, n, m->X, m->Y, m->Z,
-                                                                         m->pos + 3);
-        ctx->launches++;
-        e = encode_side(m, L.n_enc - 1, 1, m->pos + 3, n);
-        if (e != cudaSuccess) break;
-        merge_kernel<<<blocks_for((int64_t)L.dlat * n), 256, 0, ctx->stream>>>(
-            zr, 0, latent(m, 1), L.dlat, n, L.merge, m->z);
-        ctx->launches++;
-        if ((e = decode_z(m, n)) != cudaSuccess) break;
-        out_loss_kernel<<<blocks_for(n), 256, 0, ctx->stream>>>(
-            m->pre_d[L.ld - 1], nullptr, n, m->measure, static_cast<float*>(dev_out) + v0, nullptr,
-            nullptr);
-        ctx->launches++;
-        e = cudaGetLastError();
+    float* o = static_cast<float*>(dev_out);
+    cudaError_t e = cudaSuccess;
+    if (m->decode_tc) {
+        for (int32_t r0 = 0; r0 < R && e == cudaSuccess; r0 += kHashTcMaxRefs)
+            e = hash_tc_decode(m, refs + r0, std::min<int32_t>(kHashTcMaxRefs, R - r0), o + (size_t)r0 * N);
+    } else {
+        for (int32_t r = 0; r < R && e == cudaSuccess; ++r) e = hash_fp32_decode(m, refs[r], o + (size_t)r * N);
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "hash decode");
-    return finish_out(ctx, out, dev_out, sizeof(float) * (size_t)N, is_host);
+    return finish_out(ctx, out, dev_out, bytes, is_host);
 }
+
+ndf_status ndf_hash_set_decode(ndf_hash_model* m, int32_t mode, int32_t cache_queries) {
+    if (!m) return NDF_ERR_ARG;
+    if (mode != NDF_HASH_DECODE_FP32 && mode != NDF_HASH_DECODE_TC)
+        return fail(m->ctx, NDF_ERR_ARG, "unknown decode mode %d", mode);
+    if (mode == NDF_HASH_DECODE_TC && !hash_tc_eligible(m->Ly))
+        return fail(m->ctx, NDF_ERR_ARG,
+                    "the tensor-core decoder needs width 128, at most 128 embedding inputs and a "
+                    "product / sum / |difference| merge");
+    if (cache_queries && (mode != NDF_HASH_DECODE_TC || !hash_tc_cache_ok(m->Ly)))
+        return fail(m->ctx, NDF_ERR_ARG,
+                    "the query-latent cache needs the tensor-core decoder, an encoder layer and two "
+                    "decoder layers");
+    m->decode_tc = mode;
+    m->cache_q = cache_queries ? 1 : 0;
+    if (!m->cache_q && m->tc_lat) {
+        cudaStreamSynchronize(m->ctx->stream);
+        cudaFree(m->tc_lat);
+        m->tc_lat = nullptr;
+        m->lat_ver = -1;
+    }
+    return NDF_OK;
+}
+
+int32_t ndf_hash_get_decode(const ndf_hash_model* m) { return m ? m->decode_tc : -1; }
 
 // training on continuous samples renewed every pass (Sec. 4.3)
 ndf_status ndf_hash_train(ndf_ctx* ctx, int ref_field, int query_field, int measure, int k,

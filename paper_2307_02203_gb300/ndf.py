@@ -30,6 +30,7 @@ NDF_KSG_BRUTE, NDF_KSG_PRUNED = 0, 1
 NDF_RENDER_DVR, NDF_RENDER_ISO = 0, 1
 NDF_ACT_RELU, NDF_ACT_SNAKE, NDF_ACT_SNAKEALT = 0, 1, 2
 NDF_MERGE_PRODUCT, NDF_MERGE_SUM, NDF_MERGE_ABSDIFF, NDF_MERGE_CONCAT = 0, 1, 2, 3
+NDF_HASH_DECODE_FP32, NDF_HASH_DECODE_TC = 0, 1
 
 
 class HashArch(ctypes.Structure):
@@ -106,6 +107,9 @@ _sig("ndf_hash_model_info", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int),
                                            ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(_i64)])
 _sig("ndf_hash_infer", ctypes.c_int, [_vp, _i64, _vp])
+_sig("ndf_hash_infer_batch", ctypes.c_int, [_vp, _vp, ctypes.c_int32, _vp])
+_sig("ndf_hash_set_decode", ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32])
+_sig("ndf_hash_get_decode", ctypes.c_int32, [_vp])
 _sig("ndf_pearson_batch", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int,
                                          ctypes.c_int, _vp])
 _sig("ndf_set_ksg_algorithm", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int])
@@ -416,6 +420,22 @@ def ndf_hash_model_info(m) -> dict:
 
 def ndf_hash_infer(m, ref_idx: int, out) -> None:
     _check(m.ctx, _lib.ndf_hash_infer(m, ref_idx, _addr(out)), "ndf_hash_infer")
+
+
+def ndf_hash_infer_batch(m, ref_idx, out) -> None:
+    import numpy as _np
+
+    refs = _np.ascontiguousarray(_np.asarray(ref_idx, dtype=_np.int64))
+    _check(m.ctx, _lib.ndf_hash_infer_batch(m, refs.ctypes.data, int(refs.shape[0]), _addr(out)),
+           "ndf_hash_infer_batch")
+
+
+def ndf_hash_set_decode(m, mode: int, cache_queries: bool = False) -> None:
+    _check(m.ctx, _lib.ndf_hash_set_decode(m, mode, int(bool(cache_queries))), "ndf_hash_set_decode")
+
+
+def ndf_hash_get_decode(m) -> int:
+    return int(_lib.ndf_hash_get_decode(m))
 
 
 def ndf_pearson_noalloc(ref_field, query_field, M, N, ref_idx, out, cuda_stream=None) -> None:

@@ -153,3 +153,121 @@ def test_grid_only_latent_is_the_embedding():
     a, b = rng.uniform(-1, 1, (10, 3)), rng.uniform(-1, 1, (10, 3))
     np.testing.assert_allclose(oracle.hash_forward(s, p, a, b), np.tanh(a[:, 0] * b[:, 0]),
                                atol=1e-15)
+
+
+# ---- the BF16-operand forward (the arithmetic of the tensor-core decoder)
+
+def test_bf16_round_values():
+    """Round to nearest BF16 (8 significant bits), ties to even."""
+    r = oracle.bf16_round
+    assert r(1.0) == 1.0 and r(-2.5) == -2.5 and r(0.0) == 0.0
+    assert r(1 + 2 ** -8) == 1.0                      # tie, 1.0000000 is even
+    assert r(1 + 3 * 2 ** -8) == 1 + 2 ** -6          # tie, 1.0000001 is odd: up
+    assert r(1 + 2 ** -8 + 2 ** -20) == 1 + 2 ** -7   # above the tie: up
+    assert r(0.1) == 0.10009765625                    # 1.1001101 x 2^-4
+    assert r(-(1 + 2 ** -9)) == -1.0                  # below the tie: down
+    assert math.isinf(r(1e39)) and math.isnan(r(float("nan")))
+
+
+def _offsets(s):
+    """Offsets of the flat parameter layout of the header: tables, encoder layers, decoder layers."""
+    din = 3 + 6 * s.n_freq + s.levels * s.feat
+    ent = [min((s.base_res << l) ** 3, 2 ** s.log2_table) for l in range(s.levels)]
+    o = sum(ent) * s.feat
+    enc = []
+    for k in range(s.enc_layers):
+        cin = din if k == 0 else s.width
+        enc.append((o, s.width, cin, o + cin * s.width))
+        o += cin * s.width + s.width
+    o *= s.n_enc
+    dec = []
+    for k in range(s.dec_layers):
+        out = 1 if k == s.dec_layers - 1 else s.width
+        cin = (s.width if s.enc_layers else din) if k == 0 else s.width
+        dec.append((o, out, cin, o + cin * out))
+        o += cin * out + out
+    assert o == oracle.hash_param_count(s)
+    return dict(din=din, ent=ent, enc=enc, dec=dec)
+
+
+def _constant_tables(s, p, values):
+    """Every entry of level l, feature f holds values[l][f] (BF16-exact), so that
+    the trilinear feature of any position is that value."""
+    o = 0
+    for l, e in enumerate(_offsets(s)["ent"]):
+        for f in range(s.feat):
+            p[o + f:o + e * s.feat:s.feat] = values[l][f]
+        o += e * s.feat
+
+
+def _rounded(p, layers):
+    q = p.copy()
+    for (w, out, cin, _) in layers:
+        q[w:w + out * cin] = [oracle.bf16_round(x) for x in p[w:w + out * cin]]
+    return q
+
+
+VALS = [[0.75, -1.25], [0.5, 1.5]]  # BF16-exact, and so are their squares
+
+
+def test_bf16_forward_rounds_encoder_weights_only():
+    """One encoder layer, output layer on the merged latent.  At p = 0 the embedding
+    [0, 0, 0, sin 0, cos 0, table values] is BF16-exact, so the BF16 forward must
+    equal the FP64 forward with the encoder weights rounded and everything else
+    (latent, merge, output layer) untouched."""
+    s = shape(levels=2, base_res=2, log2_table=5, n_freq=1, width=8, enc_layers=1, dec_layers=1,
+              act=0)
+    off = _offsets(s)
+    p = np.random.default_rng(5).normal(0, 0.7, oracle.hash_param_count(s))
+    _constant_tables(s, p, VALS)
+    z = np.zeros((1, 3))
+    got = oracle.hash_forward_bf16(s, p, z, z)
+    want = oracle.hash_forward(s, _rounded(p, off["enc"]), z, z)
+    np.testing.assert_allclose(got, want, rtol=1e-14, atol=0)
+    assert abs(got[0] - oracle.hash_forward(s, p, z, z)[0]) > 1e-6  # the rounding mattered
+
+
+def test_bf16_forward_rounds_hidden_decoder_weights_only():
+    """Grid-only network (no encoder layer), one hidden decoder layer.  At p = 0 the
+    merged latent x0 * x0 = [0, 0, 0, 0, 1, values^2] is BF16-exact: the BF16 forward
+    equals the FP64 forward with the hidden layer's weights rounded; the output layer
+    (weights and inputs) is not rounded."""
+    s = shape(levels=2, base_res=2, log2_table=5, n_freq=1, width=8, enc_layers=0, dec_layers=2,
+              act=0)
+    off = _offsets(s)
+    p = np.random.default_rng(6).normal(0, 0.7, oracle.hash_param_count(s))
+    _constant_tables(s, p, VALS)
+    z = np.zeros((1, 3))
+    got = oracle.hash_forward_bf16(s, p, z, z)
+    want = oracle.hash_forward(s, _rounded(p, off["dec"][:1]), z, z)
+    np.testing.assert_allclose(got, want, rtol=1e-14, atol=0)
+    assert abs(got[0] - oracle.hash_forward(s, _rounded(p, off["dec"]), z, z)[0]) > 1e-6
+
+
+def test_bf16_forward_rounds_layer_inputs():
+    """No Fourier features, constant tables, one encoder layer with BF16-exact weights:
+    the BF16 forward is out(w . (h(p_r) * h(p_q)) + b) with h(p) = W [bf16(p), values] + b1,
+    i.e. the positions enter the product rounded."""
+    s = shape(levels=2, base_res=2, log2_table=5, n_freq=0, width=8, enc_layers=1, dec_layers=1,
+              act=0, measure=1)
+    off = _offsets(s)
+    p = np.random.default_rng(7).normal(0, 0.7, oracle.hash_param_count(s))
+    _constant_tables(s, p, VALS)
+    p = _rounded(p, off["enc"])
+    (w1, c, din, b1), = off["enc"]
+    (wo, _, _, bo), = off["dec"]
+    W, b, wout = p[w1:w1 + c * din].reshape(c, din), p[b1:b1 + c], p[wo:wo + c]
+    pr, pq = np.array([[1 / 3, -0.7, 0.1]]), np.array([[0.3, 0.45, -0.9]])
+
+    def h(pos, rnd):
+        x = np.concatenate([[rnd(v) for v in pos[0]], [VALS[0][0], VALS[0][1], VALS[1][0], VALS[1][1]]])
+        return W @ x + b
+
+    def soft(x):
+        return math.log1p(math.exp(-abs(x))) + max(x, 0.0)
+
+    got = oracle.hash_forward_bf16(s, p, pr, pq)[0]
+    want = soft(wout @ (h(pr, oracle.bf16_round) * h(pq, oracle.bf16_round)) + p[bo])
+    assert got == pytest.approx(want, rel=1e-12, abs=1e-14)
+    plain = soft(wout @ (h(pr, float) * h(pq, float)) + p[bo])
+    assert abs(got - plain) > 1e-6
