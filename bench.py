@@ -316,6 +316,13 @@ def measure_hash_ndf(ndf, ctx, fid, recipe, stream, args, grid_only=False, n_fre
     cfg.lr = 1e-3
     cfg.max_decays = 100
     cfg.time_budget_s = float(args.ndf_seconds)
+    # warm-up: the first training steps of a process load kernels and pick GEMM algorithms
+    warm = ndf.ndf_hash_model_create(ctx, arch, ndf.NDF_MEASURE_PEARSON, False, 1, recipe.X, recipe.Y,
+                                     recipe.Z)
+    wp = torch.rand((cfg.batch, 3), device="cuda") * 2 - 1
+    for _ in range(10):
+        ndf.ndf_hash_model_step(warm, wp, wp, wp[:, 0].contiguous(), 1e-3, True)
+    ndf.ndf_hash_model_free(warm)
     t0 = time.perf_counter()
     model = ndf.ndf_hash_train(ctx, fid, fid, ndf.NDF_MEASURE_PEARSON, 0, arch, cfg)
     ndf.ndf_synchronize(ctx)

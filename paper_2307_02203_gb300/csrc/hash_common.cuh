@@ -95,7 +95,7 @@ inline EmbedArgs embed_args(const HashLayout& Ly) {
 }
 
 struct Cell {
-    int64_t idx[8];
+    uint32_t idx[8];  // entry index (< 2^30)
     float w[8];
 };
 
@@ -114,11 +114,11 @@ __device__ __forceinline__ Cell level_cell(const EmbedArgs& E, int l, const floa
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const int x = i0[0] + (q & 1), y = i0[1] + ((q >> 1) & 1), z = i0[2] + ((q >> 2) & 1);
-        if (E.dense[l]) {
-            c.idx[q] = (int64_t)x + (int64_t)R * y + (int64_t)R * R * z;
+        if (E.dense[l]) {  // R^3 <= 2^T <= 2^30
+            c.idx[q] = (uint32_t)x + (uint32_t)R * ((uint32_t)y + (uint32_t)R * (uint32_t)z);
         } else {
             const uint32_t h = (uint32_t)x * 1u ^ (uint32_t)y * 2654435761u ^ (uint32_t)z * 805459861u;
-            c.idx[q] = (int64_t)(h & (uint32_t)(E.entries[l] - 1));  // entries = 2^T
+            c.idx[q] = h & (uint32_t)(E.entries[l] - 1);  // entries = 2^T
         }
         c.w[q] = ((q & 1) ? t[0] : 1.0f - t[0]) * (((q >> 1) & 1) ? t[1] : 1.0f - t[1]) *
                  (((q >> 2) & 1) ? t[2] : 1.0f - t[2]);
@@ -129,9 +129,9 @@ __device__ __forceinline__ Cell level_cell(const EmbedArgs& E, int l, const floa
 
 // The embedding of one position (FP32): emit(k, value) for k = 0 .. din-1 in
 // order [p_0..2, (sin, cos)(2^i pi p_j) for j < 3, i < L, level features].
+// embed_fourier emits the first 3 + 6 L entries, embed_grid the level features.
 template <class Emit>
-__device__ __forceinline__ void embed_point(const EmbedArgs& E, const float* __restrict__ tables,
-                                            const float* p, Emit&& emit) {
+__device__ __forceinline__ void embed_fourier(const EmbedArgs& E, const float* p, Emit&& emit) {
     emit(0, p[0]);
     emit(1, p[1]);
     emit(2, p[2]);
@@ -142,16 +142,62 @@ __device__ __forceinline__ void embed_point(const EmbedArgs& E, const float* __r
             emit(3 + (j * E.L + i) * 2, s);
             emit(4 + (j * E.L + i) * 2, c);
         }
-    for (int l = 0; l < E.levels; ++l) {
+}
+
+// grid features of levels [l0, l1): emit(l * F + f, value).  With two features
+// per entry, two levels at a time: their 16 corner loads are in flight together.
+template <class Emit>
+__device__ __forceinline__ void embed_levels(const EmbedArgs& E, const float* __restrict__ tables,
+                                             const float* p, int l0, int l1, Emit&& emit) {
+    int l = l0;
+    if (E.F == 2) {
+        for (; l + 1 < l1; l += 2) {
+            const Cell ca = level_cell(E, l, p), cb = level_cell(E, l + 1, p);
+            const float2* ta = reinterpret_cast<const float2*>(tables + E.toff[l]);
+            const float2* tb = reinterpret_cast<const float2*>(tables + E.toff[l + 1]);
+            float2 ga[8], gb[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                ga[q] = __ldg(ta + ca.idx[q]);
+                gb[q] = __ldg(tb + cb.idx[q]);
+            }
+            float2 va = make_float2(0.0f, 0.0f), vb = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                va.x += ca.w[q] * ga[q].x;
+                va.y += ca.w[q] * ga[q].y;
+                vb.x += cb.w[q] * gb[q].x;
+                vb.y += cb.w[q] * gb[q].y;
+            }
+            emit(l * 2, va.x);
+            emit(l * 2 + 1, va.y);
+            emit(l * 2 + 2, vb.x);
+            emit(l * 2 + 3, vb.y);
+        }
+    }
+    for (; l < l1; ++l) {
         const Cell cl = level_cell(E, l, p);
         const float* tab = tables + E.toff[l];
         for (int f = 0; f < E.F; ++f) {
             float v = 0.0f;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) v += cl.w[q] * __ldg(tab + cl.idx[q] * E.F + f);
-            emit(3 + 6 * E.L + l * E.F + f, v);
+            for (int q = 0; q < 8; ++q) v += cl.w[q] * __ldg(tab + (int64_t)cl.idx[q] * E.F + f);
+            emit(l * E.F + f, v);
         }
     }
+}
+
+template <class Emit>
+__device__ __forceinline__ void embed_grid(const EmbedArgs& E, const float* __restrict__ tables,
+                                           const float* p, Emit&& emit) {
+    embed_levels(E, tables, p, 0, E.levels, [&](int g, float v) { emit(3 + 6 * E.L + g, v); });
+}
+
+template <class Emit>
+__device__ __forceinline__ void embed_point(const EmbedArgs& E, const float* __restrict__ tables,
+                                            const float* p, Emit&& emit) {
+    embed_fourier(E, p, emit);
+    embed_grid(E, tables, p, emit);
 }
 
 // vertex v of an X x Y x Z grid -> its vertex-aligned position in [-1,1]^3

@@ -59,7 +59,7 @@ __global__ void hash_embed_backward_kernel(const float* __restrict__ pos, int64_
             const float gv = g[l * E.F + f];
             if (gv == 0.0f) continue;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) atomicAdd(tab + cl.idx[q] * E.F + f, cl.w[q] * gv);
+            for (int q = 0; q < 8; ++q) atomicAdd(tab + (int64_t)cl.idx[q] * E.F + f, cl.w[q] * gv);
         }
     }
 }
@@ -185,7 +185,8 @@ namespace ndf {
 // and the element-wise merges (not concatenation)
 static bool hash_tc_eligible(const HashLayout& L) {
     const int nL = L.le + L.ld - 1;
-    return L.c == 128 && L.din <= 128 && L.merge != NDF_MERGE_CONCAT && nL >= 1 && nL <= kHashTcMaxLayers;
+    const int kin = 3 * hash_tc_f8(L.L) + 3 + L.levels * L.F;  // embedding columns in operand order
+    return L.c == 128 && kin <= 128 && L.merge != NDF_MERGE_CONCAT && nL >= 1 && nL <= kHashTcMaxLayers;
 }
 
 // the query-latent cache needs a latent (an encoder layer) and a decoder layer after it
@@ -213,11 +214,12 @@ struct ndf_hash_model {
     float *ones = nullptr, *graw = nullptr, *tgt = nullptr, *pos = nullptr;
     double* loss = nullptr;
     // tensor-core decoding: packed BF16 weight images and biases of the parameter
-    // version tc_ver, reference latents, optional cache of the query latents
+    // version tc_ver, reference latents, per-axis Fourier features of the decode
+    // grid, optional cache of the query latents
     int decode_tc = 0, cache_q = 0;
     int64_t ver = 0, tc_ver = -1, lat_ver = -1;
     unsigned char* tc_w = nullptr;
-    float *tc_bias = nullptr, *tc_zr = nullptr, *tc_lat = nullptr;
+    float *tc_bias = nullptr, *tc_zr = nullptr, *tc_lat = nullptr, *tc_ftab = nullptr;
     // training record
     int passes = 0;
     double last_loss = 0.0, gen_seconds = 0.0, train_seconds = 0.0;
@@ -418,18 +420,28 @@ static cudaError_t hash_tc_prepare(ndf_hash_model* m) {
         e = cudaMalloc(&m->tc_w, lb * (size_t)n);
         if (e == cudaSuccess) e = cudaMalloc(&m->tc_bias, sizeof(float) * 128 * (size_t)n);
         if (e == cudaSuccess) e = cudaMalloc(&m->tc_zr, sizeof(float) * 128 * (size_t)kHashTcMaxRefs);
+        const int f8 = hash_tc_f8(L.L);
+        const size_t nf = (size_t)(m->X + m->Y + m->Z) * (size_t)f8;
+        if (e == cudaSuccess) e = cudaMalloc(&m->tc_ftab, sizeof(float) * std::max<size_t>(nf, 4));
+        if (e == cudaSuccess) e = launch_hash_tc_ftab(L.L, f8, m->X, m->Y, m->Z, m->tc_ftab, m->ctx->stream);
+        m->ctx->launches++;
         if (e != cudaSuccess) return e;
     }
     if (m->tc_ver == m->ver) return cudaSuccess;
     HashTcPack pk;
+    pk.L = L.L;
+    pk.f8 = hash_tc_f8(L.L);
+    pk.ngrid = L.levels * L.F;
     for (int en = 0; en < L.n_enc; ++en)
         for (int k = 0; k < L.le; ++k) {
+            pk.perm[pk.n] = k == 0;
             pk.cin[pk.n] = k == 0 ? L.din : L.c;
             pk.w[pk.n] = L.enc_size * en + L.ew[k];
             pk.b[pk.n] = L.enc_size * en + L.eb[k];
             ++pk.n;
         }
     for (int k = 0; k < L.ld - 1; ++k) {
+        pk.perm[pk.n] = k == 0 && L.le == 0;  // grid-only: the merged embedding
         pk.cin[pk.n] = k == 0 ? L.ddec : L.c;
         pk.w[pk.n] = L.dw[k];
         pk.b[pk.n] = L.db[k];
@@ -449,14 +461,20 @@ static HashTcArgs hash_tc_base(const ndf_hash_model* m) {
     a.Y = m->Y;
     a.Z = m->Z;
     a.status = m->ctx->flag.as<unsigned>() + 1;
+    a.ftab = m->tc_ftab;
+    a.f8 = hash_tc_f8(m->Ly.L);
+    a.foff[0] = 0;
+    a.foff[1] = m->X * a.f8;
+    a.foff[2] = (m->X + m->Y) * a.f8;
     return a;
 }
 
+// CTAs per reference: the SMs shared among the references (the launcher caps it at
+// the tile groups there are)
 static int hash_tc_ctas(const ndf_hash_model* m, int64_t rows, int R) {
-    const int64_t groups = ((rows + 127) / 128 + 1) / 2;
-    int64_t c = (m->ctx->sm_count + R - 1) / R;
-    if (c > groups) c = groups;
-    return c < 1 ? 1 : (int)c;
+    (void)rows;
+    const int c = (m->ctx->sm_count + R - 1) / R;
+    return c < 1 ? 1 : c;
 }
 
 // encode-only launch: the FP32 latents of encoder `en` for rows vertices
@@ -654,7 +672,8 @@ ndf_status ndf_hash_model_create(ndf_ctx* ctx, const ndf_hash_arch* arch, int me
 void ndf_hash_model_free(ndf_hash_model* m) {
     if (!m) return;
     if (m->ctx) cudaStreamSynchronize(m->ctx->stream);
-    void* ps[] = {m->params, m->grad, m->m, m->v, m->ws, m->tc_w, m->tc_bias, m->tc_zr, m->tc_lat};
+    void* ps[] = {m->params, m->grad, m->m, m->v, m->ws, m->tc_w, m->tc_bias, m->tc_zr, m->tc_lat,
+                  m->tc_ftab};
     for (void* q : ps)
         if (q) cudaFree(q);
     if (m->blas) cublasDestroy(m->blas);

@@ -212,6 +212,26 @@ def test_ablations_vs_oracle(ndf_mod, ctx, act, merge, enc_layers, dec_layers):
     ndf_mod.ndf_hash_model_free(m)
 
 
+@pytest.mark.parametrize("n_freq,levels,feat", [(3, 5, 1), (0, 6, 2), (5, 3, 4), (12, 6, 2)])
+def test_embedding_layouts(ndf_mod, ctx, n_freq, levels, feat):
+    """The embedding enters the first layer in operand order: Fourier blocks padded to
+    16-byte chunks per axis, then position and grid features.  Frequencies whose
+    2 L is not a multiple of 8, no Fourier features, odd feature counts."""
+    X, Y, Z = 23, 7, 6
+    N = X * Y * Z
+    a = arch(ndf_mod, n_freq=n_freq, levels=levels, feat=feat, enc_layers=2, dec_layers=2)
+    m = ndf_mod.ndf_hash_model_create(ctx, a, 0, False, 8, X, Y, Z)
+    assert ndf_mod.ndf_hash_get_decode(m) == ndf_mod.NDF_HASH_DECODE_TC
+    p = make_params(a, 1, 60 + n_freq + levels)
+    ndf_mod.ndf_hash_model_set_params(m, p)
+    out = np.empty(N, np.float32)
+    r = 300
+    ndf_mod.ndf_hash_infer(m, r, out)
+    bf, fp = oracle_pair(oshape(a, False, 0), p, positions(X, Y, Z), r, np.arange(N))
+    check(out, bf, fp, f"L {n_freq} levels {levels} F {feat}")
+    ndf_mod.ndf_hash_model_free(m)
+
+
 def test_small_grids_many_references(ndf_mod, ctx):
     """Fewer vertices than one tile; 70 references (two launches of at most 64)."""
     X, Y, Z = 5, 4, 3
