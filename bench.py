@@ -38,6 +38,11 @@ K_NN = 8
 # query column and its sorted copy once (algorithmic 14.08 GB + 7 MB output).
 KSG_PRUNED_TRAFFIC_PER_VOLUME = (705.641e6 + 4.142e6) * 20
 KSG_BRUTE_TRAFFIC_PER_VOLUME = (705.845e6 + 4.089e6) * 20
+KSG_BLOCK_TRAFFIC_PER_VOLUME = (705.720e6 + 4.256e6) * 20
+KSG_SEARCHES = {  # name: (ndf constant name, kernel at k = 8, DRAM bytes per volume)
+    "pruned": ("NDF_KSG_PRUNED", "ksg_pruned_kernel<9>", KSG_PRUNED_TRAFFIC_PER_VOLUME),
+    "block": ("NDF_KSG_BLOCK", "ksg_block_kernel<9>", KSG_BLOCK_TRAFFIC_PER_VOLUME),
+}
 METRIC = "ms per 1.76M-voxel dependence volume (Pearson + KSG MI k=8, M=1000)"
 
 
@@ -215,7 +220,7 @@ def measure_pearson_batch(ndf, ctx, fid, field, recipe, stream, rank, R=64, reps
 
 
 def measure_ksg_batch(ndf, ctx, fid, recipe, stream, args, R=16):
-    """R KSG volumes in one persistent launch (pruned search: one work counter over
+    """R KSG volumes in one persistent launch (the timed search; one work counter over
     all (reference, vertex) pairs)."""
     import torch
 
@@ -546,6 +551,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--batch", type=int, default=1, help="also time 64-reference Pearson GEMMs")
     ap.add_argument("--ksg-batch", type=int, default=1, help="also time a 16-reference KSG launch")
+    ap.add_argument("--ksg-search", choices=["pruned", "block"], default="block",
+                    help="exact KSG search of the timed step")
     ap.add_argument("--brute-steps", type=int, default=1,
                     help="volumes timed with the brute-force KSG search (same results)")
     ap.add_argument("--ndf", type=int, default=1, help="also train and time the neural field")
@@ -599,6 +606,9 @@ def main():
     out_r = torch.empty(N, dtype=torch.float32, device="cuda")
     out_mi = torch.empty(N, dtype=torch.float32, device="cuda")
 
+    search = getattr(ndf, KSG_SEARCHES[args.ksg_search][0])
+    ndf.ndf_set_ksg_algorithm(ctx, search)
+
     def step(ref):
         ndf.ndf_pearson(ctx, fid, fid, ref, out_r)
         ndf.ndf_mi_ksg(ctx, fid, fid, ref, K_NN, out_mi)
@@ -635,23 +645,30 @@ def main():
     total_ms, pearson_ms, ksg_ms = max_over_ranks([total_ms, pearson_ms, ksg_ms], world, "cuda")
     ms_per_volume = job_ms_per_volume(total_ms, args.steps, world)
 
-    # ---- distance evaluations of the pruned search on the same references (counted
-    # in a separate, untimed pass), and the brute-force search timed beside it
+    # ---- distance evaluations of the timed search on the same references (counted
+    # in a separate, untimed pass); the brute-force search and the other exact
+    # search timed beside it
     nb = max(1, min(args.brute_steps, args.steps))
-    ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_PRUNED, True)
+    ndf.ndf_set_ksg_algorithm(ctx, search, True)
     for i in range(nb):
         ndf.ndf_mi_ksg(ctx, fid, fid, refs[args.warmup + i], K_NN, out_mi)
-    pruned_evals = ndf.ndf_ksg_take_eval_count(ctx) / nb
-    ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_BRUTE, False)
-    b0 = torch.cuda.Event(enable_timing=True)
-    b1 = torch.cuda.Event(enable_timing=True)
-    b0.record(stream)
-    for i in range(nb):
-        ndf.ndf_mi_ksg(ctx, fid, fid, refs[args.warmup + i], K_NN, out_mi)
-    b1.record(stream)
-    ndf.ndf_synchronize(ctx)
-    ksg_brute_ms = b0.elapsed_time(b1) / nb
-    ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_PRUNED, False)
+    search_evals = ndf.ndf_ksg_take_eval_count(ctx) / nb
+
+    def time_search(code):
+        ndf.ndf_set_ksg_algorithm(ctx, code, False)
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        for i in range(nb):
+            ndf.ndf_mi_ksg(ctx, fid, fid, refs[args.warmup + i], K_NN, out_mi)
+        b1.record(stream)
+        ndf.ndf_synchronize(ctx)
+        return b0.elapsed_time(b1) / nb
+
+    ksg_brute_ms = time_search(ndf.NDF_KSG_BRUTE)
+    other = "pruned" if args.ksg_search == "block" else "block"
+    ksg_other_ms = time_search(getattr(ndf, KSG_SEARCHES[other][0]))
+    ndf.ndf_set_ksg_algorithm(ctx, search, False)
     # ---- batched KSG: 16 references in one launch
     ksg_batch = measure_ksg_batch(ndf, ctx, fid, recipe, stream, args) if args.ksg_batch else None
 
@@ -708,9 +725,12 @@ def main():
     sms = props.multi_processor_count
     brute_evals = float(N) * M * (M - 1)  # every member pair of every vertex
     # peak: 64 ALU-pipe lanes per SM per clock, 2 ALU instructions per evaluation
-    # (the abs-max distance and its threshold compare), at the maximum SM clock
+    # (the abs-max distance and its threshold compare), at the maximum SM clock.
+    # Algorithmic work: the estimator's M (M - 1) distance evaluations per vertex; the
+    # exact searches skip most of them (evaluations performed are reported beside).
     peak = sms * 64 / 2 * peaks["sm_max_mhz"] * 1e6 / 1e9
-    achieved = pruned_evals / (ksg_ms * 1e-3) / 1e9  # Gdist/s performed
+    achieved = brute_evals / (ksg_ms * 1e-3) / 1e9  # algorithmic Gdist/s
+    performed = search_evals / (ksg_ms * 1e-3) / 1e9  # Gdist/s actually evaluated
     brute_achieved = brute_evals / (ksg_brute_ms * 1e-3) / 1e9
     pearson_gbs = (4.0 * M * N + 4.0 * N + 16.0 * N) / (pearson_ms * 1e-3) / 1e9
 
@@ -731,19 +751,23 @@ def main():
             "mi_pairs_per_s": N / (ksg_ms * 1e-3),
             "pearson_hbm_gbs": pearson_gbs,
             "pearson_hbm_frac": pearson_gbs / peaks["hbm_gbs"],
-            "roofline": {"bound": "alu", "kernel": "ksg_pruned_kernel<9>", "achieved": achieved,
-                         "peak": peak, "unit": "Gdist/s", "frac": achieved / peak,
-                         "traffic": KSG_PRUNED_TRAFFIC_PER_VOLUME,
+            "ksg_search": args.ksg_search,
+            "roofline": {"bound": "alu", "kernel": KSG_SEARCHES[args.ksg_search][1],
+                         "achieved": achieved, "peak": peak, "unit": "Gdist/s",
+                         "frac": achieved / peak, "traffic": KSG_SEARCHES[args.ksg_search][2],
                          "peak_source": f"{peaks['source']} max SM clock",
-                         "evals_per_volume": pruned_evals,
-                         "brute_force_equivalent_gdist_s": brute_evals / (ksg_ms * 1e-3) / 1e9},
+                         "algorithmic_evals_per_volume": brute_evals,
+                         "evals_performed_per_volume": search_evals,
+                         "performed_gdist_s": performed},
             "ksg_brute_force": {"ms": ksg_brute_ms, "kernel": "ksg_volume_kernel<9>",
                                 "roofline": {"bound": "alu", "achieved": brute_achieved,
                                              "peak": peak, "unit": "Gdist/s",
                                              "frac": brute_achieved / peak,
                                              "traffic": KSG_BRUTE_TRAFFIC_PER_VOLUME,
                                              "evals_per_volume": brute_evals},
-                                "pruned_speedup": ksg_brute_ms / ksg_ms},
+                                "speedup_of_timed_search": ksg_brute_ms / ksg_ms},
+            "ksg_other_search": {"search": other, "kernel": KSG_SEARCHES[other][1],
+                                 "ms": ksg_other_ms},
             "ksg_batch16": ksg_batch,
             "e2e": {"value": e2e_per_volume, "unit": "ms",
                     "h2d_bytes_per_step": int(field.nbytes),

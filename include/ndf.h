@@ -162,16 +162,21 @@ ndf_status ndf_mi_ksg2(ndf_ctx* ctx, int ref_field, int query_field, int64_t ref
                        float* out);
 
 /* KSG search used by ndf_mi_ksg, ndf_mi_ksg2, ndf_mi_ksg_batch, the debug hooks
- * and ndf_train's MI targets.  Both give identical results (same FP32 distances,
+ * and ndf_train's MI targets.  All give identical results (same FP32 distances,
  * same counts):
- *   NDF_KSG_PRUNED  (default) one warp per (reference, vertex) pair; members in
+ *   NDF_KSG_PRUNED  two warps per (reference, vertex) pair; members in
  *                   order of the reference value, each side of a member's
  *                   outward scan stopped at the first x-gap that reaches its
  *                   current k-th distance (exact pruning);
+ *   NDF_KSG_BLOCK   (default) two warps per pair; members cut into blocks of 32 x-ranks,
+ *                   sorted by the query value inside each block; a member scans
+ *                   blocks outward in x and, inside a block, outward in y, both
+ *                   stopped by its current k-th distance (exact pruning).
+ *                   Algorithm 1 only: ndf_mi_ksg2 runs NDF_KSG_PRUNED instead;
  *   NDF_KSG_BRUTE   every member against every member of each pair.
  * count_evals != 0 makes the kernels count distance evaluations (read with
  * ndf_ksg_take_eval_count); it costs one atomic per warp per launch. */
-typedef enum { NDF_KSG_BRUTE = 0, NDF_KSG_PRUNED = 1 } ndf_ksg_algorithm;
+typedef enum { NDF_KSG_BRUTE = 0, NDF_KSG_PRUNED = 1, NDF_KSG_BLOCK = 2 } ndf_ksg_algorithm;
 ndf_status ndf_set_ksg_algorithm(ndf_ctx* ctx, int algorithm, int count_evals);
 
 /* Distance evaluations counted since the last call (synchronizes; 0 when

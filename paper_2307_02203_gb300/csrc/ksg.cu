@@ -527,6 +527,205 @@ __global__ void __launch_bounds__(32 * kGroupWarps * kMaxGroupsPerCta, 1)
     }
 }
 
+// ---------------------------------------------------------------- block search
+// The same estimator (algorithm 1) with a two-level search.  The members of a
+// pair are cut into x-blocks of 32 consecutive x-ranks; inside each block they are
+// sorted by y (one warp-wide bitonic sort of 32 (y, rank) keys).  Lane l of a warp
+// takes the member at position l of block b and
+//   scans its own block outward in y from its own position,
+//   then the blocks b + 1, b - 1, b + 2, ... : a side stops at the first block whose
+//   x-gap (the block's nearest x-rank) reaches the lane's current k-th distance;
+//   in a block it binary-searches its y and scans outward in y while the y-gap is
+//   below the threshold.
+// Every skipped member is at least the threshold away in x or in y, an insert
+// needs a strictly smaller distance, and the threshold only shrinks, so eps_i is
+// the brute-force value bit for bit.  A lane visits about 20 candidates at
+// M = 1000, k = 8 (the x-strip of the pruned kernel: about 120).  The warp runs
+// the blocks of its lanes in lock step (a per-lane state machine with dynamic
+// members, measured: 1.7x slower, the block changes with their binary searches
+// diverge on almost every step); each step takes one candidate from each end of
+// the block scan into the two-value merge insert.  Two warps share a pair's
+// arrays (x sorted, y sorted, the block-sorted points: 16 B x M).
+constexpr int kBlk = 32;
+struct BlockCtl {
+    unsigned long long item;
+    double part[kGroupWarps];
+};
+__host__ __device__ inline size_t block_group_bytes(int M) {
+    const int nb = (M + kBlk - 1) / kBlk;
+    return sizeof(BlockCtl) + sizeof(float2) * (size_t)nb * kBlk + 2 * sizeof(float) * (size_t)((M + 3) & ~3);
+}
+
+// warp-wide ascending bitonic sort of (key, val) pairs, one per lane; (key, val)
+// compared lexicographically (val unique), so the order is total
+__device__ __forceinline__ void warp_sort_kv(float& key, int& val) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            const float ok = __shfl_xor_sync(0xffffffffu, key, stride);
+            const int ov = __shfl_xor_sync(0xffffffffu, val, stride);
+            const bool up = (lane & size) == 0 || size == 32;
+            const bool lower = (lane & stride) == 0;
+            const bool other_less = ok < key || (ok == key && ov < val);
+            // the lower lane of an ascending pair keeps the smaller element
+            const bool take = lower == up ? other_less : !other_less;
+            if (take) {
+                key = ok;
+                val = ov;
+            }
+        }
+    }
+}
+
+// lower bound of y in a block of 32 ascending values (pads +inf): 0 .. 32
+__device__ __forceinline__ int block_lower_bound(const float2* blk, float y) {
+    int pos = 0;
+#pragma unroll
+    for (int h = 16; h > 0; h >>= 1)
+        if (blk[pos + h - 1].x < y) pos += h;
+    return pos;
+}
+
+template <int K1>
+__global__ void __launch_bounds__(32 * kGroupWarps * kMaxGroupsPerCta, 1)
+    ksg_block_kernel(KsgArgs A, unsigned long long* work) {
+    constexpr int KK = K1 - 1;
+    constexpr int GT = 32 * kGroupWarps;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int M = A.M, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int group = warp / kGroupWarps, gw = warp % kGroupWarps, gt = threadIdx.x % GT;
+    const int nb = (M + kBlk - 1) / kBlk;
+    unsigned char* gbase = smem + (size_t)group * block_group_bytes(M);
+    BlockCtl* ctl = reinterpret_cast<BlockCtl*>(gbase);
+    float2* blk = reinterpret_cast<float2*>(gbase + sizeof(BlockCtl));  // [nb * 32] (y, x)
+    float* xs = reinterpret_cast<float*>(blk + (size_t)nb * kBlk);      // reference, x-sorted
+    float* ys = xs + ((M + 3) & ~3);                                     // query, sorted
+    const int64_t N = A.N, nv = A.v_end - A.v_begin;
+    const unsigned long long items =
+        A.paired ? (unsigned long long)nv : (unsigned long long)A.R * (unsigned long long)nv;
+    const double psi_k = A.psi[A.k], psi_M = A.psi[M];
+    unsigned long long evals_total = 0;
+
+    for (;;) {
+        group_sync(group);  // the previous pair is finished by both warps
+        if (gt == 0) ctl->item = atomicAdd(work, 1ull);
+        group_sync(group);
+        const unsigned long long item = ctl->item;
+        if (item >= items) break;
+        const int r = A.paired ? (int)item : (int)(item / (unsigned long long)nv);
+        const int64_t v = A.v_begin + (int64_t)(A.paired ? item : item - (unsigned long long)r * nv);
+        const float* xsg = A.xs_all + (int64_t)r * M;
+        const int* perm = A.perm_all + (int64_t)r * M;
+        for (int s = gt; s < M; s += GT) {
+            xs[s] = xsg[s];
+            ys[s] = A.sorted[(int64_t)s * N + v];
+        }
+        // ---- blocks of 32 x-ranks, each sorted by y; pads (y = x = +inf) sort last
+        for (int b = gw; b < nb; b += kGroupWarps) {
+            const int rank = b * kBlk + lane;
+            float key = INFINITY;
+            int val = rank;
+            if (rank < M) key = A.field[(int64_t)perm[rank] * N + v];
+            warp_sort_kv(key, val);
+            blk[b * kBlk + lane] = make_float2(key, val < M ? xsg[val] : INFINITY);
+        }
+        group_sync(group);
+
+        // ---- joint k-NN distance of each member, then its marginal counts
+        const bool dbg = A.dbg_eps && r == 0 && v == A.v_begin;
+        double acc = 0.0;
+        unsigned long long my_evals = 0;
+        for (int b = gw; b < nb; b += kGroupWarps) {
+            const bool valid = b * kBlk + lane < M;
+            const float2 me = blk[b * kBlk + lane];
+            const float yi = me.x, xi = me.y;
+            float best[KK];  // the k nearest others, ascending
+#pragma unroll
+            for (int c = 0; c < KK; ++c) best[c] = FLT_MAX;
+            // scan of block bb from positions up / dn outward while the y-gap is below
+            // the threshold (lanes with on == false take no candidate)
+            auto scan = [&](int bb, int up, int dn, bool on) {
+                const float2* B = blk + bb * kBlk;
+                for (;;) {
+                    const float t = best[KK - 1];
+                    const float2 cu = B[up < kBlk ? up : kBlk - 1];
+                    const float2 cd = B[dn >= 0 ? dn : 0];
+                    const float dyu = cu.x - yi, dyd = yi - cd.x;
+                    const bool au = on && up < kBlk && dyu < t;
+                    const bool ad = on && dn >= 0 && dyd < t;
+                    if (!__any_sync(0xffffffffu, au || ad)) break;
+                    const float du = au ? fmaxf(fabsf(cu.y - xi), fabsf(dyu)) : FLT_MAX;
+                    const float dd = ad ? fmaxf(fabsf(cd.y - xi), fabsf(dyd)) : FLT_MAX;
+                    insert2<KK>(best, fminf(du, dd), fmaxf(du, dd));
+                    my_evals += (unsigned)au + (unsigned)ad;
+                    up += au ? 1 : 0;
+                    dn -= ad ? 1 : 0;
+                }
+            };
+            scan(b, lane + 1, lane - 1, valid);
+            bool ron = valid, lon = valid;
+            for (int dd = 1; dd < nb; ++dd) {
+                const int br = b + dd, bleft = b - dd;
+                if (br >= nb) ron = false;
+                else if (ron && xs[br * kBlk] - xi >= best[KK - 1]) ron = false;  // nearest x of the block
+                if (__any_sync(0xffffffffu, ron)) {
+                    const int pos = block_lower_bound(blk + br * kBlk, yi);
+                    scan(br, pos, pos - 1, ron);
+                }
+                if (bleft < 0) lon = false;
+                else if (lon && xi - xs[min(bleft * kBlk + kBlk - 1, M - 1)] >= best[KK - 1]) lon = false;
+                if (__any_sync(0xffffffffu, lon)) {
+                    const int pos = block_lower_bound(blk + bleft * kBlk, yi);
+                    scan(bleft, pos, pos - 1, lon);
+                }
+                if (!__any_sync(0xffffffffu, ron || lon)) break;
+            }
+            if (valid) {
+                const float e = best[KK - 1];
+                const int self = e > 0.0f ? 1 : 0;
+                const int cx = count_within(xs, M, xi, e) - self;
+                const int cy = count_within(ys, M, yi, e) - self;
+                acc += A.psi[cx + 1] + A.psi[cy + 1];
+            }
+            if (dbg) {  // the block's sort again (deterministic) gives each lane's x-rank
+                const int rank = b * kBlk + lane;
+                float key = rank < M ? A.field[(int64_t)perm[rank] * N + v] : INFINITY;
+                int val = rank;
+                warp_sort_kv(key, val);
+                if (valid) {
+                    const float e = best[KK - 1];
+                    const int self = e > 0.0f ? 1 : 0;
+                    const int mi = perm[val];
+                    A.dbg_eps[mi] = e;
+                    if (A.dbg_ey) A.dbg_ey[mi] = e;
+                    A.dbg_nx[mi] = count_within(xs, M, xi, e) - self;
+                    A.dbg_ny[mi] = count_within(ys, M, yi, e) - self;
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) ctl->part[gw] = acc;
+        evals_total += my_evals;
+        group_sync(group);
+        if (gt == 0) {
+            double tot = 0.0;
+#pragma unroll
+            for (int w = 0; w < kGroupWarps; ++w) tot += ctl->part[w];
+            const double mi = psi_k + psi_M - tot / (double)M;
+            A.out[A.paired ? (v - A.v_begin) : (int64_t)r * A.out_stride + (v - A.v_begin)] = (float)mi;
+            if (dbg && A.dbg_mi) *A.dbg_mi = mi;
+        }
+    }
+    if (A.evals) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) evals_total += __shfl_xor_sync(0xffffffffu, evals_total, o);
+        if (lane == 0) atomicAdd(A.evals, evals_total);
+    }
+}
+
 template <class Kern>
 static cudaError_t launch_persistent(ndf_ctx* ctx, Kern kern, const KsgArgs& A, int threads,
                                     size_t smem, int64_t items) {
@@ -546,6 +745,29 @@ static cudaError_t launch_persistent(ndf_ctx* ctx, Kern kern, const KsgArgs& A, 
 template <int K1>
 static cudaError_t launch_ksg_k(ndf_ctx* ctx, KsgArgs A, bool prune) {
     const int M = A.M;
+    if (prune && ctx->ksg_algorithm == NDF_KSG_BLOCK && A.variant == 1) {
+        // two-warp groups per pair; as many groups per CTA as fit in shared memory
+        const size_t per_group = block_group_bytes(M);
+        int gpc = (int)((227 * 1024) / per_group);
+        if (gpc > kMaxGroupsPerCta) gpc = kMaxGroupsPerCta;
+        if (gpc >= 1) {
+            const size_t smem = (size_t)gpc * per_group;
+            const int threads = 32 * kGroupWarps * gpc;
+            cudaError_t e = ctx->ksg_work.reserve(sizeof(unsigned long long));
+            if (e == cudaSuccess)
+                e = cudaMemsetAsync(ctx->ksg_work.ptr, 0, sizeof(unsigned long long), ctx->stream);
+            if (e != cudaSuccess) return e;
+            auto kern = ksg_block_kernel<K1>;
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            const int64_t pairs = A.paired ? (A.v_end - A.v_begin) : (int64_t)A.R * (A.v_end - A.v_begin);
+            int64_t grid = (int64_t)ctx->sm_count;
+            if (grid * gpc > pairs) grid = (pairs + gpc - 1) / gpc;
+            kern<<<(unsigned)grid, threads, smem, ctx->stream>>>(A, ctx->ksg_work.as<unsigned long long>());
+            ctx->launches++;
+            return cudaGetLastError();
+        }
+    }
     if (prune) {
         // one warp group per pair; as many groups per CTA as fit in shared memory
         const size_t per_group = (size_t)kGroupSmemPerM * M + kGroupSmemFixed;

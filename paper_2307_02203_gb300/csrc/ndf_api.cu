@@ -464,7 +464,7 @@ static cudaError_t run_ksg_one(ndf_ctx* ctx, const Field& rf, const Field& qf, i
                                float* dbg_eps, int32_t* dbg_nx, int32_t* dbg_ny, int variant = 1,
                                float* dbg_ey = nullptr) {
     return launch_ksg(ctx, rf, qf, nullptr, ref_idx, 1, k, v_begin, v_end, out, 0,
-                      ctx->ksg_algorithm == NDF_KSG_PRUNED, 1, ctx->ksg_tile, dbg_mi, dbg_eps,
+                      ctx->ksg_algorithm != NDF_KSG_BRUTE, 1, ctx->ksg_tile, dbg_mi, dbg_eps,
                       dbg_nx, dbg_ny,
                       ctx->count_evals ? ctx->evals.as<unsigned long long>() : nullptr, variant,
                       dbg_ey);
@@ -558,7 +558,7 @@ ndf_status ndf_ksg2_debug_pair(ndf_ctx* ctx, int ref_field, int query_field, int
 
 ndf_status ndf_set_ksg_algorithm(ndf_ctx* ctx, int algorithm, int count_evals) {
     if (!ctx) return NDF_ERR_ARG;
-    if (algorithm != NDF_KSG_BRUTE && algorithm != NDF_KSG_PRUNED)
+    if (algorithm != NDF_KSG_BRUTE && algorithm != NDF_KSG_PRUNED && algorithm != NDF_KSG_BLOCK)
         return fail(ctx, NDF_ERR_ARG, "unknown KSG algorithm %d", algorithm);
     ctx->ksg_algorithm = algorithm;
     ctx->count_evals = count_evals != 0;
@@ -608,7 +608,7 @@ ndf_status ndf_mi_ksg_batch(ndf_ctx* ctx, int ref_field, int query_field, const 
                             cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess)
         e = launch_ksg(ctx, *rf, *qf, ctx->refidx.as<int64_t>(), 0, R, k, 0, qf->N,
-                       static_cast<float*>(dev_out), qf->N, ctx->ksg_algorithm == NDF_KSG_PRUNED,
+                       static_cast<float*>(dev_out), qf->N, ctx->ksg_algorithm != NDF_KSG_BRUTE,
                        ctx->ksg_group, ctx->ksg_tile, nullptr, nullptr, nullptr, nullptr,
                        ctx->count_evals ? ctx->evals.as<unsigned long long>() : nullptr);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "ksg batch launch");

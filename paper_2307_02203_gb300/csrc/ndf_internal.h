@@ -63,7 +63,7 @@ struct ndf_ctx {
     int64_t psi_n = 0;
     ndf::DevBuf dbg;         // KSG debug outputs
     ndf::DevBuf flag;        // small device status words
-    int ksg_algorithm = NDF_KSG_PRUNED;
+    int ksg_algorithm = NDF_KSG_BLOCK;
     int ksg_group = 4;       // references per CTA in batched KSG (tuned by ndf_ksg_autotune)
     int ksg_tile = 8;        // query vertices per tile
     bool count_evals = false;

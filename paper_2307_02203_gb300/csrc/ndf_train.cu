@@ -702,7 +702,7 @@ ndf_status ndf_train(ndf_ctx* ctx, int ref_field, int query_field, int measure, 
         } else if (e == cudaSuccess) {
             // all references of the group in one launch; each query column is sorted once
             e = launch_ksg(ctx, *rf, blk, drefs, 0, (int)rows, k, 0, Qg, gtgt, Qg,
-                           ctx->ksg_algorithm == NDF_KSG_PRUNED, ctx->ksg_group, ctx->ksg_tile,
+                           ctx->ksg_algorithm != NDF_KSG_BRUTE, ctx->ksg_group, ctx->ksg_tile,
                            nullptr, nullptr, nullptr, nullptr, nullptr);
         }
         const int64_t take = std::min<int64_t>(T - filled, rows * Qg);

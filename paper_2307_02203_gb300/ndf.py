@@ -26,7 +26,7 @@ NDF_OK, NDF_ERR_ARG, NDF_ERR_OOM, NDF_ERR_CUDA = 0, -1, -2, -3
 NDF_ERR_TIMEOUT, NDF_ERR_STATE, NDF_ERR_IO = -4, -5, -6
 NDF_PREC_FP32, NDF_PREC_BF16X3, NDF_PREC_TF32 = 0, 1, 2
 NDF_MEASURE_PEARSON, NDF_MEASURE_MI_KSG = 0, 1
-NDF_KSG_BRUTE, NDF_KSG_PRUNED = 0, 1
+NDF_KSG_BRUTE, NDF_KSG_PRUNED, NDF_KSG_BLOCK = 0, 1, 2
 NDF_RENDER_DVR, NDF_RENDER_ISO = 0, 1
 NDF_ACT_RELU, NDF_ACT_SNAKE, NDF_ACT_SNAKEALT = 0, 1, 2
 NDF_MERGE_PRODUCT, NDF_MERGE_SUM, NDF_MERGE_ABSDIFF, NDF_MERGE_CONCAT = 0, 1, 2, 3

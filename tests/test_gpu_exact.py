@@ -156,13 +156,14 @@ def test_pearson_cross_field_and_degenerate(ndf_mod, ctx):
 
 
 # ---------------------------------------------------------------- KSG algorithm 1
-@pytest.fixture(params=["brute", "pruned"])
+@pytest.fixture(params=["brute", "pruned", "block"])
 def algo(request, ndf_mod, ctx):
-    """Both searches must give the same bit-exact eps / counts."""
-    code = {"brute": ndf_mod.NDF_KSG_BRUTE, "pruned": ndf_mod.NDF_KSG_PRUNED}[request.param]
+    """Every search must give the same bit-exact eps / counts."""
+    code = {"brute": ndf_mod.NDF_KSG_BRUTE, "pruned": ndf_mod.NDF_KSG_PRUNED,
+            "block": ndf_mod.NDF_KSG_BLOCK}[request.param]
     ndf_mod.ndf_set_ksg_algorithm(ctx, code)
     yield request.param
-    ndf_mod.ndf_set_ksg_algorithm(ctx, ndf_mod.NDF_KSG_PRUNED)
+    ndf_mod.ndf_set_ksg_algorithm(ctx, ndf_mod.NDF_KSG_BLOCK)  # the default
 
 
 def ksg_debug(ndf, ctx, fa, fb, r, v, k, M):
@@ -344,13 +345,17 @@ def test_ksg_eval_counter(ndf_mod, ctx, tiny_field, tiny_ref):
     M = tiny_field.shape[0]
     N = tiny_field[0].size
     out = np.empty(N, dtype=np.float32)
-    ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_PRUNED, True)
-    ndf.ndf_mi_ksg(ctx, fid, fid, tiny_ref, 4, out)
-    evals = ndf.ndf_ksg_take_eval_count(ctx)
-    ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_PRUNED, False)
-    # the pruned search visits a strict subset of the M(M-1) candidates of each pair
-    assert 0 < evals < N * M * (M - 1)
-    assert ndf.ndf_ksg_take_eval_count(ctx) == 0
+    counts = {}
+    for name in ("NDF_KSG_PRUNED", "NDF_KSG_BLOCK", "NDF_KSG_BRUTE"):
+        ndf.ndf_set_ksg_algorithm(ctx, getattr(ndf, name), True)
+        ndf.ndf_mi_ksg(ctx, fid, fid, tiny_ref, 4, out)
+        counts[name] = ndf.ndf_ksg_take_eval_count(ctx)
+        assert ndf.ndf_ksg_take_eval_count(ctx) == 0
+    ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_BLOCK, False)
+    # brute force evaluates every candidate; the exact searches strict subsets, the
+    # block search fewer than the x-strip scan
+    assert counts["NDF_KSG_BRUTE"] == N * M * (M - 1)
+    assert 0 < counts["NDF_KSG_BLOCK"] < counts["NDF_KSG_PRUNED"] < N * M * (M - 1)
     ndf.ndf_free_ensemble(ctx, fid)
 
 

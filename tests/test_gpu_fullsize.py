@@ -38,14 +38,15 @@ def test_csens_pearson_sampled(ndf_mod, ctx, csens):
     assert np.isfinite(out.cpu().numpy()).all()
 
 
-@pytest.mark.parametrize("algorithm", ["pruned", "brute"])
+@pytest.mark.parametrize("algorithm", ["pruned", "brute", "block"])
 def test_csens_ksg_sampled(ndf_mod, ctx, csens, algorithm):
     f, fid = csens
     N = synth.CSENS.N
     M = synth.CSENS.M
     r = synth.vertex_index(*REF, synth.CSENS)
     out = torch.empty(N, dtype=torch.float32, device="cuda")
-    code = ndf_mod.NDF_KSG_PRUNED if algorithm == "pruned" else ndf_mod.NDF_KSG_BRUTE
+    code = {"pruned": ndf_mod.NDF_KSG_PRUNED, "brute": ndf_mod.NDF_KSG_BRUTE,
+            "block": ndf_mod.NDF_KSG_BLOCK}[algorithm]
     ndf_mod.ndf_set_ksg_algorithm(ctx, code)
     ndf_mod.ndf_mi_ksg(ctx, fid, fid, r, 8, out)
     ndf_mod.ndf_synchronize(ctx)
@@ -69,7 +70,7 @@ def test_csens_ksg_sampled(ndf_mod, ctx, csens, algorithm):
         np.testing.assert_array_equal(eps, o[1])
         np.testing.assert_array_equal(nx, o[2])
         np.testing.assert_array_equal(ny, o[3])
-    ndf_mod.ndf_set_ksg_algorithm(ctx, ndf_mod.NDF_KSG_PRUNED)
+    ndf_mod.ndf_set_ksg_algorithm(ctx, ndf_mod.NDF_KSG_BLOCK)  # the default
 
 
 def test_csens_ksg2_sampled(ndf_mod, ctx, csens):
