@@ -560,7 +560,7 @@ def main():
     ap.add_argument("--ndf-hash", type=int, default=1,
                     help="also train the paper's hash-grid architecture (continuous samples)")
     ap.add_argument("--ndf-hash-variants", type=int, default=0,
-                    help="also train the grid-only ablation of the hash-grid architecture")
+                    help="also train the L = 4 and grid-only variants of the hash-grid architecture")
     ap.add_argument("--ndf-cross", type=int, default=1,
                     help="also train cross-field networks (reference in A, query in a second field B)")
     ap.add_argument("--ndf-triples", type=int, default=1 << 26, help="Pearson training triples")
@@ -693,9 +693,9 @@ def main():
         ndf_res = {} if ndf_res is None else ndf_res
         if args.ndf_hash:
             ndf_res["hash_grid_pearson"] = measure_hash_ndf(ndf, ctx, fid, recipe, stream, args)
+        if args.ndf_hash_variants:
             ndf_res["hash_grid_pearson_L4"] = measure_hash_ndf(ndf, ctx, fid, recipe, stream, args,
                                                                n_freq=4)
-        if args.ndf_hash_variants:
             ndf_res["hash_grid_only_pearson"] = measure_hash_ndf(ndf, ctx, fid, recipe, stream,
                                                                  args, grid_only=True)
 

@@ -241,6 +241,8 @@ typedef struct {
     int32_t continuous;       /* 0: grid-vertex pairs, generated once; 1: uniform random
                                  positions with trilinear samples (ndf_sample_triples),
                                  n_triples fresh pairs every pass (Sec. 4.3) [0] */
+    int32_t hash_tf32;        /* ndf_hash_train: dense layers as TF32 tensor-core GEMMs
+                                 (10-bit mantissa operands, FP32 accumulation); 0: FP32 [1] */
 } ndf_train_cfg;
 
 /* What a model is and how it was trained. */

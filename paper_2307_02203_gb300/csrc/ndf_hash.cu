@@ -700,6 +700,24 @@ ndf_status ndf_hash_model_set_params(ndf_hash_model* m, const float* in) {
 }
 
 // positions / targets / outputs may be host or device; staged through the workspace
+// one training step on device batches (no copies, no host synchronisation): the
+// summed |error| of the batch accumulates in m->loss
+static cudaError_t hash_train_step(ndf_hash_model* m, const float* pr, const float* pq,
+                                   const float* target, int64_t B, float lr) {
+    ndf_ctx* ctx = m->ctx;
+    cudaError_t e = cudaMemsetAsync(m->grad, 0, sizeof(float) * (size_t)m->Ly.total, ctx->stream);
+    if (e == cudaSuccess) e = hash_forward_backward(m, pr, pq, target, B, nullptr);
+    if (e != cudaSuccess) return e;
+    ++m->t;
+    ++m->ver;
+    const float c1 = 1.0f - powf(0.9f, (float)m->t), c2 = 1.0f - powf(0.999f, (float)m->t);
+    hash_adam_kernel<<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(m->params, m->grad, m->m, m->v,
+                                                                m->Ly.total, lr, 0.9f, 0.999f, 1e-8f,
+                                                                c1, c2);
+    ctx->launches++;
+    return cudaGetLastError();
+}
+
 ndf_status ndf_hash_model_step(ndf_hash_model* m, const float* pr, const float* pq,
                                const float* target, int64_t B, float lr, int apply,
                                float* grad_out, double* loss_out) {
@@ -830,6 +848,7 @@ ndf_status ndf_hash_train(ndf_ctx* ctx, int ref_field, int query_field, int meas
         return st;
     }
     const int64_t T = cfg.n_triples, B = std::min(cfg.batch, T);
+    if (cfg.hash_tf32) cublasSetMathMode(m->blas, CUBLAS_TF32_TENSOR_OP_MATH);
     float *pref = nullptr, *pq = nullptr, *tgt = nullptr;
     cudaError_t e = cudaMalloc(&pref, sizeof(float) * 3 * (size_t)T);
     if (e == cudaSuccess) e = cudaMalloc(&pq, sizeof(float) * 3 * (size_t)T);
@@ -851,18 +870,15 @@ ndf_status ndf_hash_train(ndf_ctx* ctx, int ref_field, int query_field, int meas
         e = sample_triples_dev(ctx, *rf, *qf, measure, k, T, cfg.seed + (uint64_t)pass, pref, pq, tgt, sc);
         m->gen_seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - g0).count();
         if (e != cudaSuccess) break;
+        // the pass's steps run back to back; its summed |error| is read once
+        e = cudaMemsetAsync(m->loss, 0, sizeof(double), ctx->stream);
+        for (int64_t b0 = 0; b0 < T && e == cudaSuccess; b0 += B)
+            e = hash_train_step(m, pref + 3 * b0, pq + 3 * b0, tgt + b0, std::min(B, T - b0), lr);
         double pass_sum = 0.0;
-        for (int64_t b0 = 0; b0 < T && e == cudaSuccess; b0 += B) {
-            const int64_t nb = std::min(B, T - b0);
-            double l = 0.0;
-            st = ndf_hash_model_step(m, pref + 3 * b0, pq + 3 * b0, tgt + b0, nb, lr, 1, nullptr, &l);
-            if (st != NDF_OK) {
-                cleanup();
-                ndf_hash_model_free(m);
-                return st;
-            }
-            pass_sum += l * (double)nb;
-        }
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&pass_sum, m->loss, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) break;
         const double pass_loss = pass_sum / (double)T;
         m->last_loss = pass_loss;
         m->passes = pass + 1;
@@ -880,6 +896,7 @@ ndf_status ndf_hash_train(ndf_ctx* ctx, int ref_field, int query_field, int meas
     m->train_seconds =
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count() - m->gen_seconds;
     m->n_triples = T;
+    cublasSetMathMode(m->blas, CUBLAS_DEFAULT_MATH);  // the step / forward calls stay FP32
     cleanup();
     if (e != cudaSuccess) {
         ndf_hash_model_free(m);

@@ -365,6 +365,7 @@ void ndf_train_cfg_default(ndf_train_cfg* c) {
     c->seed = 20230705ULL;
     c->time_budget_s = 0.0;
     c->continuous = 0;
+    c->hash_tf32 = 1;
 }
 
 ndf_status ndf_model_create(ndf_ctx* ctx, const int res[4], int measure, uint64_t seed, int64_t X,

@@ -133,7 +133,7 @@ class TrainCfg(ctypes.Structure):
                 ("patience", ctypes.c_int), ("max_decays", ctypes.c_int), ("lr", ctypes.c_float),
                 ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
                 ("seed", ctypes.c_uint64), ("time_budget_s", ctypes.c_double),
-                ("continuous", ctypes.c_int32)]
+                ("continuous", ctypes.c_int32), ("hash_tf32", ctypes.c_int32)]
 
 
 class ModelInfo(ctypes.Structure):
