@@ -101,6 +101,21 @@ ndf_status ndf_load_ensemble(ndf_ctx* ctx, const float* field, int64_t M, int64_
  * allocating; ndf_trim_cache or ndf_destroy returns them to the device. */
 ndf_status ndf_free_ensemble(ndf_ctx* ctx, int field_id);
 
+/* Load an ensemble (as ndf_load_ensemble) and compute one reference vertex's
+ * Pearson volume (Sec. 3.1) and KSG-MI volume (algorithm 1, Sec. 3.2) with the
+ * upload pipelined against the computation: the field is copied in vertex ranges
+ * (the reference's range first) on the context's copy stream, and each range's
+ * statistics, column sort and KSG search run on the context's stream as soon as
+ * it has arrived; Pearson follows the last range.  The same kernels as
+ * ndf_load_ensemble + ndf_pearson + ndf_mi_ksg, so the same results.  Outputs
+ * (host or device, N floats each) may be NULL to skip that measure.  The field
+ * stays loaded (*field_id_out).  Errors as ndf_load_ensemble, ndf_pearson and
+ * ndf_mi_ksg; non-finite input is reported after the pipeline drained
+ * (NDF_ERR_ARG, nothing stays loaded). */
+ndf_status ndf_load_and_compute(ndf_ctx* ctx, const float* field, int64_t M, int64_t Z, int64_t Y,
+                                int64_t X, int64_t ref_idx, int k, float* pearson_out,
+                                float* mi_out, int* field_id_out);
+
 /* Free every device buffer the context keeps from released fields (synchronizes
  * the context's stream first). */
 ndf_status ndf_trim_cache(ndf_ctx* ctx);

@@ -377,6 +377,93 @@ ndf_status ndf_load_ensemble(ndf_ctx* ctx, const float* field, int64_t M, int64_
     return NDF_OK;
 }
 
+// Upload, statistics, column sorts and the KSG search pipelined over vertex ranges:
+// range r's search runs on the context's stream while range r + 1 is copied on the
+// copy stream.  The reference's range goes first (both searches stage its column).
+ndf_status ndf_load_and_compute(ndf_ctx* ctx, const float* field, int64_t M, int64_t Z, int64_t Y,
+                                int64_t X, int64_t ref_idx, int k, float* pearson_out,
+                                float* mi_out, int* field_id_out) {
+    if (!ctx) return NDF_ERR_ARG;
+    if (!field || !field_id_out) return fail(ctx, NDF_ERR_ARG, "null pointer");
+    if (M < 2 || Z < 1 || Y < 1 || X < 1)
+        return fail(ctx, NDF_ERR_ARG, "need M >= 2 and a non-empty grid");
+    const int64_t N = Z * Y * X;
+    if (N / X / Y != Z || M > (int64_t(1) << 40) / N) return fail(ctx, NDF_ERR_ARG, "field too large");
+    if (ref_idx < 0 || ref_idx >= N) return fail(ctx, NDF_ERR_ARG, "ref_idx out of range");
+    if (mi_out) {
+        if (k < 1 || k >= M) return fail(ctx, NDF_ERR_ARG, "need 1 <= k < M (k=%d)", k);
+        if (k > kKsgMaxK) return fail(ctx, NDF_ERR_ARG, "k=%d above the supported %d", k, kKsgMaxK);
+        if (M > kKsgMaxM) return fail(ctx, NDF_ERR_ARG, "M=%lld above the supported %d", (long long)M, kKsgMaxM);
+    }
+    cudaSetDevice(ctx->device);
+    ndf_status st;
+    if (mi_out && (st = ensure_psi_table(ctx, M + 1)) != NDF_OK) return st;
+    Field f;
+    f.M = M; f.Z = Z; f.Y = Y; f.X = X; f.N = N;
+    const size_t bytes = sizeof(float) * (size_t)M * (size_t)N, vol = sizeof(float) * (size_t)N;
+    const bool want_sorted = mi_out && M <= kKsgMaxM;  // the KSG searches read it
+    cudaError_t e = ctx_alloc(ctx, (void**)&f.data, bytes);
+    if (e == cudaSuccess) e = ctx_alloc(ctx, (void**)&f.mean, sizeof(double) * (size_t)N);
+    if (e == cudaSuccess) e = ctx_alloc(ctx, (void**)&f.inv_norm, sizeof(double) * (size_t)N);
+    if (e == cudaSuccess && want_sorted) e = ctx_alloc(ctx, (void**)&f.sorted, bytes);
+    // outputs: device pointers as given, host ones staged in the context's scratch
+    float *dp = nullptr, *dm = nullptr;
+    const bool hp = pearson_out && pointer_kind(pearson_out) != PTR_DEVICE;
+    const bool hm = mi_out && pointer_kind(mi_out) != PTR_DEVICE;
+    if (e == cudaSuccess && (hp || hm)) e = ctx->out_tmp.reserve(2 * vol);
+    if (e != cudaSuccess) {
+        release_field(ctx, f);
+        return cuda_fail(ctx, e, "allocation");
+    }
+    if (pearson_out) dp = hp ? ctx->out_tmp.as<float>() : pearson_out;
+    if (mi_out) dm = hm ? ctx->out_tmp.as<float>() + N : mi_out;
+    const cudaMemcpyKind kind = pointer_kind(field) == PTR_DEVICE ? cudaMemcpyDeviceToDevice
+                                                                  : cudaMemcpyHostToDevice;
+    int* d_flag = ctx->flag.as<int>();
+    int64_t chunk = ((int64_t)(64 << 20) / M + 31) / 32 * 32;
+    if (chunk < 1024) chunk = 1024;
+    const int64_t nchunks = (N + chunk - 1) / chunk, cref = ref_idx / chunk;
+    e = cudaMemsetAsync(d_flag, 0, sizeof(int), ctx->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->copy_event, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->copy_stream, ctx->copy_event, 0);
+    for (int64_t q = 0; q < nchunks && e == cudaSuccess; ++q) {
+        const int64_t c = q == 0 ? cref : (q <= cref ? q - 1 : q);  // the reference's range first
+        const int64_t v0 = c * chunk, v1 = v0 + chunk < N ? v0 + chunk : N;
+        e = cudaMemcpy2DAsync(f.data + v0, sizeof(float) * (size_t)N, field + v0, sizeof(float) * (size_t)N,
+                              sizeof(float) * (size_t)(v1 - v0), (size_t)M, kind, ctx->copy_stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->copy_event, ctx->copy_stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->copy_event, 0);
+        if (e == cudaSuccess) e = launch_field_stats(ctx, f, v0, v1, d_flag);
+        if (e == cudaSuccess && want_sorted) e = launch_sort_columns(ctx, f, v0, v1, ctx->stream);
+        if (e == cudaSuccess && mi_out)
+            e = launch_ksg(ctx, f, f, nullptr, ref_idx, 1, k, v0, v1, dm + v0, 0,
+                           ctx->ksg_algorithm != NDF_KSG_BRUTE, 1, ctx->ksg_tile, nullptr, nullptr,
+                           nullptr, nullptr,
+                           ctx->count_evals ? ctx->evals.as<unsigned long long>() : nullptr);
+    }
+    if (e == cudaSuccess && pearson_out) e = launch_pearson(ctx, f, f, ref_idx, dp);
+    int nonfinite = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&nonfinite, d_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && hp) e = cudaMemcpyAsync(pearson_out, dp, vol, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && hm) e = cudaMemcpyAsync(mi_out, dm, vol, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess || nonfinite) {
+        cudaStreamSynchronize(ctx->copy_stream);
+        release_field(ctx, f);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "pipelined upload / volumes");
+        return fail(ctx, NDF_ERR_ARG, "field contains non-finite values");
+    }
+    if ((st = check_device_status(ctx)) != NDF_OK) {
+        release_field(ctx, f);
+        return st;
+    }
+    f.live = true;
+    ctx->fields.push_back(f);
+    *field_id_out = (int)ctx->fields.size() - 1;
+    return NDF_OK;
+}
+
 ndf_status ndf_free_ensemble(ndf_ctx* ctx, int field_id) {
     if (!ctx) return NDF_ERR_ARG;
     if (field_id < 0 || field_id >= (int)ctx->fields.size())

@@ -78,6 +78,8 @@ _sig("ndf_launch_count", ctypes.c_uint64, [_vp])
 _sig("ndf_index", _i64, [_i64, _i64, _i64, _i64, _i64, _i64])
 _sig("ndf_load_ensemble", ctypes.c_int, [_vp, _vp, _i64, _i64, _i64, _i64,
                                          ctypes.POINTER(ctypes.c_int)])
+_sig("ndf_load_and_compute", ctypes.c_int, [_vp, _vp, _i64, _i64, _i64, _i64, _i64, ctypes.c_int,
+                                            _vp, _vp, ctypes.POINTER(ctypes.c_int)])
 _sig("ndf_free_ensemble", ctypes.c_int, [_vp, ctypes.c_int])
 _sig("ndf_trim_cache", ctypes.c_int, [_vp])
 _sig("ndf_selftest_timeout", ctypes.c_int, [_vp])
@@ -234,6 +236,17 @@ def ndf_load_ensemble(ctx, field, M, Z, Y, X) -> int:
     fid = ctypes.c_int(-1)
     _check(ctx, _lib.ndf_load_ensemble(ctx, _addr(field), M, Z, Y, X, ctypes.byref(fid)),
            "ndf_load_ensemble")
+    return fid.value
+
+
+def ndf_load_and_compute(ctx, field, M, Z, Y, X, ref_idx: int, k: int, pearson_out=None,
+                         mi_out=None) -> int:
+    """Load + Pearson + KSG-MI of one reference, the upload pipelined with the search."""
+    fid = ctypes.c_int(-1)
+    _check(ctx, _lib.ndf_load_and_compute(ctx, _addr(field), M, Z, Y, X, ref_idx, k,
+                                          None if pearson_out is None else _addr(pearson_out),
+                                          None if mi_out is None else _addr(mi_out),
+                                          ctypes.byref(fid)), "ndf_load_and_compute")
     return fid.value
 
 

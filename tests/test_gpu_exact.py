@@ -396,3 +396,61 @@ def test_argument_errors(ndf_mod, ctx, tiny_field, tiny_ref):
     assert ei.value.status == ndf.NDF_ERR_STATE
     ndf.ndf_free_ensemble(ctx, fid)
     assert ndf.ndf_launch_count(ctx) > 0
+
+
+# ---------------------------------------------------------------- pipelined load + volumes
+def test_load_and_compute_matches_separate_calls(ndf_mod, ctx):
+    """The pipelined entry point runs the same kernels range by range (three ranges at
+    M = 2048, the reference's middle range first): bit-equal volumes, host and device
+    outputs, a skipped measure, and the field stays loaded."""
+    ndf = ndf_mod
+    shape = (2048, 17, 63, 64)  # 68,544 vertices: ranges of 32,768 + 32,768 + 3,008
+    f = rand_field(shape, 31)
+    f[:, :, :, ::2] = np.tanh(f[:, :, :, ::2] + 0.3 * f[:, :, :, 1::2])
+    f = np.ascontiguousarray(f)
+    M, Z, Y, X = shape
+    N = Z * Y * X
+    ref = 40000
+    fid = load(ndf, ctx, f)
+    p1 = np.empty(N, np.float32)
+    m1 = np.empty(N, np.float32)
+    ndf.ndf_pearson(ctx, fid, fid, ref, p1)
+    ndf.ndf_mi_ksg(ctx, fid, fid, ref, 8, m1)
+    ndf.ndf_free_ensemble(ctx, fid)
+    p2 = np.empty(N, np.float32)
+    m2 = torch.empty(N, dtype=torch.float32, device="cuda")
+    fid2 = ndf.ndf_load_and_compute(ctx, f, M, Z, Y, X, ref, 8, p2, m2)
+    ndf.ndf_synchronize(ctx)
+    np.testing.assert_array_equal(p2, p1)
+    np.testing.assert_array_equal(m2.cpu().numpy(), m1)
+    p3 = np.empty(N, np.float32)
+    ndf.ndf_pearson(ctx, fid2, fid2, ref, p3)  # the field stays loaded
+    np.testing.assert_array_equal(p3, p1)
+    # the x-strip search on the same loaded field agrees bit for bit
+    ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_PRUNED)
+    m3 = np.empty(N, np.float32)
+    ndf.ndf_mi_ksg(ctx, fid2, fid2, ref, 8, m3)
+    ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_BLOCK)
+    np.testing.assert_array_equal(m3, m1)
+    ndf.ndf_free_ensemble(ctx, fid2)
+    p4 = np.empty(N, np.float32)
+    fid3 = ndf.ndf_load_and_compute(ctx, f, M, Z, Y, X, ref, 8, p4, None)  # Pearson only
+    np.testing.assert_array_equal(p4, p1)
+    ndf.ndf_free_ensemble(ctx, fid3)
+
+
+def test_load_and_compute_rejects_bad_input(ndf_mod, ctx, tiny_field, tiny_ref):
+    ndf = ndf_mod
+    f = tiny_field.copy()
+    M, Z, Y, X = f.shape
+    out = np.empty(Z * Y * X, np.float32)
+    with pytest.raises(ndf.NdfError):
+        ndf.ndf_load_and_compute(ctx, f, M, Z, Y, X, Z * Y * X, 4, out, out)  # ref out of range
+    with pytest.raises(ndf.NdfError):
+        ndf.ndf_load_and_compute(ctx, f, M, Z, Y, X, tiny_ref, M, out, out)  # k >= M
+    f[3, 0, 0, 5] = np.nan
+    with pytest.raises(ndf.NdfError):
+        ndf.ndf_load_and_compute(ctx, f, M, Z, Y, X, tiny_ref, 4, out, out)
+    # the context stays usable
+    fid = ndf.ndf_load_and_compute(ctx, tiny_field, M, Z, Y, X, tiny_ref, 4, out, None)
+    ndf.ndf_free_ensemble(ctx, fid)
