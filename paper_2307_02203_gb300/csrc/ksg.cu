@@ -551,9 +551,13 @@ struct BlockCtl {
     unsigned long long item;
     double part[kGroupWarps];
 };
+// block b's 32 points sit at 1 + b * kBlkStride + p, between +inf separators at
+// b * kBlkStride (both scan directions stop on |y - y_i| = inf without bounds checks)
+constexpr int kBlkStride = kBlk + 1;
 __host__ __device__ inline size_t block_group_bytes(int M) {
     const int nb = (M + kBlk - 1) / kBlk;
-    return sizeof(BlockCtl) + sizeof(float2) * (size_t)nb * kBlk + 2 * sizeof(float) * (size_t)((M + 3) & ~3);
+    return sizeof(BlockCtl) + sizeof(float2) * ((size_t)nb * kBlkStride + 1) +
+           2 * sizeof(float) * (size_t)((M + 3) & ~3);
 }
 
 // warp-wide ascending bitonic sort of (key, val) pairs, one per lane; (key, val)
@@ -599,8 +603,8 @@ __global__ void __launch_bounds__(32 * kGroupWarps * kMaxGroupsPerCta, 1)
     const int nb = (M + kBlk - 1) / kBlk;
     unsigned char* gbase = smem + (size_t)group * block_group_bytes(M);
     BlockCtl* ctl = reinterpret_cast<BlockCtl*>(gbase);
-    float2* blk = reinterpret_cast<float2*>(gbase + sizeof(BlockCtl));  // [nb * 32] (y, x)
-    float* xs = reinterpret_cast<float*>(blk + (size_t)nb * kBlk);      // reference, x-sorted
+    float2* blk = reinterpret_cast<float2*>(gbase + sizeof(BlockCtl));  // (y, x), separated blocks
+    float* xs = reinterpret_cast<float*>(blk + (size_t)nb * kBlkStride + 1);  // reference, x-sorted
     float* ys = xs + ((M + 3) & ~3);                                     // query, sorted
     const int64_t N = A.N, nv = A.v_end - A.v_begin;
     const unsigned long long items =
@@ -623,13 +627,14 @@ __global__ void __launch_bounds__(32 * kGroupWarps * kMaxGroupsPerCta, 1)
             ys[s] = A.sorted[(int64_t)s * N + v];
         }
         // ---- blocks of 32 x-ranks, each sorted by y; pads (y = x = +inf) sort last
+        for (int b = gt; b <= nb; b += GT) blk[b * kBlkStride] = make_float2(INFINITY, INFINITY);
         for (int b = gw; b < nb; b += kGroupWarps) {
             const int rank = b * kBlk + lane;
             float key = INFINITY;
             int val = rank;
             if (rank < M) key = A.field[(int64_t)perm[rank] * N + v];
             warp_sort_kv(key, val);
-            blk[b * kBlk + lane] = make_float2(key, val < M ? xsg[val] : INFINITY);
+            blk[1 + b * kBlkStride + lane] = make_float2(key, val < M ? xsg[val] : INFINITY);
         }
         group_sync(group);
 
@@ -639,30 +644,34 @@ __global__ void __launch_bounds__(32 * kGroupWarps * kMaxGroupsPerCta, 1)
         unsigned long long my_evals = 0;
         for (int b = gw; b < nb; b += kGroupWarps) {
             const bool valid = b * kBlk + lane < M;
-            const float2 me = blk[b * kBlk + lane];
+            const float2 me = blk[1 + b * kBlkStride + lane];
             const float yi = me.x, xi = me.y;
             float best[KK];  // the k nearest others, ascending
 #pragma unroll
             for (int c = 0; c < KK; ++c) best[c] = FLT_MAX;
             // scan of block bb from positions up / dn outward while the y-gap is below
-            // the threshold (lanes with on == false take no candidate)
+            // the threshold; a lane with on == false starts on the separators
             auto scan = [&](int bb, int up, int dn, bool on) {
-                const float2* B = blk + bb * kBlk;
+                const float2* B = blk + 1 + bb * kBlkStride;
+                if (!on) {
+                    up = kBlk;
+                    dn = -1;
+                }
+                const int up0 = up, dn0 = dn;
                 for (;;) {
                     const float t = best[KK - 1];
-                    const float2 cu = B[up < kBlk ? up : kBlk - 1];
-                    const float2 cd = B[dn >= 0 ? dn : 0];
+                    const float2 cu = B[up], cd = B[dn];
                     const float dyu = cu.x - yi, dyd = yi - cd.x;
-                    const bool au = on && up < kBlk && dyu < t;
-                    const bool ad = on && dn >= 0 && dyd < t;
+                    const bool au = fabsf(dyu) < t;  // false on a separator (and for pads: NaN)
+                    const bool ad = fabsf(dyd) < t;
                     if (!__any_sync(0xffffffffu, au || ad)) break;
                     const float du = au ? fmaxf(fabsf(cu.y - xi), fabsf(dyu)) : FLT_MAX;
                     const float dd = ad ? fmaxf(fabsf(cd.y - xi), fabsf(dyd)) : FLT_MAX;
                     insert2<KK>(best, fminf(du, dd), fmaxf(du, dd));
-                    my_evals += (unsigned)au + (unsigned)ad;
                     up += au ? 1 : 0;
                     dn -= ad ? 1 : 0;
                 }
+                my_evals += (unsigned)((up - up0) + (dn0 - dn));
             };
             scan(b, lane + 1, lane - 1, valid);
             bool ron = valid, lon = valid;
@@ -671,13 +680,13 @@ __global__ void __launch_bounds__(32 * kGroupWarps * kMaxGroupsPerCta, 1)
                 if (br >= nb) ron = false;
                 else if (ron && xs[br * kBlk] - xi >= best[KK - 1]) ron = false;  // nearest x of the block
                 if (__any_sync(0xffffffffu, ron)) {
-                    const int pos = block_lower_bound(blk + br * kBlk, yi);
+                    const int pos = block_lower_bound(blk + 1 + br * kBlkStride, yi);
                     scan(br, pos, pos - 1, ron);
                 }
                 if (bleft < 0) lon = false;
                 else if (lon && xi - xs[min(bleft * kBlk + kBlk - 1, M - 1)] >= best[KK - 1]) lon = false;
                 if (__any_sync(0xffffffffu, lon)) {
-                    const int pos = block_lower_bound(blk + bleft * kBlk, yi);
+                    const int pos = block_lower_bound(blk + 1 + bleft * kBlkStride, yi);
                     scan(bleft, pos, pos - 1, lon);
                 }
                 if (!__any_sync(0xffffffffu, ron || lon)) break;
