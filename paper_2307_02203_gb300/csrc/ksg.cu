@@ -665,8 +665,11 @@ __global__ void __launch_bounds__(32 * kGroupWarps * kMaxGroupsPerCta, 1)
                     const bool au = fabsf(dyu) < t;  // false on a separator (and for pads: NaN)
                     const bool ad = fabsf(dyd) < t;
                     if (!__any_sync(0xffffffffu, au || ad)) break;
-                    const float du = au ? fmaxf(fabsf(cu.y - xi), fabsf(dyu)) : FLT_MAX;
-                    const float dd = ad ? fmaxf(fabsf(cd.y - xi), fabsf(dyd)) : FLT_MAX;
+                    // a candidate outside the window has |dy| >= t, so its distance is >= t
+                    // and leaves the list unchanged: no select needed (for a valid lane;
+                    // the padding lanes' lists are never read)
+                    const float du = fmaxf(fabsf(cu.y - xi), fabsf(dyu));
+                    const float dd = fmaxf(fabsf(cd.y - xi), fabsf(dyd));
                     insert2<KK>(best, fminf(du, dd), fmaxf(du, dd));
                     up += au ? 1 : 0;
                     dn -= ad ? 1 : 0;
