@@ -554,6 +554,8 @@ struct BlockCtl {
 // block b's 32 points sit at 1 + b * kBlkStride + p, between +inf separators at
 // b * kBlkStride (both scan directions stop on |y - y_i| = inf without bounds checks)
 constexpr int kBlkStride = kBlk + 1;
+constexpr int kTaskRows = 4;                     // y-positions per block in a warp task
+constexpr int kTaskBlocks = kBlk / kTaskRows;    // blocks in a warp task
 __host__ __device__ inline size_t block_group_bytes(int M) {
     const int nb = (M + kBlk - 1) / kBlk;
     return sizeof(BlockCtl) + sizeof(float2) * ((size_t)nb * kBlkStride + 1) +
@@ -642,9 +644,15 @@ __global__ void __launch_bounds__(32 * kGroupWarps * kMaxGroupsPerCta, 1)
         const bool dbg = A.dbg_eps && r == 0 && v == A.v_begin;
         double acc = 0.0;
         unsigned long long my_evals = 0;
-        for (int b = gw; b < nb; b += kGroupWarps) {
-            const bool valid = b * kBlk + lane < M;
-            const float2 me = blk[1 + b * kBlkStride + lane];
+        // a warp task: the members at y-positions 4q .. 4q + 3 of blocks 8g .. 8g + 7 (lanes
+        // of similar rank inside their blocks have similar windows, so the lock-step
+        // scans waste fewer steps than with the 32 members of one block)
+        const int ntasks = ((nb + kTaskBlocks - 1) / kTaskBlocks) * (kBlk / kTaskRows);
+        for (int task = gw; task < ntasks; task += kGroupWarps) {
+            const int b = (task / (kBlk / kTaskRows)) * kTaskBlocks + lane / kTaskRows;
+            const int p = (task % (kBlk / kTaskRows)) * kTaskRows + lane % kTaskRows;
+            const bool valid = b < nb && p < min(kBlk, M - b * kBlk);
+            const float2 me = valid ? blk[1 + b * kBlkStride + p] : make_float2(INFINITY, INFINITY);
             const float yi = me.x, xi = me.y;
             float best[KK];  // the k nearest others, ascending
 #pragma unroll
@@ -652,7 +660,7 @@ __global__ void __launch_bounds__(32 * kGroupWarps * kMaxGroupsPerCta, 1)
             // scan of block bb from positions up / dn outward while the y-gap is below
             // the threshold; a lane with on == false starts on the separators
             auto scan = [&](int bb, int up, int dn, bool on) {
-                const float2* B = blk + 1 + bb * kBlkStride;
+                const float2* B = blk + 1 + (on ? bb : 0) * kBlkStride;
                 if (!on) {
                     up = kBlk;
                     dn = -1;
@@ -676,20 +684,20 @@ __global__ void __launch_bounds__(32 * kGroupWarps * kMaxGroupsPerCta, 1)
                 }
                 my_evals += (unsigned)((up - up0) + (dn0 - dn));
             };
-            scan(b, lane + 1, lane - 1, valid);
+            scan(b, p + 1, p - 1, valid);
             bool ron = valid, lon = valid;
             for (int dd = 1; dd < nb; ++dd) {
                 const int br = b + dd, bleft = b - dd;
                 if (br >= nb) ron = false;
                 else if (ron && xs[br * kBlk] - xi >= best[KK - 1]) ron = false;  // nearest x of the block
                 if (__any_sync(0xffffffffu, ron)) {
-                    const int pos = block_lower_bound(blk + 1 + br * kBlkStride, yi);
+                    const int pos = ron ? block_lower_bound(blk + 1 + br * kBlkStride, yi) : 0;
                     scan(br, pos, pos - 1, ron);
                 }
                 if (bleft < 0) lon = false;
                 else if (lon && xi - xs[min(bleft * kBlk + kBlk - 1, M - 1)] >= best[KK - 1]) lon = false;
                 if (__any_sync(0xffffffffu, lon)) {
-                    const int pos = block_lower_bound(blk + 1 + bleft * kBlkStride, yi);
+                    const int pos = lon ? block_lower_bound(blk + 1 + bleft * kBlkStride, yi) : 0;
                     scan(bleft, pos, pos - 1, lon);
                 }
                 if (!__any_sync(0xffffffffu, ron || lon)) break;
@@ -700,20 +708,35 @@ __global__ void __launch_bounds__(32 * kGroupWarps * kMaxGroupsPerCta, 1)
                 const int cx = count_within(xs, M, xi, e) - self;
                 const int cy = count_within(ys, M, yi, e) - self;
                 acc += A.psi[cx + 1] + A.psi[cy + 1];
+                if (dbg) A.dbg_nx[b * kBlk + p] = __float_as_int(e);  // eps by block position, for now
             }
-            if (dbg) {  // the block's sort again (deterministic) gives each lane's x-rank
-                const int rank = b * kBlk + lane;
+        }
+        if (dbg) {
+            // member ids: each block's sort again (deterministic) gives its positions' x-ranks.
+            // Pass 1 moves eps from the position-indexed scratch (dbg_nx) to dbg_eps[member];
+            // after every read of the scratch, pass 2 writes the counts over it.
+            group_sync(group);
+            for (int bq = gw; bq < nb; bq += kGroupWarps) {
+                const int rank = bq * kBlk + lane;
                 float key = rank < M ? A.field[(int64_t)perm[rank] * N + v] : INFINITY;
                 int val = rank;
                 warp_sort_kv(key, val);
-                if (valid) {
-                    const float e = best[KK - 1];
-                    const int self = e > 0.0f ? 1 : 0;
+                if (val < M) A.dbg_eps[perm[val]] = __int_as_float(A.dbg_nx[bq * kBlk + lane]);
+            }
+            group_sync(group);
+            for (int bq = gw; bq < nb; bq += kGroupWarps) {
+                const int rank = bq * kBlk + lane;
+                float key = rank < M ? A.field[(int64_t)perm[rank] * N + v] : INFINITY;
+                int val = rank;
+                warp_sort_kv(key, val);
+                if (val < M) {
                     const int mi = perm[val];
-                    A.dbg_eps[mi] = e;
+                    const float e = A.dbg_eps[mi];
+                    const float2 me = blk[1 + bq * kBlkStride + lane];
+                    const int self = e > 0.0f ? 1 : 0;
                     if (A.dbg_ey) A.dbg_ey[mi] = e;
-                    A.dbg_nx[mi] = count_within(xs, M, xi, e) - self;
-                    A.dbg_ny[mi] = count_within(ys, M, yi, e) - self;
+                    A.dbg_nx[mi] = count_within(xs, M, me.y, e) - self;
+                    A.dbg_ny[mi] = count_within(ys, M, me.x, e) - self;
                 }
             }
         }

@@ -426,12 +426,13 @@ def test_load_and_compute_matches_separate_calls(ndf_mod, ctx):
     p3 = np.empty(N, np.float32)
     ndf.ndf_pearson(ctx, fid2, fid2, ref, p3)  # the field stays loaded
     np.testing.assert_array_equal(p3, p1)
-    # the x-strip search on the same loaded field agrees bit for bit
+    # the x-strip search on the same loaded field: the same eps and counts, its FP64
+    # digamma sum accumulated in another member order (MI within 1e-6 relative)
     ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_PRUNED)
     m3 = np.empty(N, np.float32)
     ndf.ndf_mi_ksg(ctx, fid2, fid2, ref, 8, m3)
     ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_BLOCK)
-    np.testing.assert_array_equal(m3, m1)
+    np.testing.assert_allclose(m3, m1, rtol=1e-6, atol=1e-9)
     ndf.ndf_free_ensemble(ctx, fid2)
     p4 = np.empty(N, np.float32)
     fid3 = ndf.ndf_load_and_compute(ctx, f, M, Z, Y, X, ref, 8, p4, None)  # Pearson only
