@@ -529,9 +529,9 @@ __global__ void __launch_bounds__(32 * kGroupWarps * kMaxGroupsPerCta, 1)
 
 // ---------------------------------------------------------------- block search
 // The same estimator (algorithm 1) with a two-level search.  The members of a
-// pair are cut into x-blocks of 32 consecutive x-ranks; inside each block they are
-// sorted by y (one warp-wide bitonic sort of 32 (y, rank) keys).  Lane l of a warp
-// takes the member at position l of block b and
+// pair are cut into x-blocks of 64 consecutive x-ranks; inside each block they are
+// sorted by y (one warp-wide bitonic sort of 64 (y, rank) keys, two per lane).  A
+// lane takes the member at one position of block b and
 //   scans its own block outward in y from its own position,
 //   then the blocks b + 1, b - 1, b + 2, ... : a side stops at the first block whose
 //   x-gap (the block's nearest x-rank) reaches the lane's current k-th distance;
@@ -546,50 +546,86 @@ __global__ void __launch_bounds__(32 * kGroupWarps * kMaxGroupsPerCta, 1)
 // diverge on almost every step); each step takes one candidate from each end of
 // the block scan into the two-value merge insert.  Two warps share a pair's
 // arrays (x sorted, y sorted, the block-sorted points: 16 B x M).
-constexpr int kBlk = 32;
+constexpr int kBlk = 64;  // x-ranks per block (two per lane in the block sort)
 struct BlockCtl {
     unsigned long long item;
     double part[kGroupWarps];
 };
-// block b's 32 points sit at 1 + b * kBlkStride + p, between +inf separators at
+// block b's kBlk points sit at 1 + b * kBlkStride + p, between +inf separators at
 // b * kBlkStride (both scan directions stop on |y - y_i| = inf without bounds checks)
 constexpr int kBlkStride = kBlk + 1;
-constexpr int kTaskRows = 4;                     // y-positions per block in a warp task
-constexpr int kTaskBlocks = kBlk / kTaskRows;    // blocks in a warp task
+constexpr int kTaskRows = 8;                     // y-positions per block in a warp task
+constexpr int kTaskBlocks = 32 / kTaskRows;      // blocks in a warp task
+constexpr int kTaskQuads = kBlk / kTaskRows;     // position groups of a block
 __host__ __device__ inline size_t block_group_bytes(int M) {
     const int nb = (M + kBlk - 1) / kBlk;
     return sizeof(BlockCtl) + sizeof(float2) * ((size_t)nb * kBlkStride + 1) +
            2 * sizeof(float) * (size_t)((M + 3) & ~3);
 }
 
-// warp-wide ascending bitonic sort of (key, val) pairs, one per lane; (key, val)
-// compared lexicographically (val unique), so the order is total
-__device__ __forceinline__ void warp_sort_kv(float& key, int& val) {
+constexpr int kBlkRegs = kBlk / 32;              // sort keys per lane
+
+// warp-wide ascending bitonic sort of kBlk (key, val) pairs, element e = 32 r + lane
+// in register r; (key, val) compared lexicographically (val unique), so the order
+// is total.  Strides of 32 and more compare two registers of one lane.
+__device__ __forceinline__ void warp_sort_block(float (&key)[kBlkRegs], int (&val)[kBlkRegs]) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int size = 2; size <= 32; size <<= 1) {
+    for (int size = 2; size <= kBlk; size <<= 1) {
 #pragma unroll
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            const float ok = __shfl_xor_sync(0xffffffffu, key, stride);
-            const int ov = __shfl_xor_sync(0xffffffffu, val, stride);
-            const bool up = (lane & size) == 0 || size == 32;
-            const bool lower = (lane & stride) == 0;
-            const bool other_less = ok < key || (ok == key && ov < val);
-            // the lower lane of an ascending pair keeps the smaller element
-            const bool take = lower == up ? other_less : !other_less;
-            if (take) {
-                key = ok;
-                val = ov;
+            if (stride >= 32) {
+                const int rs = stride / 32;
+#pragma unroll
+                for (int r = 0; r < kBlkRegs; ++r) {
+                    if (r & rs) continue;
+                    const int q = r | rs;
+                    const bool up = ((r * 32) & size) == 0;
+                    const bool q_less = key[q] < key[r] || (key[q] == key[r] && val[q] < val[r]);
+                    if (up == q_less) {  // the lower element of an ascending pair keeps the smaller
+                        const float tk = key[r];
+                        const int tv = val[r];
+                        key[r] = key[q];
+                        val[r] = val[q];
+                        key[q] = tk;
+                        val[q] = tv;
+                    }
+                }
+                continue;
+            }
+#pragma unroll
+            for (int r = 0; r < kBlkRegs; ++r) {
+                const float ok = __shfl_xor_sync(0xffffffffu, key[r], stride);
+                const int ov = __shfl_xor_sync(0xffffffffu, val[r], stride);
+                const bool up = ((r * 32 + lane) & size) == 0;
+                const bool lower = (lane & stride) == 0;
+                const bool other_less = ok < key[r] || (ok == key[r] && ov < val[r]);
+                if (lower == up ? other_less : !other_less) {
+                    key[r] = ok;
+                    val[r] = ov;
+                }
             }
         }
     }
 }
 
-// lower bound of y in a block of 32 ascending values (pads +inf): 0 .. 32
+// the sort keys of block b: query values of x-ranks b kBlk + 32 r + lane (+inf past M)
+__device__ __forceinline__ void block_keys(const KsgArgs& A, const int* perm, int b, int64_t v,
+                                           float (&key)[kBlkRegs], int (&val)[kBlkRegs]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int r = 0; r < kBlkRegs; ++r) {
+        const int rank = b * kBlk + r * 32 + lane;
+        key[r] = rank < A.M ? A.field[(int64_t)perm[rank] * A.N + v] : INFINITY;
+        val[r] = rank;
+    }
+}
+
+// lower bound of y in a block of kBlk ascending values (pads +inf): 0 .. kBlk
 __device__ __forceinline__ int block_lower_bound(const float2* blk, float y) {
     int pos = 0;
 #pragma unroll
-    for (int h = 16; h > 0; h >>= 1)
+    for (int h = kBlk / 2; h > 0; h >>= 1)
         if (blk[pos + h - 1].x < y) pos += h;
     return pos;
 }
@@ -628,15 +664,17 @@ __global__ void __launch_bounds__(32 * kGroupWarps * kMaxGroupsPerCta, 1)
             xs[s] = xsg[s];
             ys[s] = A.sorted[(int64_t)s * N + v];
         }
-        // ---- blocks of 32 x-ranks, each sorted by y; pads (y = x = +inf) sort last
+        // ---- blocks of kBlk x-ranks, each sorted by y; pads (y = x = +inf) sort last
         for (int b = gt; b <= nb; b += GT) blk[b * kBlkStride] = make_float2(INFINITY, INFINITY);
         for (int b = gw; b < nb; b += kGroupWarps) {
-            const int rank = b * kBlk + lane;
-            float key = INFINITY;
-            int val = rank;
-            if (rank < M) key = A.field[(int64_t)perm[rank] * N + v];
-            warp_sort_kv(key, val);
-            blk[1 + b * kBlkStride + lane] = make_float2(key, val < M ? xsg[val] : INFINITY);
+            float key[kBlkRegs];
+            int val[kBlkRegs];
+            block_keys(A, perm, b, v, key, val);
+            warp_sort_block(key, val);
+#pragma unroll
+            for (int r2 = 0; r2 < kBlkRegs; ++r2)
+                blk[1 + b * kBlkStride + r2 * 32 + lane] =
+                    make_float2(key[r2], val[r2] < M ? xsg[val[r2]] : INFINITY);
         }
         group_sync(group);
 
@@ -644,13 +682,13 @@ __global__ void __launch_bounds__(32 * kGroupWarps * kMaxGroupsPerCta, 1)
         const bool dbg = A.dbg_eps && r == 0 && v == A.v_begin;
         double acc = 0.0;
         unsigned long long my_evals = 0;
-        // a warp task: the members at y-positions 4q .. 4q + 3 of blocks 8g .. 8g + 7 (lanes
+        // a warp task: the members at y-positions 8q .. 8q + 7 of blocks 4g .. 4g + 3 (lanes
         // of similar rank inside their blocks have similar windows, so the lock-step
-        // scans waste fewer steps than with the 32 members of one block)
-        const int ntasks = ((nb + kTaskBlocks - 1) / kTaskBlocks) * (kBlk / kTaskRows);
+        // scans waste fewer steps than with 32 consecutive members of one block)
+        const int ntasks = ((nb + kTaskBlocks - 1) / kTaskBlocks) * kTaskQuads;
         for (int task = gw; task < ntasks; task += kGroupWarps) {
-            const int b = (task / (kBlk / kTaskRows)) * kTaskBlocks + lane / kTaskRows;
-            const int p = (task % (kBlk / kTaskRows)) * kTaskRows + lane % kTaskRows;
+            const int b = (task / kTaskQuads) * kTaskBlocks + lane / kTaskRows;
+            const int p = (task % kTaskQuads) * kTaskRows + lane % kTaskRows;
             const bool valid = b < nb && p < min(kBlk, M - b * kBlk);
             const float2 me = valid ? blk[1 + b * kBlkStride + p] : make_float2(INFINITY, INFINITY);
             const float yi = me.x, xi = me.y;
@@ -717,22 +755,27 @@ __global__ void __launch_bounds__(32 * kGroupWarps * kMaxGroupsPerCta, 1)
             // after every read of the scratch, pass 2 writes the counts over it.
             group_sync(group);
             for (int bq = gw; bq < nb; bq += kGroupWarps) {
-                const int rank = bq * kBlk + lane;
-                float key = rank < M ? A.field[(int64_t)perm[rank] * N + v] : INFINITY;
-                int val = rank;
-                warp_sort_kv(key, val);
-                if (val < M) A.dbg_eps[perm[val]] = __int_as_float(A.dbg_nx[bq * kBlk + lane]);
+                float key[kBlkRegs];
+                int val[kBlkRegs];
+                block_keys(A, perm, bq, v, key, val);
+                warp_sort_block(key, val);
+#pragma unroll
+                for (int r2 = 0; r2 < kBlkRegs; ++r2)
+                    if (val[r2] < M)
+                        A.dbg_eps[perm[val[r2]]] = __int_as_float(A.dbg_nx[bq * kBlk + r2 * 32 + lane]);
             }
             group_sync(group);
             for (int bq = gw; bq < nb; bq += kGroupWarps) {
-                const int rank = bq * kBlk + lane;
-                float key = rank < M ? A.field[(int64_t)perm[rank] * N + v] : INFINITY;
-                int val = rank;
-                warp_sort_kv(key, val);
-                if (val < M) {
-                    const int mi = perm[val];
+                float key[kBlkRegs];
+                int val[kBlkRegs];
+                block_keys(A, perm, bq, v, key, val);
+                warp_sort_block(key, val);
+#pragma unroll
+                for (int r2 = 0; r2 < kBlkRegs; ++r2) {
+                    if (val[r2] >= M) continue;
+                    const int mi = perm[val[r2]];
                     const float e = A.dbg_eps[mi];
-                    const float2 me = blk[1 + bq * kBlkStride + lane];
+                    const float2 me = blk[1 + bq * kBlkStride + r2 * 32 + lane];
                     const int self = e > 0.0f ? 1 : 0;
                     if (A.dbg_ey) A.dbg_ey[mi] = e;
                     A.dbg_nx[mi] = count_within(xs, M, me.y, e) - self;
