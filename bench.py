@@ -38,7 +38,7 @@ K_NN = 8
 # query column and its sorted copy once (algorithmic 14.08 GB + 7 MB output).
 KSG_PRUNED_TRAFFIC_PER_VOLUME = (705.641e6 + 4.142e6) * 20
 KSG_BRUTE_TRAFFIC_PER_VOLUME = (705.845e6 + 4.089e6) * 20
-KSG_BLOCK_TRAFFIC_PER_VOLUME = (706.840e6 + 4.282e6) * 20
+KSG_BLOCK_TRAFFIC_PER_VOLUME = (704.332e6 + 4.026e6) * 20
 KSG_SEARCHES = {  # name: (ndf constant name, kernel at k = 8, DRAM bytes per volume)
     "pruned": ("NDF_KSG_PRUNED", "ksg_pruned_kernel<9>", KSG_PRUNED_TRAFFIC_PER_VOLUME),
     "block": ("NDF_KSG_BLOCK", "ksg_block_kernel<9>", KSG_BLOCK_TRAFFIC_PER_VOLUME),
