@@ -183,7 +183,7 @@ ndf_status ndf_mi_ksg2(ndf_ctx* ctx, int ref_field, int query_field, int64_t ref
  *                   order of the reference value, each side of a member's
  *                   outward scan stopped at the first x-gap that reaches its
  *                   current k-th distance (exact pruning);
- *   NDF_KSG_BLOCK   (default) two warps per pair; members cut into blocks of 32 x-ranks,
+ *   NDF_KSG_BLOCK   (default) two warps per pair; members cut into blocks of 64 x-ranks,
  *                   sorted by the query value inside each block; a member scans
  *                   blocks outward in x and, inside a block, outward in y, both
  *                   stopped by its current k-th distance (exact pruning).
