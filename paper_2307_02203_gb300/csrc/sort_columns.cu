@@ -4,12 +4,17 @@
 // upload, vertex range by vertex range) instead of once per (reference, vertex)
 // pair.
 //
-// Columns of up to 1024 members: one warp per column, the column in registers
-// (R = 32..1024 / 32 values per lane, padded with FLT_MAX), lane-major element
-// order e = lane * R + r, sorted by the bitonic network in its "mirror" form
-// (each merge of size kk first compares e with e ^ (kk - 1), then half-cleaners
-// e ^ j, the lower index always keeping the minimum, so no direction flags):
-// distances below R are register pairs, larger ones a shuffle with lane ^ (d/R).
+// Columns of up to 1024 members: a CTA per tile of kSortTile consecutive
+// vertices.  The tile's rows (kSortTile floats of one member, contiguous in the
+// field) are read and written whole, through shared memory; there each column is
+// stored with one skip every 32 elements and an odd column stride, so that the
+// row accesses and the warps' column accesses are free of bank conflicts.  A warp
+// sorts one column at a time in registers (R = 1024 / 32 values per lane at most,
+// padded with +inf), lane-major element order e = lane * R + r, by the bitonic
+// network in its "mirror" form (each merge of size kk first compares e with
+// e ^ (kk - 1), then half-cleaners e ^ j, the lower index always keeping the
+// minimum, so no direction flags): distances below R are register pairs, larger
+// ones a shuffle with lane ^ (d/R).
 // Larger columns: a CTA per group of columns, the same network in shared memory.
 #include <float.h>
 
@@ -17,20 +22,18 @@
 
 namespace ndf {
 
+constexpr int kSortTile = 16;     // vertices per CTA
+constexpr int kSortThreads = 256;
+
+// shared-memory floats of one column: 32 R elements with a skip after every 32,
+// rounded up to an odd count
+__host__ __device__ constexpr int sort_col_stride(int R) { return 33 * R + 1 - (R & 1); }
+__device__ __forceinline__ int sort_col_slot(int e) { return e + (e >> 5); }
+
+// the network on a warp's column in registers (element e = lane * R + r)
 template <int R>
-__global__ void __launch_bounds__(256) sort_columns_reg_kernel(const float* __restrict__ field,
-                                                                int M, int64_t N, int64_t v_begin,
-                                                                int64_t v_end,
-                                                                float* __restrict__ sorted) {
+__device__ __forceinline__ void sort_warp_column(float (&a)[R]) {
     const int lane = threadIdx.x & 31;
-    const int64_t v = v_begin + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (v >= v_end) return;  // whole warps leave together
-    float a[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int m = r * 32 + lane;  // any member may go to any slot before sorting
-        a[r] = m < M ? __ldcs(field + (int64_t)m * N + v) : FLT_MAX;
-    }
     auto cmpx = [&](float& lo, float& hi) {
         const float x = fminf(lo, hi), y = fmaxf(lo, hi);
         lo = x;
@@ -70,11 +73,59 @@ __global__ void __launch_bounds__(256) sort_columns_reg_kernel(const float* __re
             }
         }
     }
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int e = lane * R + r;
-        if (e < M) __stcs(sorted + (int64_t)e * N + v, a[r]);
+}
+
+template <int R>
+__global__ void __launch_bounds__(kSortThreads, 3) sort_columns_tile_kernel(const float* __restrict__ field,
+                                                                         int M, int64_t N,
+                                                                         int64_t v_begin, int64_t v_end,
+                                                                         float* __restrict__ sorted) {
+    constexpr int S = sort_col_stride(R);
+    extern __shared__ float tile[];  // [kSortTile][S]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t v0 = v_begin + (int64_t)blockIdx.x * kSortTile;
+    const int vc = v_end - v0 < kSortTile ? (int)(v_end - v0) : kSortTile;
+    // rows in: thread t takes member t / kSortTile, vertex t % kSortTile
+#pragma unroll 8
+    for (int idx = threadIdx.x; idx < M * kSortTile; idx += kSortThreads) {
+        const int m = idx / kSortTile, p = idx - m * kSortTile;
+        if (p < vc) tile[p * S + sort_col_slot(m)] = __ldcs(field + (int64_t)m * N + v0 + p);
     }
+    __syncthreads();
+    for (int p = warp; p < vc; p += kSortThreads / 32) {
+        float* col = tile + p * S;
+        float a[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int e = r * 32 + lane;  // any member may go to any slot before sorting
+            a[r] = e < M ? col[sort_col_slot(e)] : INFINITY;
+        }
+        sort_warp_column<R>(a);
+        __syncwarp();  // every lane has read the column before it is overwritten
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int e = lane * R + r;
+            if (e < M) col[sort_col_slot(e)] = a[r];
+        }
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int idx = threadIdx.x; idx < M * kSortTile; idx += kSortThreads) {
+        const int m = idx / kSortTile, p = idx - m * kSortTile;
+        if (p < vc) __stcs(sorted + (int64_t)m * N + v0 + p, tile[p * S + sort_col_slot(m)]);
+    }
+}
+
+template <int R>
+static cudaError_t launch_sort_tile(const Field& f, int64_t v_begin, int64_t v_end, cudaStream_t stream) {
+    const size_t smem = sizeof(float) * (size_t)kSortTile * sort_col_stride(R);
+    const cudaError_t attr = cudaFuncSetAttribute(
+        sort_columns_tile_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (attr != cudaSuccess) return attr;
+    const int64_t blocks = (v_end - v_begin + kSortTile - 1) / kSortTile;
+    sort_columns_tile_kernel<R><<<(unsigned)blocks, kSortThreads, smem, stream>>>(f.data, (int)f.M, f.N, v_begin,
+                                                                                 v_end, f.sorted);
+    return cudaGetLastError();
 }
 
 __global__ void __launch_bounds__(256)
@@ -117,13 +168,14 @@ cudaError_t launch_sort_columns(ndf_ctx* ctx, const Field& f, int64_t v_begin, i
     const int64_t nv = v_end - v_begin;
     if (nv <= 0) return cudaSuccess;
     if (M <= 1024) {
-        const unsigned blocks = (unsigned)((nv + 7) / 8);
-        if (M <= 32) sort_columns_reg_kernel<1><<<blocks, 256, 0, stream>>>(f.data, M, f.N, v_begin, v_end, f.sorted);
-        else if (M <= 64) sort_columns_reg_kernel<2><<<blocks, 256, 0, stream>>>(f.data, M, f.N, v_begin, v_end, f.sorted);
-        else if (M <= 128) sort_columns_reg_kernel<4><<<blocks, 256, 0, stream>>>(f.data, M, f.N, v_begin, v_end, f.sorted);
-        else if (M <= 256) sort_columns_reg_kernel<8><<<blocks, 256, 0, stream>>>(f.data, M, f.N, v_begin, v_end, f.sorted);
-        else if (M <= 512) sort_columns_reg_kernel<16><<<blocks, 256, 0, stream>>>(f.data, M, f.N, v_begin, v_end, f.sorted);
-        else sort_columns_reg_kernel<32><<<blocks, 256, 0, stream>>>(f.data, M, f.N, v_begin, v_end, f.sorted);
+        cudaError_t e;
+        if (M <= 32) e = launch_sort_tile<1>(f, v_begin, v_end, stream);
+        else if (M <= 64) e = launch_sort_tile<2>(f, v_begin, v_end, stream);
+        else if (M <= 128) e = launch_sort_tile<4>(f, v_begin, v_end, stream);
+        else if (M <= 256) e = launch_sort_tile<8>(f, v_begin, v_end, stream);
+        else if (M <= 512) e = launch_sort_tile<16>(f, v_begin, v_end, stream);
+        else e = launch_sort_tile<32>(f, v_begin, v_end, stream);
+        if (e != cudaSuccess) return e;
     } else {
         int n2 = 1;
         while (n2 < M) n2 <<= 1;
