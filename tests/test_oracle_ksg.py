@@ -159,6 +159,25 @@ def test_volume_matches_pairs(tiny_field, tiny_ref):
     assert vol[2] == pytest.approx(psi_exact(M) - psi_exact(4), abs=1e-9)
 
 
+def test_volumes_take_reference_from_ref_field():
+    """Cross-field volumes (the A -> B case): the reference column comes from the
+    first field and every query column from the second, vertex by vertex, for
+    both estimators (a swapped pair of fields gives other columns and fails)."""
+    rng = np.random.default_rng(31)
+    M, N, r = 200, 12, 5
+    a = rng.normal(size=(M, 1, 1, N)).astype(np.float32)
+    b = (np.tanh(a[:, :, :, ::-1]) + 0.4 * rng.normal(size=(M, 1, 1, N))).astype(np.float32)
+    a2, b2 = a.reshape(M, N), b.reshape(M, N)
+    verts = list(range(N))
+    v1 = oracle.ksg_volume(a, b, r, 4, verts=verts)
+    v2 = oracle.ksg2_volume(a, b, r, 4, verts=verts)
+    for v in verts:
+        assert v1[v] == oracle.ksg_pair(a2[:, r], b2[:, v], 4)[0]
+        assert v2[v] == oracle.ksg2_pair(a2[:, r], b2[:, v], 4)[0]
+    swapped = oracle.ksg_volume(b, a, r, 4, verts=verts)
+    assert np.abs(swapped - v1).max() > 1e-3
+
+
 # ---------------------------------------------------------------- algorithm 2
 @pytest.mark.parametrize("case", ksg2_hand_cases(), ids=lambda c: "alg2_" + c["name"])
 def test_alg2_hand_enumerated(case):
@@ -213,3 +232,23 @@ def test_alg2_gaussian_theory():
         y = (rho * z[0] + np.sqrt(1 - rho ** 2) * z[1]).astype(np.float32)
         vals.append(oracle.ksg2_pair(x, y, 4)[0])
     assert np.mean(vals) == pytest.approx(-0.5 * np.log(1 - rho ** 2), abs=0.04)
+
+
+def test_alg2_volume_matches_pairs(tiny_field, tiny_ref):
+    M = tiny_field.shape[0]
+    f2 = tiny_field.reshape(M, -1)
+    verts = [0, 3, tiny_ref, 700, 1023]
+    vol = oracle.ksg2_volume(tiny_field, tiny_field, tiny_ref, 4, verts=verts)
+    for i, v in enumerate(verts):
+        assert vol[i] == oracle.ksg2_pair(f2[:, tiny_ref], f2[:, v], 4)[0]
+    # the self pair: psi(M) - psi(k) - 1/k when the k-th and (k+1)-th nearest
+    # |dx| of every member differ
+    x = f2[:, tiny_ref].astype(np.float64)
+    for i in range(M):
+        d = np.sort(np.abs(np.float32(x[i]) - np.delete(f2[:, tiny_ref], i)))
+        assert d[3] != d[4]
+    assert vol[2] == pytest.approx(psi_exact(M) - psi_exact(4) - 0.25, abs=1e-9)
+    # the whole volume equals the listed vertices where they overlap
+    full = oracle.ksg2_volume(tiny_field, tiny_field, tiny_ref, 4)
+    np.testing.assert_array_equal(full[verts], vol)
+
