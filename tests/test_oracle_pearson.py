@@ -56,3 +56,18 @@ def test_volume_matches_pairs(tiny_field, tiny_ref):
 def test_volume_rejects_bad_ref(tiny_field):
     with pytest.raises(ValueError):
         oracle.pearson_volume(tiny_field, tiny_field, 10**6)
+
+
+def test_volume_cross_field_reference_from_first_field():
+    """A -> B volumes: r(A[:, ref], B[:, v]) against numpy's corrcoef; the
+    swapped call reads other columns and differs."""
+    rng = np.random.default_rng(41)
+    M, N, ref = 300, 20, 7
+    a = rng.normal(size=(M, 1, 2, N // 2)).astype(np.float32)
+    b = (0.7 * a[:, :, ::-1] + 0.5 * rng.normal(size=a.shape)).astype(np.float32)
+    a2, b2 = a.reshape(M, N), b.reshape(M, N)
+    vol = oracle.pearson_volume(a, b, ref)
+    for v in range(N):
+        want = np.corrcoef(a2[:, ref].astype(np.float64), b2[:, v].astype(np.float64))[0, 1]
+        assert vol[v] == pytest.approx(want, abs=1e-12)
+    assert np.abs(oracle.pearson_volume(b, a, ref) - vol).max() > 1e-2
