@@ -112,6 +112,36 @@ def test_dense_level_reads_its_vertex_entry():
         assert oracle.hash_forward(s, p, pos, pos)[0] == pytest.approx(want, rel=1e-12)
 
 
+def test_hashed_level_reads_one_entry_per_vertex():
+    # level 2 (R = 8, 512 vertices) over a 64-entry table is hashed.  With entry =
+    # index, a vertex must read exactly one entry (trilinear weight 1), and along
+    # x the index must change as index(0, y, z) XOR x: the x coordinate enters the
+    # spatial hash with multiplier 1 and the coordinates combine by XOR, so the 8
+    # vertices of an x-row fill one aligned block of 8 entries (an additive
+    # combination, or another x multiplier, breaks this)
+    s = shape(width=1, n_freq=0, act=2, enc_layers=1, dec_layers=1, log2_table=6, measure=1)
+    p = np.zeros(oracle.hash_param_count(s))
+    off2 = 8 * 2 + 64 * 2
+    p[off2:off2 + 64 * 2:2] = np.arange(64)   # feature 0 of level 2
+    tables = sum(min(2 ** 6, (2 << l) ** 3) * 2 for l in range(3))
+    p[tables + 3 + 2 * 2] = 1.0                # encoder picks level 2, feature 0
+    p[tables + 3 + 3 * 2 + 1 + 0] = 1.0        # decoder weight
+    g = np.arange(8)
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    pos = np.stack([-1 + 2 * X / 7, -1 + 2 * Y / 7, -1 + 2 * Z / 7], axis=-1).reshape(-1, 3)
+    out = oracle.hash_forward(s, p, pos, pos)
+    cand = np.arange(64, dtype=np.float64) ** 2
+    cand = np.log1p(np.exp(-cand)) + cand      # softplus(entry^2), as for the dense level
+    diff = np.abs(out[:, None] - cand[None, :])
+    e = diff.argmin(axis=1)
+    assert (diff[np.arange(len(e)), e] <= 1e-9 * cand[e]).all()
+    e = e.reshape(8, 8, 8)
+    for y in range(8):
+        for z in range(8):
+            np.testing.assert_array_equal(e[:, y, z] ^ e[0, y, z], g)
+    assert len(np.unique(e)) > 32  # the hash spreads the 512 vertices over the table
+
+
 @pytest.mark.parametrize("merge,enc_layers", [(1, 2), (2, 2), (3, 2), (0, 0), (3, 0)])
 def test_ablations_gradient_vs_central_differences(merge, enc_layers):
     # merge: 1 sum, 2 |difference|, 3 concatenation; enc_layers = 0: grid only
