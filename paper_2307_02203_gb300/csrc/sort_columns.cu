@@ -8,7 +8,8 @@
 // vertices.  The tile's rows (kSortTile floats of one member, contiguous in the
 // field) are read and written whole, through shared memory; there each column is
 // stored with one skip every 32 elements and an odd column stride, so that the
-// row accesses and the warps' column accesses are free of bank conflicts.  A warp
+// warps' column accesses are free of bank conflicts and the row accesses (two
+// rows of 16 per warp instruction) at most 2-way conflicted.  A warp
 // sorts one column at a time in registers (R = 1024 / 32 values per lane at most,
 // padded with +inf), lane-major element order e = lane * R + r, by the bitonic
 // network in its "mirror" form (each merge of size kk first compares e with
