@@ -137,6 +137,18 @@ ndf_status ndf_field_stats(ndf_ctx* ctx, int field_id, double* mean_out, double*
 
 /* ---- exact estimators ---------------------------------------------------- */
 
+/* Errors of every volume call in this section (and of the debug hooks):
+ *   NDF_ERR_ARG     a field id that was never issued, fields of different
+ *                   shape, a reference (or query) index outside [0, N), a null
+ *                   output, R < 1 or a null index list (batches), an unknown
+ *                   precision; for KSG also k outside [1, M), k > 16 or M > 4096;
+ *   NDF_ERR_STATE   a field that has been freed;
+ *   NDF_ERR_OOM     scratch or output staging could not be allocated;
+ *   NDF_ERR_CUDA    a launch or copy failed;
+ *   NDF_ERR_TIMEOUT a bounded device wait gave up (reported by the next host
+ *                   check: a call with host outputs, or ndf_synchronize).
+ * Argument errors leave the outputs untouched. */
+
 /* Pearson volume (Sec. 3.1, Eq. 1): out[v] = r(e^ref(p_ref), e^query(v)) for
  * all N vertices v of the query field, FP32, clamped to [-1, 1]; 0 where
  * either sample has zero variance.  ref_field may equal query_field (the
@@ -230,6 +242,15 @@ ndf_status ndf_ksg2_debug_pair(ndf_ctx* ctx, int ref_field, int query_field, int
                                int32_t* ny, double* mi);
 
 /* ---- neural dependence field (Sec. 4) ------------------------------------ */
+
+/* Errors of the model calls in this section and the next: NDF_ERR_ARG for a
+ * null model or pointer, B < 1 or R < 1, a reference index outside [0, N), an
+ * unknown measure, decode mode or merge, grid dimensions or a training
+ * configuration out of range, or k / M outside the KSG limits for MI targets;
+ * NDF_ERR_STATE for a freed field; NDF_ERR_OOM / NDF_ERR_CUDA for failed
+ * allocations, cuBLAS set-up, launches or copies; NDF_ERR_IO for model files
+ * that cannot be opened, written, or are not (complete) model files of the
+ * same parameter count. */
 
 typedef struct ndf_model ndf_model; /* opaque; owned by the caller, freed by ndf_model_free */
 
@@ -431,6 +452,12 @@ ndf_status ndf_hash_set_decode(ndf_hash_model* m, int32_t mode, int32_t cache_qu
 int32_t ndf_hash_get_decode(const ndf_hash_model* m); /* the mode, -1 for NULL */
 
 /* ---- headless volume rendering (Sec. 5, Sec. 6.5) -------------------------- */
+
+/* Errors: NDF_ERR_ARG for a null volume, configuration or image, a volume with
+ * an axis of fewer than 2 vertices or more than 2^31 vertices in all, a bad
+ * image size or render
+ * configuration, an eye at the target, or an up vector parallel to the view
+ * direction; NDF_ERR_OOM / NDF_ERR_CUDA as above. */
 
 /* Direct volume rendering with a transfer function, or an iso-surface. */
 typedef enum { NDF_RENDER_DVR = 0, NDF_RENDER_ISO = 1 } ndf_render_mode;
