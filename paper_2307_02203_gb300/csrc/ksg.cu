@@ -746,7 +746,8 @@ __global__ void __launch_bounds__(32 * kGroupWarps * kMaxGroupsPerCta, 1)
                 const int cx = count_within(xs, M, xi, e) - self;
                 const int cy = count_within(ys, M, yi, e) - self;
                 acc += A.psi[cx + 1] + A.psi[cy + 1];
-                if (dbg) A.dbg_nx[b * kBlk + p] = __float_as_int(e);  // eps by block position, for now
+                // debug pair: eps by block position (scratch), put in member order below
+                if (dbg) A.dbg_nx[b * kBlk + p] = __float_as_int(e);
             }
         }
         if (dbg) {
