@@ -196,12 +196,18 @@ cudaError_t launch_sort_columns(ndf_ctx* ctx, const Field& f, int64_t v_begin, i
 
 cudaError_t ensure_sorted_columns(ndf_ctx* ctx, Field& f) {
     if (f.sorted) return cudaSuccess;
-    cudaError_t e = cudaMalloc(&f.sorted, sizeof(float) * (size_t)f.M * (size_t)f.N);
+    const size_t bytes = sizeof(float) * (size_t)f.M * (size_t)f.N;
+    cudaError_t e = cudaMalloc(&f.sorted, bytes);
     if (e != cudaSuccess) {
         f.sorted = nullptr;
         return e;
     }
-    return launch_sort_columns(ctx, f, 0, f.N, ctx->stream);
+    e = launch_sort_columns(ctx, f, 0, f.N, ctx->stream);
+    if (e != cudaSuccess) {  // not sorted: a later call must not take it for sorted
+        ctx_release(ctx, f.sorted, bytes);
+        f.sorted = nullptr;
+    }
+    return e;
 }
 
 }  // namespace ndf
