@@ -65,3 +65,39 @@ def test_null_context_is_rejected(lib):
 
     assert lib.ndf_synchronize(None) == ndf.NDF_ERR_ARG
     assert lib.ndf_launch_count(None) == 0
+
+
+def _handle_calls():
+    """(name, first parameter) of every ndf_status call on a context or model."""
+    src = open(os.path.join(ROOT, "include", "ndf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = []
+    for name, params in re.findall(r"\bndf_status\s+(ndf_\w+)\s*\(([^)]*)\)", src):
+        first = params.split(",")[0]
+        if re.search(r"\b(ndf_ctx|ndf_model|ndf_hash_model)\s*\*", first):
+            out.append(name)
+    return out
+
+
+def test_null_handles_are_rejected(lib):
+    """Every call on a context or model returns NDF_ERR_ARG for a NULL handle
+    (checked on the host before anything else), whatever the other arguments."""
+    from paper_2307_02203_gb300 import ndf
+
+    names = _handle_calls()
+    assert len(names) >= 40
+    for name in names:
+        f = getattr(ndf._lib, name)
+        args = []
+        for t in f.argtypes:
+            if isinstance(t, type) and issubclass(t, ctypes.Structure):
+                args.append(t())
+            elif t in (ctypes.c_float, ctypes.c_double):
+                args.append(0.0)
+            elif isinstance(t, type) and issubclass(t, ctypes._SimpleCData) and t not in (
+                    ctypes.c_void_p, ctypes.c_char_p):
+                args.append(0)
+            else:
+                args.append(None)
+        assert f(*args) == ndf.NDF_ERR_ARG, name
+    assert ndf._lib.ndf_pearson_noalloc(None, None, 2, 1, 0, None, None) == ndf.NDF_ERR_ARG
