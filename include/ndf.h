@@ -200,11 +200,27 @@ ndf_status ndf_mi_ksg2(ndf_ctx* ctx, int ref_field, int query_field, int64_t ref
  *                   blocks outward in x and, inside a block, outward in y, both
  *                   stopped by its current k-th distance (exact pruning).
  *                   Algorithm 1 only: ndf_mi_ksg2 runs NDF_KSG_PRUNED instead;
+ *   NDF_KSG_LANES   the same two-level search scheduled per lane: each lane walks
+ *                   its own member's blocks and takes the pair's next member when
+ *                   its member is finished; block switches and refills run in a
+ *                   shared service step (ndf_ksg_set_schedule).
+ *                   Algorithm 1 only, like NDF_KSG_BLOCK;
  *   NDF_KSG_BRUTE   every member against every member of each pair.
  * count_evals != 0 makes the kernels count distance evaluations (read with
  * ndf_ksg_take_eval_count); it costs one atomic per warp per launch. */
-typedef enum { NDF_KSG_BRUTE = 0, NDF_KSG_PRUNED = 1, NDF_KSG_BLOCK = 2 } ndf_ksg_algorithm;
+typedef enum {
+    NDF_KSG_BRUTE = 0,
+    NDF_KSG_PRUNED = 1,
+    NDF_KSG_BLOCK = 2,
+    NDF_KSG_LANES = 3
+} ndf_ksg_algorithm;
 ndf_status ndf_set_ksg_algorithm(ndf_ctx* ctx, int algorithm, int count_evals);
+
+/* NDF_KSG_LANES schedule: a warp checks every `every` scan steps (1..8,
+ * default 1) whether to run its service step (block switches, refills), and
+ * runs it when at least `switch_min` lanes wait (1..32, default 8) or none
+ * scans.  Results do not depend on either.  NDF_ERR_ARG outside the ranges. */
+ndf_status ndf_ksg_set_schedule(ndf_ctx* ctx, int switch_min, int every);
 
 /* Distance evaluations counted since the last call (synchronizes; 0 when
  * counting is off). */
@@ -240,6 +256,33 @@ ndf_status ndf_ksg_debug_pair(ndf_ctx* ctx, int ref_field, int query_field, int6
 ndf_status ndf_ksg2_debug_pair(ndf_ctx* ctx, int ref_field, int query_field, int64_t ref_idx,
                                int64_t query_idx, int k, float* ex, float* ey, int32_t* nx,
                                int32_t* ny, double* mi);
+
+/* ---- grids split across GPUs (z-slabs) ------------------------------------ */
+
+/* Given the reference vertex's member column, every vertex is an independent
+ * problem (Sec. 3: R(p_ref, .) vertex by vertex), so a grid split into z-slabs
+ * over several GPUs exchanges one M-float column per reference: the GPU whose
+ * slab holds the reference vertex reads it with ndf_field_column and sends it;
+ * every GPU computes its own slab with ndf_pearson_column / ndf_mi_ksg_column.
+ * The column is staged as a one-vertex field whose statistics come from the
+ * same per-vertex kernel as a loaded field's, so a slab's volume is bit-equal
+ * to the same vertex range of ndf_pearson / ndf_mi_ksg on the whole grid. */
+
+/* The M member values of one vertex of a loaded field: out[m] = e_m(vertex).
+ * out: M floats, host or device.  NDF_ERR_ARG for an unknown field or a vertex
+ * outside [0, N); NDF_ERR_STATE for a freed field. */
+ndf_status ndf_field_column(ndf_ctx* ctx, int field_id, int64_t vertex, float* out);
+
+/* ndf_pearson with the reference given as its member column (M floats of the
+ * query field's member count, host or device, finite) instead of a vertex:
+ * out[v] = r(ref_column, e^query(v)) for the N vertices of the query field.
+ * Errors as ndf_pearson, and NDF_ERR_ARG for a null column. */
+ndf_status ndf_pearson_column(ndf_ctx* ctx, const float* ref_column, int query_field, float* out);
+
+/* ndf_mi_ksg (algorithm 1, the context's search) with the reference given as
+ * its member column, as ndf_pearson_column.  Errors as ndf_mi_ksg. */
+ndf_status ndf_mi_ksg_column(ndf_ctx* ctx, const float* ref_column, int query_field, int k,
+                             float* out);
 
 /* ---- neural dependence field (Sec. 4) ------------------------------------ */
 
@@ -511,17 +554,33 @@ ndf_status ndf_render_volume(ndf_ctx* ctx, const float* vol_a, const float* vol_
  *
  * Scratch: a fixed 64 KB file-scope device array (NDF_NOALLOC_MAX_M floats and
  * two doubles) that every GPU loading the library holds until the process
- * exits.  The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress) with the device current; make that first call before
- * any stream capture.  All calls share the array and each rewrites what it
- * reads, so calls that overlap on the GPU (other streams, other threads) race:
- * serialise them.
+ * exits.  Each call outside stream capture looks up that array's device
+ * address on the current device (cudaGetSymbolAddress); a call during capture
+ * uses the address found by the last call outside capture, so make the first
+ * call on a device, and the first call after a device reset, before any stream
+ * capture (otherwise NDF_ERR_STATE).  All calls share the array and each
+ * rewrites what it reads, so calls that overlap on the GPU (other streams,
+ * other threads) race: serialise them.
  *
- * Errors: NDF_ERR_ARG for a null or non-device pointer, M < 2,
- * M > NDF_NOALLOC_MAX_M, N < 1 or ref_idx outside [0, N); NDF_ERR_CUDA when
- * the set-up or a launch fails.  There is no context, so no error string. */
+ * All three buffers must be memory of the CURRENT device (or managed memory):
+ * a buffer of another GPU is rejected, since the kernels read without peer
+ * access.
+ *
+ * Errors: NDF_ERR_ARG for a null pointer, a pointer that is not device memory
+ * of the current device, M < 2, M > NDF_NOALLOC_MAX_M, N < 1 or ref_idx
+ * outside [0, N); NDF_ERR_STATE for the first call on a device made during
+ * stream capture; NDF_ERR_CUDA when the set-up or a launch fails, and also,
+ * without launching anything, when a CUDA error from the caller's earlier work
+ * is already pending on this thread (it is left pending for the caller to
+ * read).  There is no context, so no error string. */
 ndf_status ndf_pearson_noalloc(const float* ref_field, const float* query_field, int64_t M,
                                int64_t N, int64_t ref_idx, float* out, void* cuda_stream);
+
+/* The pointer rule of ndf_pearson_noalloc as a pure host function (a test
+ * hook; no CUDA call): 1 when a buffer with these attributes is accepted --
+ * managed memory, or device memory whose device equals the current device --
+ * else 0.  The paper has no counterpart. */
+int ndf_noalloc_pointer_usable(int is_device, int is_managed, int ptr_device, int current_device);
 
 #ifdef __cplusplus
 }

@@ -35,19 +35,25 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device; looked up once per
-// device (the host-side symbol is only a stand-in and must not reach a kernel).
-ndf_status scratch_address(void** out) {
+// Device address of the scratch array on the current device (the host-side
+// symbol is only a stand-in and must not reach a kernel).  Outside stream
+// capture the address is looked up again on every call (a cheap host call), so
+// a module reloaded at another address after a device reset is followed; during
+// capture the address recorded by the last call outside capture is used.
+ndf_status scratch_address(cudaStream_t s, void** out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return NDF_ERR_CUDA;
     if (dev < 0 || dev >= kMaxDevices) return NDF_ERR_ARG;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return NDF_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) return NDF_ERR_CUDA;
         g_scratch_addr[dev] = p;
     }
+    if (!g_scratch_addr[dev]) return NDF_ERR_STATE;  // first call of this device under capture
     *out = g_scratch_addr[dev];
     return NDF_OK;
 }
@@ -162,13 +168,21 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-bool is_device_ptr(const void* p) {
+bool pointer_usable(bool is_device, bool is_managed, int ptr_device, int current_device) {
+    if (is_managed) return true;  // reachable from every device
+    return is_device && ptr_device == current_device;
+}
+
+// Device (or managed) memory of the current device; memory of another GPU is
+// rejected, since the kernels read their buffers without peer access.
+bool is_device_ptr(const void* p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    return pointer_usable(a.type == cudaMemoryTypeDevice, a.type == cudaMemoryTypeManaged,
+                          a.device, dev);
 }
 
 }  // namespace
@@ -178,12 +192,17 @@ extern "C" ndf_status ndf_pearson_noalloc(const float* ref_field, const float* q
                                           void* cuda_stream) {
     if (!ref_field || !query_field || !out) return NDF_ERR_ARG;
     if (M < 2 || M > kMaxM || N < 1 || ref_idx < 0 || ref_idx >= N) return NDF_ERR_ARG;
-    if (!is_device_ptr(ref_field) || !is_device_ptr(query_field) || !is_device_ptr(out))
+    // an error left pending by the caller's earlier work is reported, not consumed
+    if (cudaPeekAtLastError() != cudaSuccess) return NDF_ERR_CUDA;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return NDF_ERR_CUDA;
+    if (!is_device_ptr(ref_field, dev) || !is_device_ptr(query_field, dev) ||
+        !is_device_ptr(out, dev))
         return NDF_ERR_ARG;
-    void* scratch = nullptr;
-    ndf_status st = scratch_address(&scratch);
-    if (st != NDF_OK) return st;
     cudaStream_t s = (cudaStream_t)cuda_stream;
+    void* scratch = nullptr;
+    ndf_status st = scratch_address(s, &scratch);
+    if (st != NDF_OK) return st;
     unsigned char* sc = static_cast<unsigned char*>(scratch);
     noalloc_stage_kernel<<<1, 1024, 0, s>>>(ref_field, (int)M, N, ref_idx, sc);
     if (cudaGetLastError() != cudaSuccess) return NDF_ERR_CUDA;
@@ -195,4 +214,11 @@ extern "C" ndf_status ndf_pearson_noalloc(const float* ref_field, const float* q
         noalloc_volume_kernel<1><<<(unsigned)blocks, 256, 0, s>>>(query_field, (int)M, N, sc, out);
     }
     return cudaGetLastError() == cudaSuccess ? NDF_OK : NDF_ERR_CUDA;
+}
+
+// The pointer rule of ndf_pearson_noalloc as a pure function of the attributes
+// (a host-side hook, so that the rule is testable without a second GPU).
+extern "C" int ndf_noalloc_pointer_usable(int is_device, int is_managed, int ptr_device,
+                                          int current_device) {
+    return pointer_usable(is_device != 0, is_managed != 0, ptr_device, current_device) ? 1 : 0;
 }

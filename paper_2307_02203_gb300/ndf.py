@@ -26,7 +26,7 @@ NDF_OK, NDF_ERR_ARG, NDF_ERR_OOM, NDF_ERR_CUDA = 0, -1, -2, -3
 NDF_ERR_TIMEOUT, NDF_ERR_STATE, NDF_ERR_IO = -4, -5, -6
 NDF_PREC_FP32, NDF_PREC_BF16X3, NDF_PREC_TF32 = 0, 1, 2
 NDF_MEASURE_PEARSON, NDF_MEASURE_MI_KSG = 0, 1
-NDF_KSG_BRUTE, NDF_KSG_PRUNED, NDF_KSG_BLOCK = 0, 1, 2
+NDF_KSG_BRUTE, NDF_KSG_PRUNED, NDF_KSG_BLOCK, NDF_KSG_LANES = 0, 1, 2, 3
 NDF_RENDER_DVR, NDF_RENDER_ISO = 0, 1
 NDF_ACT_RELU, NDF_ACT_SNAKE, NDF_ACT_SNAKEALT = 0, 1, 2
 NDF_MERGE_PRODUCT, NDF_MERGE_SUM, NDF_MERGE_ABSDIFF, NDF_MERGE_CONCAT = 0, 1, 2, 3
@@ -115,12 +115,17 @@ _sig("ndf_hash_get_decode", ctypes.c_int32, [_vp])
 _sig("ndf_pearson_batch", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int,
                                          ctypes.c_int, _vp])
 _sig("ndf_set_ksg_algorithm", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int])
+_sig("ndf_ksg_set_schedule", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int])
 _sig("ndf_ksg_take_eval_count", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64)])
 _sig("ndf_mi_ksg_batch", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int,
                                         ctypes.c_int, _vp])
 _sig("ndf_ksg_autotune", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)])
 _sig("ndf_pearson_noalloc", ctypes.c_int, [_vp, _vp, _i64, _i64, _i64, _vp, _vp])
+_sig("ndf_field_column", ctypes.c_int, [_vp, ctypes.c_int, _i64, _vp])
+_sig("ndf_pearson_column", ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp])
+_sig("ndf_mi_ksg_column", ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp])
+_sig("ndf_noalloc_pointer_usable", ctypes.c_int, [ctypes.c_int] * 4)
 _sig("ndf_ksg_debug_pair", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, _i64,
                                           ctypes.c_int, _vp, _vp, _vp, _vp])
 _sig("ndf_ksg2_debug_pair", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, _i64,
@@ -304,6 +309,10 @@ def ndf_set_ksg_algorithm(ctx, algorithm: int, count_evals: bool = False) -> Non
            "ndf_set_ksg_algorithm")
 
 
+def ndf_ksg_set_schedule(ctx, switch_min: int, every: int = 1) -> None:
+    _check(ctx, _lib.ndf_ksg_set_schedule(ctx, int(switch_min), int(every)), "ndf_ksg_set_schedule")
+
+
 def ndf_ksg_take_eval_count(ctx) -> int:
     v = ctypes.c_uint64(0)
     _check(ctx, _lib.ndf_ksg_take_eval_count(ctx, ctypes.byref(v)), "ndf_ksg_take_eval_count")
@@ -457,6 +466,30 @@ def ndf_pearson_noalloc(ref_field, query_field, M, N, ref_idx, out, cuda_stream=
                                   _addr(out), cuda_stream)
     if st != NDF_OK:
         raise NdfError(st, "ndf_pearson_noalloc", "see include/ndf.h for the argument limits")
+
+
+def ndf_field_column(ctx, field_id: int, vertex: int, out) -> None:
+    """out[m] = member m's value at the vertex (M floats, host or device)."""
+    _check(ctx, _lib.ndf_field_column(ctx, field_id, vertex, _addr(out)), "ndf_field_column")
+
+
+def ndf_pearson_column(ctx, ref_column, query_field: int, out) -> None:
+    """Pearson volume of the query field against a reference member column."""
+    _check(ctx, _lib.ndf_pearson_column(ctx, _addr(ref_column), query_field, _addr(out)),
+           "ndf_pearson_column")
+
+
+def ndf_mi_ksg_column(ctx, ref_column, query_field: int, k: int, out) -> None:
+    """KSG MI volume of the query field against a reference member column."""
+    _check(ctx, _lib.ndf_mi_ksg_column(ctx, _addr(ref_column), query_field, k, _addr(out)),
+           "ndf_mi_ksg_column")
+
+
+def ndf_noalloc_pointer_usable(is_device: bool, is_managed: bool, ptr_device: int,
+                               current_device: int) -> bool:
+    """The buffer rule of ndf_pearson_noalloc (a host-only test hook)."""
+    return bool(_lib.ndf_noalloc_pointer_usable(int(is_device), int(is_managed), ptr_device,
+                                                current_device))
 
 
 def ndf_sample_triples(ctx, ref_field: int, query_field: int, measure: int, k: int, n: int,

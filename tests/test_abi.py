@@ -101,3 +101,17 @@ def test_null_handles_are_rejected(lib):
                 args.append(None)
         assert f(*args) == ndf.NDF_ERR_ARG, name
     assert ndf._lib.ndf_pearson_noalloc(None, None, 2, 1, 0, None, None) == ndf.NDF_ERR_ARG
+
+
+def test_noalloc_pointer_rule(lib):
+    """ndf_pearson_noalloc accepts device memory of the current device and managed
+    memory, and rejects host memory and memory of another GPU (the rule itself is
+    a host function, so a second GPU is not needed to check it)."""
+    from paper_2307_02203_gb300 import ndf
+
+    assert ndf.ndf_noalloc_pointer_usable(True, False, 0, 0)
+    assert ndf.ndf_noalloc_pointer_usable(True, False, 3, 3)
+    assert not ndf.ndf_noalloc_pointer_usable(True, False, 1, 0)   # another GPU's memory
+    assert not ndf.ndf_noalloc_pointer_usable(True, False, 0, 1)
+    assert ndf.ndf_noalloc_pointer_usable(False, True, 1, 0)       # managed: every device
+    assert not ndf.ndf_noalloc_pointer_usable(False, False, 0, 0)  # host memory
