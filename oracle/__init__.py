@@ -8,7 +8,8 @@ its own build.
 
 Functions and the passages they follow:
   pearson / pearson_volume -- Sec. 3.1, Eq. 1 (FP64, two-pass, plain definition)
-  ksg_pair / ksg_volume    -- Sec. 3.2 / Sec. 6.2: the cited KSG estimator,
+  ksg_pair / ksg_pairs /
+  ksg_volume               -- Sec. 3.2 / Sec. 6.2: the cited KSG estimator,
                               algorithm 1, brute force (FP32 max-norm distances,
                               k-th order statistic by nth_element, linear-scan
                               strict counts, long-double digamma sum)
@@ -115,6 +116,10 @@ def _load():
             lib.oracle_ksg_volume.argtypes = [_f32p, _f32p, ctypes.c_int64, ctypes.c_int64,
                                               ctypes.c_int64, ctypes.c_int, _i64p, ctypes.c_int64,
                                               _f64p, ctypes.c_int]
+            lib.oracle_ksg_pairs.restype = ctypes.c_int
+            lib.oracle_ksg_pairs.argtypes = [_f32p, _f32p, ctypes.c_int64, ctypes.c_int64,
+                                             ctypes.c_int64, ctypes.c_int, _i64p, ctypes.c_int64,
+                                             _f32p, _i32p, _i32p, _f64p, ctypes.c_int]
             lib.oracle_ksg2_pair.restype = ctypes.c_double
             lib.oracle_ksg2_pair.argtypes = [_f32p, _f32p, ctypes.c_int64, ctypes.c_int, _f32p,
                                              _f32p, _i32p, _i32p]
@@ -233,6 +238,30 @@ def ksg_volume(ref_field, q_field, ref_idx: int, k: int, verts=None, nthreads: i
     if rc != 0:
         raise ValueError("oracle_ksg_volume: bad arguments")
     return out
+
+
+def ksg_pairs(ref_field, q_field, ref_idx: int, k: int, verts, nthreads: int = 0):
+    """ksg_pair of the reference column against each listed query column, in
+    parallel: returns (mi[n], eps[n][M], nx[n][M], ny[n][M])."""
+    rf, M = _field2d(ref_field)
+    qf, Mq = _field2d(q_field)
+    if Mq != M or rf.shape != qf.shape:
+        raise ValueError("fields differ in shape")
+    N = rf.shape[1]
+    verts = np.ascontiguousarray(verts, dtype=np.int64)
+    n = verts.shape[0]
+    eps = np.empty((n, M), dtype=np.float32)
+    nx = np.empty((n, M), dtype=np.int32)
+    ny = np.empty((n, M), dtype=np.int32)
+    mi = np.empty(n, dtype=np.float64)
+    rc = _load().oracle_ksg_pairs(rf.ctypes.data_as(_f32p), qf.ctypes.data_as(_f32p), M, N,
+                                  int(ref_idx), int(k), verts.ctypes.data_as(_i64p), n,
+                                  eps.ctypes.data_as(_f32p), nx.ctypes.data_as(_i32p),
+                                  ny.ctypes.data_as(_i32p), mi.ctypes.data_as(_f64p),
+                                  int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle_ksg_pairs: bad arguments")
+    return mi, eps, nx, ny
 
 
 def ksg2_pair(x, y, k: int):

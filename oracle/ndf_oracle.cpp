@@ -173,6 +173,37 @@ int oracle_ksg_volume(const float* ref_field, const float* q_field, int64_t M, i
     return bad ? -1 : 0;
 }
 
+// oracle_ksg_pair for the reference vertex and each listed query vertex, with
+// the per-member eps / nx / ny of every pair (row i of the [nverts][M] outputs
+// belongs to verts[i]); the pairs are independent and run in parallel.
+int oracle_ksg_pairs(const float* ref_field, const float* q_field, int64_t M, int64_t N,
+                     int64_t ref_idx, int k, const int64_t* verts, int64_t nverts, float* eps,
+                     int32_t* nx, int32_t* ny, double* mi, int nthreads) {
+    if (!ref_field || !q_field || !verts || !eps || !nx || !ny || !mi || M < 2 || N < 1 ||
+        ref_idx < 0 || ref_idx >= N || k < 1 || k >= M || nverts < 0)
+        return -1;
+    std::vector<float> x(static_cast<size_t>(M));
+    gather_column(ref_field, M, N, ref_idx, x.data());
+    set_threads(nthreads);
+    int bad = 0;
+#pragma omp parallel
+    {
+        std::vector<float> y(static_cast<size_t>(M));
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t i = 0; i < nverts; ++i) {
+            int64_t v = verts[i];
+            if (v < 0 || v >= N) {
+#pragma omp atomic write
+                bad = 1;
+                continue;
+            }
+            gather_column(q_field, M, N, v, y.data());
+            mi[i] = oracle_ksg_pair(x.data(), y.data(), M, k, eps + i * M, nx + i * M, ny + i * M);
+        }
+    }
+    return bad ? -1 : 0;
+}
+
 // KSG algorithm 2 (the second estimator of the article cited in Sec. 3.2), one pair:
 //   d_ij, eps_i      as in algorithm 1 (k-th smallest joint max-norm distance, j != i)
 //   neighbour set    S_i = {j != i : d_ij <= eps_i}: the k nearest; with ties at the

@@ -45,6 +45,12 @@ double oracle_ksg_pair(const float* x, const float* y, int64_t M, int k, float* 
 int oracle_ksg_volume(const float* ref_field, const float* q_field, int64_t M, int64_t N,
                       int64_t ref_idx, int k, const int64_t* verts, int64_t nverts, double* out,
                       int nthreads);
+/* oracle_ksg_pair for the reference vertex against each of verts[0..nverts):
+ * eps/nx/ny are [nverts][M] (row i for verts[i]), mi is [nverts].  0, or -1 for
+ * bad arguments. */
+int oracle_ksg_pairs(const float* ref_field, const float* q_field, int64_t M, int64_t N,
+                     int64_t ref_idx, int k, const int64_t* verts, int64_t nverts, float* eps,
+                     int32_t* nx, int32_t* ny, double* mi, int nthreads);
 
 /* KSG algorithm-2 estimate for one pair of samples.  ex/ey/nx/ny (length M, may
  * be NULL) receive per member the marginal extents of its neighbour set and the

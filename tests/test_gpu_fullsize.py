@@ -38,39 +38,61 @@ def test_csens_pearson_sampled(ndf_mod, ctx, csens):
     assert np.isfinite(out.cpu().numpy()).all()
 
 
-@pytest.mark.parametrize("algorithm", ["pruned", "brute", "block"])
-def test_csens_ksg_sampled(ndf_mod, ctx, csens, algorithm):
+MI_SAMPLE = 65536   # vertices whose MI the oracle computes at paper scale
+PAIR_SAMPLE = 4096  # (reference, vertex) pairs whose per-member eps / nx / ny are compared
+
+
+@pytest.fixture(scope="module")
+def csens_ksg_oracle(csens):
+    """The oracle's MI on a seeded 65,536-vertex sample (plus the grid's first and
+    last vertex and the reference itself) and its per-member eps / nx / ny on
+    4,096 seeded pairs; shared by the three searches."""
+    f, _ = csens
+    N = synth.CSENS.N
+    r = synth.vertex_index(*REF, synth.CSENS)
+    verts = np.unique(np.concatenate([synth.sample_vertices(synth.CSENS, MI_SAMPLE, seed=6),
+                                      [0, r, N - 1]])).astype(np.int64)
+    mi = oracle.ksg_volume(f, f, r, 8, verts=verts)
+    pverts = synth.sample_vertices(synth.CSENS, PAIR_SAMPLE, seed=7)
+    pairs = oracle.ksg_pairs(f, f, r, 8, pverts)
+    return r, verts, mi, pverts, pairs
+
+
+@pytest.mark.parametrize("algorithm", ["pruned", "brute", "block", "lanes"])
+def test_csens_ksg_sampled(ndf_mod, ctx, csens, csens_ksg_oracle, algorithm):
+    """Every exact search at paper scale: MI within the O12 tolerance on 65,536
+    seeded vertices, and eps, n_x, n_y bit-equal to the oracle on 4,096 seeded
+    pairs through the debug hook."""
     f, fid = csens
     N = synth.CSENS.N
     M = synth.CSENS.M
-    r = synth.vertex_index(*REF, synth.CSENS)
+    r, verts, mi_ref, pverts, (pmi, peps, pnx, pny) = csens_ksg_oracle
     out = torch.empty(N, dtype=torch.float32, device="cuda")
     code = {"pruned": ndf_mod.NDF_KSG_PRUNED, "brute": ndf_mod.NDF_KSG_BRUTE,
-            "block": ndf_mod.NDF_KSG_BLOCK}[algorithm]
+            "block": ndf_mod.NDF_KSG_BLOCK, "lanes": ndf_mod.NDF_KSG_LANES}[algorithm]
     ndf_mod.ndf_set_ksg_algorithm(ctx, code)
-    ndf_mod.ndf_mi_ksg(ctx, fid, fid, r, 8, out)
-    ndf_mod.ndf_synchronize(ctx)
-    vol = out.cpu().numpy()
-    assert np.isfinite(vol).all()
-    verts = np.concatenate([synth.sample_vertices(synth.CSENS, 4096, seed=6),
-                            [0, r, N - 1]]).astype(np.int64)
-    ref = oracle.ksg_volume(f, f, r, 8, verts=verts)
-    got = vol[verts].astype(np.float64)
-    bad = np.abs(got - ref) > 1e-6 * np.abs(ref) + 1e-9
-    assert not bad.any(), (verts[bad][:5], got[bad][:5], ref[bad][:5])
-    # per-member eps / counts bit-exact on a smaller sample
-    f2 = f.reshape(M, N)
-    for v in synth.sample_vertices(synth.CSENS, 64, seed=7):
+    try:
+        ndf_mod.ndf_mi_ksg(ctx, fid, fid, r, 8, out)
+        ndf_mod.ndf_synchronize(ctx)
+        vol = out.cpu().numpy()
+        assert np.isfinite(vol).all()
+        got = vol[verts].astype(np.float64)
+        bad = np.abs(got - mi_ref) > 1e-6 * np.abs(mi_ref) + 1e-9
+        assert not bad.any(), (int(bad.sum()), verts[bad][:5], got[bad][:5], mi_ref[bad][:5])
         eps = np.empty(M, np.float32)
         nx = np.empty(M, np.int32)
         ny = np.empty(M, np.int32)
         mi = np.empty(1, np.float64)
-        ndf_mod.ndf_ksg_debug_pair(ctx, fid, fid, r, int(v), 8, eps, nx, ny, mi)
-        o = oracle.ksg_pair(f2[:, r], f2[:, v], 8)
-        np.testing.assert_array_equal(eps, o[1])
-        np.testing.assert_array_equal(nx, o[2])
-        np.testing.assert_array_equal(ny, o[3])
-    ndf_mod.ndf_set_ksg_algorithm(ctx, ndf_mod.NDF_KSG_BLOCK)  # the default
+        mism = []
+        for i, v in enumerate(pverts):
+            ndf_mod.ndf_ksg_debug_pair(ctx, fid, fid, r, int(v), 8, eps, nx, ny, mi)
+            if not (np.array_equal(eps, peps[i]) and np.array_equal(nx, pnx[i]) and
+                    np.array_equal(ny, pny[i])):
+                mism.append(int(v))
+            assert abs(mi[0] - pmi[i]) <= 1e-6 * abs(pmi[i]) + 1e-9, (int(v), mi[0], pmi[i])
+        assert not mism, (len(mism), mism[:5])
+    finally:
+        ndf_mod.ndf_set_ksg_algorithm(ctx, ndf_mod.NDF_KSG_BLOCK)  # the default
 
 
 def test_csens_ksg2_sampled(ndf_mod, ctx, csens):
@@ -106,16 +128,26 @@ def test_csens_ksg2_sampled(ndf_mod, ctx, csens):
 
 
 def test_csens_ksg_batch_sampled(ndf_mod, ctx, csens):
-    """Four references in one batched launch against the oracle on sampled vertices."""
+    """Sixty-four references in one batched launch (the default search) against
+    the oracle on 128 seeded vertices per reference (8,192 pairs), and two of
+    its volumes bit-equal to single-reference calls."""
     f, fid = csens
     N = synth.CSENS.N
-    refs = [int(v) for v in synth.sample_vertices(synth.CSENS, 4, seed=8)]
-    out = torch.empty((4, N), dtype=torch.float32, device="cuda")
+    R = 64
+    refs = [int(v) for v in synth.sample_vertices(synth.CSENS, R, seed=8)]
+    out = torch.empty((R, N), dtype=torch.float32, device="cuda")
     ndf_mod.ndf_mi_ksg_batch(ctx, fid, fid, refs, 8, out)
     ndf_mod.ndf_synchronize(ctx)
     vol = out.cpu().numpy()
-    verts = synth.sample_vertices(synth.CSENS, 512, seed=9)
+    assert np.isfinite(vol).all()
     for i, r in enumerate(refs):
+        verts = synth.sample_vertices(synth.CSENS, 128, seed=900 + i)
         ref = oracle.ksg_volume(f, f, r, 8, verts=verts)
         got = vol[i][verts].astype(np.float64)
-        assert (np.abs(got - ref) <= 1e-6 * np.abs(ref) + 1e-9).all()
+        bad = np.abs(got - ref) > 1e-6 * np.abs(ref) + 1e-9
+        assert not bad.any(), (i, r, verts[bad][:5], got[bad][:5], ref[bad][:5])
+    one = torch.empty(N, dtype=torch.float32, device="cuda")
+    for i in (0, R - 1):
+        ndf_mod.ndf_mi_ksg(ctx, fid, fid, refs[i], 8, one)
+        ndf_mod.ndf_synchronize(ctx)
+        assert torch.equal(one, out[i])

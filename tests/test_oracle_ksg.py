@@ -159,6 +159,25 @@ def test_volume_matches_pairs(tiny_field, tiny_ref):
     assert vol[2] == pytest.approx(psi_exact(M) - psi_exact(4), abs=1e-9)
 
 
+def test_pairs_match_single_pairs(tiny_field, tiny_ref):
+    """ksg_pairs (the parallel per-member form used by the paper-scale GPU
+    parity) gives, row by row, what ksg_pair gives for the same columns."""
+    M = tiny_field.shape[0]
+    f2 = tiny_field.reshape(M, -1)
+    verts = np.array([0, 3, tiny_ref, 700, 1023], dtype=np.int64)
+    mi, eps, nx, ny = oracle.ksg_pairs(tiny_field, tiny_field, tiny_ref, 4, verts)
+    for i, v in enumerate(verts):
+        o = oracle.ksg_pair(f2[:, tiny_ref], f2[:, v], 4)
+        assert mi[i] == o[0]
+        np.testing.assert_array_equal(eps[i], o[1])
+        np.testing.assert_array_equal(nx[i], o[2])
+        np.testing.assert_array_equal(ny[i], o[3])
+    # self pair without ties: every member has n_x = n_y = k - 1
+    assert (nx[2] == 3).all() and (ny[2] == 3).all()
+    with pytest.raises(ValueError):
+        oracle.ksg_pairs(tiny_field, tiny_field, tiny_ref, 4, np.array([1 << 20]))
+
+
 def test_volumes_take_reference_from_ref_field():
     """Cross-field volumes (the A -> B case): the reference column comes from the
     first field and every query column from the second, vertex by vertex, for
