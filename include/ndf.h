@@ -195,12 +195,12 @@ ndf_status ndf_mi_ksg2(ndf_ctx* ctx, int ref_field, int query_field, int64_t ref
  *                   order of the reference value, each side of a member's
  *                   outward scan stopped at the first x-gap that reaches its
  *                   current k-th distance (exact pruning);
- *   NDF_KSG_BLOCK   (default) two warps per pair; members cut into blocks of 64 x-ranks,
+ *   NDF_KSG_BLOCK   two warps per pair; members cut into blocks of 64 x-ranks,
  *                   sorted by the query value inside each block; a member scans
  *                   blocks outward in x and, inside a block, outward in y, both
  *                   stopped by its current k-th distance (exact pruning).
  *                   Algorithm 1 only: ndf_mi_ksg2 runs NDF_KSG_PRUNED instead;
- *   NDF_KSG_LANES   the same two-level search scheduled per lane: each lane walks
+ *   NDF_KSG_LANES   (default) the same two-level search scheduled per lane: each lane walks
  *                   its own member's blocks and takes the pair's next member when
  *                   its member is finished; block switches and refills run in a
  *                   shared service step (ndf_ksg_set_schedule).
@@ -217,8 +217,8 @@ typedef enum {
 ndf_status ndf_set_ksg_algorithm(ndf_ctx* ctx, int algorithm, int count_evals);
 
 /* NDF_KSG_LANES schedule: a warp checks every `every` scan steps (1..8,
- * default 1) whether to run its service step (block switches, refills), and
- * runs it when at least `switch_min` lanes wait (1..32, default 8) or none
+ * default 5) whether to run its service step (block switches, refills), and
+ * runs it when at least `switch_min` lanes wait (1..32, default 12) or none
  * scans.  Results do not depend on either.  NDF_ERR_ARG outside the ranges. */
 ndf_status ndf_ksg_set_schedule(ndf_ctx* ctx, int switch_min, int every);
 
@@ -227,11 +227,18 @@ ndf_status ndf_ksg_set_schedule(ndf_ctx* ctx, int switch_min, int every);
 ndf_status ndf_ksg_take_eval_count(ndf_ctx* ctx, uint64_t* evals);
 
 /* R KSG volumes in one persistent launch (the context's search): out[i*N + v] =
- * I(e^ref(ref_idx[i]); e^query(v)).  The pruned search takes (reference,
+ * I(e^ref(ref_idx[i]); e^query(v)).  The exact searches take (reference,
  * vertex) pairs from one work counter; the brute-force search processes
  * references in groups that share each loaded query column and its sorted copy,
  * the group size and tile from ndf_ksg_autotune (defaults 4 references x 8
- * vertices). */
+ * vertices).  ref_idx: R indices in host or device memory.  Host indices are
+ * range-checked before anything is enqueued; device indices are checked by the
+ * staging kernel (an index outside [0, N) leaves that reference's volume
+ * meaningless and makes the next host check return NDF_ERR_ARG).  With device
+ * indices and a device output the call enqueues only kernels and a memset --
+ * no host copy, synchronisation or allocation once an earlier call with the
+ * same R and fields has sized the scratch -- so it can be captured in a CUDA
+ * graph on the context's stream and replayed. */
 ndf_status ndf_mi_ksg_batch(ndf_ctx* ctx, int ref_field, int query_field, const int64_t* ref_idx,
                             int R, int k, float* out);
 

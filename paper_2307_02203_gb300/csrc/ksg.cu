@@ -53,13 +53,25 @@ __host__ __device__ __forceinline__ int padi(int i) { return i + (i >> 2); }  //
 // ---------------------------------------------------------------- stage
 // one CTA per reference: sorted reference values and their member ids
 // (refs == nullptr: references ref0, ref0 + 1, ...)
+// A device-resident index outside [0, N) (host-given ones are checked before the
+// launch) stages NaN values with the identity order: the reference's volume is
+// meaningless but every later access stays in bounds, and the status word tells
+// the next host check.
 __global__ void __launch_bounds__(1024)
     ksg_stage_kernel(const float* __restrict__ field, int M, int64_t N,
                      const int64_t* __restrict__ refs, int64_t ref0, float* __restrict__ xs_all,
-                     int* __restrict__ perm_all) {
+                     int* __restrict__ perm_all, unsigned* __restrict__ status) {
     __shared__ float key[kKsgMaxM];
     __shared__ int val[kKsgMaxM];
     const int64_t ref = refs ? refs[blockIdx.x] : ref0 + blockIdx.x;
+    if (ref < 0 || ref >= N) {
+        if (threadIdx.x == 0 && status) atomicOr(status, kDevBadInput);
+        for (int i = threadIdx.x; i < M; i += blockDim.x) {
+            xs_all[(int64_t)blockIdx.x * M + i] = __int_as_float(0x7fc00000);
+            perm_all[(int64_t)blockIdx.x * M + i] = i;
+        }
+        return;
+    }
     int n2 = 1;
     while (n2 < M) n2 <<= 1;
     for (int i = threadIdx.x; i < n2; i += blockDim.x) {
@@ -805,6 +817,284 @@ __global__ void __launch_bounds__(32 * kGroupWarps * kMaxGroupsPerCta, 1)
     }
 }
 
+// ---------------------------------------------------------------- lane-refill block search
+// The same two-level search as ksg_block_kernel (x-blocks of kBlk ranks sorted by
+// the query value, +inf separators, the same window, x-gap and insert rules, so
+// eps_i is again the brute-force value bit for bit), scheduled per lane instead of
+// per block scan:
+//   - a lane owns one member at a time and walks its own sequence of blocks: its own
+//     block from its position outward, then the neighbouring blocks, at each switch
+//     the side whose nearest x-rank is closer (a side ends at the first block whose
+//     nearest x-rank is at least the current k-th distance away);
+//   - a lane whose member is finished stores eps_i (by block position) and takes the
+//     pair's next member from a counter the group's two warps share;
+//   - block switches (gap tests and the 6-step binary search) and refills run in a
+//     warp-uniform service step, entered only when at least `switch_min` lanes wait
+//     or no lane is scanning, so the divergent code runs for many lanes at once;
+//   - every other lock step is the scan step of the block kernel for all lanes;
+//   - the marginal counts and the digamma sum follow in an evenly split pass over
+//     the stored eps.
+// A lock-step model of both schedules on csens-like pairs (M = 1000, k = 8) counts
+// about 600 lock steps per pair here against about 1300 for the block kernel (lane
+// utilisation 0.70 against 0.33).  Members are handed out in the block kernel's task
+// order (8 y-positions of 4 neighbouring blocks per 32), so the lanes of a warp start
+// on members of similar rank.  Shared memory per pair: the block-sorted points, the
+// sorted query column and the stored eps (16 B x M); the sorted reference values are
+// read from the staging buffer in global memory (L1), for the x-gap tests and n_x.
+struct LaneCtl {
+    unsigned long long item;
+    int next;  // the pair's next member slot
+    int pad;
+    double part[kGroupWarps];
+};
+__host__ __device__ inline int lane_slots(int nb) {
+    return ((nb + kTaskBlocks - 1) / kTaskBlocks) * kTaskQuads * 32;
+}
+__host__ __device__ inline size_t lane_group_bytes(int M) {
+    const int nb = (M + kBlk - 1) / kBlk;
+    return sizeof(LaneCtl) + sizeof(float2) * ((size_t)nb * kBlkStride + 1) +
+           sizeof(float) * (size_t)((M + 3) & ~3) + sizeof(float) * (size_t)nb * kBlk +
+           sizeof(float2) * (size_t)nb;
+}
+// lock steps a warp may take per pair before it gives up (a safety bound far above
+// any real schedule: every member visits at most nb blocks of kBlk + 1 steps)
+__host__ __device__ inline long long lane_step_bound(int nb) {
+    return (long long)lane_slots(nb) * (nb + 2) * (kBlk + 4);
+}
+
+template <int K1>
+__global__ void __launch_bounds__(32 * kGroupWarps * kMaxGroupsPerCta, 1)
+    ksg_lane_kernel(KsgArgs A, unsigned long long* work, int switch_min, int every) {
+    constexpr int KK = K1 - 1;
+    constexpr int GT = 32 * kGroupWarps;
+    constexpr unsigned FULL = 0xffffffffu;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int M = A.M, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int group = warp / kGroupWarps, gw = warp % kGroupWarps, gt = threadIdx.x % GT;
+    const int nb = (M + kBlk - 1) / kBlk;
+    const int slots = lane_slots(nb);
+    unsigned char* gbase = smem + (size_t)group * lane_group_bytes(M);
+    LaneCtl* ctl = reinterpret_cast<LaneCtl*>(gbase);
+    float2* blk = reinterpret_cast<float2*>(gbase + sizeof(LaneCtl));  // (y, x), separated blocks
+    float* ys = reinterpret_cast<float*>(blk + (size_t)nb * kBlkStride + 1);  // query, sorted
+    float* eps_s = ys + ((M + 3) & ~3);                                  // eps by block position
+    float2* bx = reinterpret_cast<float2*>(eps_s + (size_t)nb * kBlk);   // (first, last) x per block
+    const int64_t N = A.N, nv = A.v_end - A.v_begin;
+    const unsigned long long items =
+        A.paired ? (unsigned long long)nv : (unsigned long long)A.R * (unsigned long long)nv;
+    const double psi_k = A.psi[A.k], psi_M = A.psi[M];
+    const int step_bound = (int)min(lane_step_bound(nb), (long long)INT_MAX);
+    unsigned long long evals_total = 0;
+
+    for (;;) {
+        group_sync(group);  // the previous pair is finished by both warps
+        if (gt == 0) {
+            ctl->item = atomicAdd(work, 1ull);
+            ctl->next = 0;
+        }
+        group_sync(group);
+        const unsigned long long item = ctl->item;
+        if (item >= items) break;
+        const int r = A.paired ? (int)item : (int)(item / (unsigned long long)nv);
+        const int64_t v = A.v_begin + (int64_t)(A.paired ? item : item - (unsigned long long)r * nv);
+        const float* xsg = A.xs_all + (int64_t)r * M;  // reference values, x-sorted (global)
+        const int* perm = A.perm_all + (int64_t)r * M;
+        for (int s = gt; s < M; s += GT) ys[s] = A.sorted[(int64_t)s * N + v];
+        // ---- blocks of kBlk x-ranks, each sorted by y; pads (y = x = +inf) sort last
+        for (int b = gt; b <= nb; b += GT) blk[b * kBlkStride] = make_float2(INFINITY, INFINITY);
+        for (int b = gt; b < nb; b += GT)
+            bx[b] = make_float2(xsg[b * kBlk], xsg[min(b * kBlk + kBlk - 1, M - 1)]);
+        for (int b = gw; b < nb; b += kGroupWarps) {
+            float key[kBlkRegs];
+            int val[kBlkRegs];
+            block_keys(A, perm, b, v, key, val);
+            warp_sort_block(key, val);
+#pragma unroll
+            for (int r2 = 0; r2 < kBlkRegs; ++r2)
+                blk[1 + b * kBlkStride + r2 * 32 + lane] =
+                    make_float2(key[r2], val[r2] < M ? xsg[val[r2]] : INFINITY);
+        }
+        group_sync(group);
+
+        // ---- joint k-NN distance of every member, lanes refilled from the pair's counter
+        bool has = false, inblk = false, exhausted = false;
+        int cb = 0, up = kBlk, dn = -1, nr = 0, nl = -1, slot_pos = 0, start = 0;
+        float xi = INFINITY, yi = INFINITY;
+        float best[KK];
+#pragma unroll
+        for (int c = 0; c < KK; ++c) best[c] = FLT_MAX;
+        unsigned my_evals = 0;
+        // member slot q (task order) -> block, position; slots past a block's end are empty
+        auto take = [&](int q) {
+            has = false;
+            inblk = false;
+            cb = 0;
+            up = kBlk;  // separators: an idle lane reads +inf
+            dn = -1;
+            xi = INFINITY;
+            yi = INFINITY;
+            if (q >= slots) return;
+            const int task = q >> 5, l = q & 31;
+            const int b = (task / kTaskQuads) * kTaskBlocks + l / kTaskRows;
+            const int p = (task % kTaskQuads) * kTaskRows + l % kTaskRows;
+            if (b >= nb || p >= min(kBlk, M - b * kBlk)) return;
+            const float2 me = blk[1 + b * kBlkStride + p];
+            yi = me.x;
+            xi = me.y;
+            has = true;
+            inblk = true;
+            cb = b;
+            up = p + 1;
+            dn = p - 1;
+            start = p;  // the candidates visited in a block are up - dn - 1 - (own block)
+            nr = b + 1;
+            nl = b - 1;
+            slot_pos = b * kBlk + p;
+#pragma unroll
+            for (int c = 0; c < KK; ++c) best[c] = FLT_MAX;
+        };
+        {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&ctl->next, 32);
+            base = __shfl_sync(FULL, base, 0);
+            take(base + lane);
+            exhausted = base + 32 >= slots;
+        }
+        int steps = 0;
+        for (;;) {
+            const bool waiting = has ? !inblk : !exhausted;
+            const unsigned wm = __ballot_sync(FULL, waiting);
+            const unsigned em = __ballot_sync(FULL, has && inblk);
+            if (wm != 0u && (__popc(wm) >= switch_min || em == 0u)) {
+                // service: block switches of the lanes whose window closed, then refills
+                if (has && !inblk) {
+                    my_evals += (unsigned)(up - dn - 1 - (start >= 0 ? 1 : 0));
+                    const float t = best[KK - 1];
+                    const float gr = nr < nb ? bx[nr].x - xi : INFINITY;
+                    const float gl = nl >= 0 ? xi - bx[nl].y : INFINITY;
+                    const bool okr = gr < t, okl = gl < t;
+                    if (!okr && !okl) {
+                        eps_s[slot_pos] = t;  // member finished
+                        has = false;
+                        cb = 0;
+                        up = kBlk;
+                        dn = -1;
+                        xi = INFINITY;
+                        yi = INFINITY;
+                    } else {
+                        const bool go_r = okr && (!okl || gr <= gl);
+                        cb = go_r ? nr : nl;
+                        nr += go_r ? 1 : 0;
+                        nl -= go_r ? 0 : 1;
+                        const int pos = block_lower_bound(blk + 1 + cb * kBlkStride, yi);
+                        up = pos;
+                        dn = pos - 1;
+                        start = -1;
+                        inblk = true;
+                    }
+                }
+                const unsigned dm = __ballot_sync(FULL, !has);
+                if (dm != 0u && !exhausted) {
+                    int base = 0;
+                    if (lane == 0) base = atomicAdd(&ctl->next, __popc(dm));
+                    base = __shfl_sync(FULL, base, 0);
+                    if (!has) take(base + __popc(dm & ((1u << lane) - 1u)));
+                    exhausted = base + __popc(dm) >= slots;
+                }
+            }
+            if (!__any_sync(FULL, has)) {
+                if (exhausted) break;
+                continue;
+            }
+            steps += every;
+            if (steps > step_bound) break;  // never expected: the pair's MI becomes NaN
+            // `every` scan steps: one candidate above and one below in the lane's current
+            // block (idle lanes, and lanes whose window has closed, re-read candidates at
+            // least the threshold away and leave their lists unchanged)
+            const float2* B = blk + 1 + cb * kBlkStride;
+#pragma unroll 2
+            for (int rep = 0; rep < every; ++rep) {
+                const float t = best[KK - 1];
+                const float2 cu = B[up], cd = B[dn];
+                const float dyu = cu.x - yi, dyd = yi - cd.x;
+                const bool au = fabsf(dyu) < t;
+                const bool ad = fabsf(dyd) < t;
+                const float du = fmaxf(fabsf(cu.y - xi), fabsf(dyu));
+                const float dd = fmaxf(fabsf(cd.y - xi), fabsf(dyd));
+                insert2<KK>(best, fminf(du, dd), fmaxf(du, dd));
+                up += au ? 1 : 0;
+                dn -= ad ? 1 : 0;
+                if (!au && !ad) inblk = false;
+            }
+        }
+        const bool aborted = steps > step_bound;
+        group_sync(group);
+
+        // ---- marginal counts and the digamma sum, evenly split over the group
+        const bool dbg = A.dbg_eps && r == 0 && v == A.v_begin;
+        double acc = 0.0;
+        for (int pos = gt; pos < nb * kBlk; pos += GT) {
+            const int b = pos / kBlk, p = pos - b * kBlk;
+            if (p >= min(kBlk, M - b * kBlk)) continue;
+            const float e = eps_s[pos];
+            const float2 me = blk[1 + b * kBlkStride + p];
+            const int self = e > 0.0f ? 1 : 0;
+            const int cx = count_within(xsg, M, me.y, e) - self;
+            const int cy = count_within(ys, M, me.x, e) - self;
+            acc += A.psi[cx + 1] + A.psi[cy + 1];
+            if (dbg) A.dbg_nx[pos] = __float_as_int(e);  // eps by block position (scratch)
+        }
+        if (dbg) {
+            // member ids: each block's sort again (deterministic) gives its positions' x-ranks.
+            // Pass 1 moves eps from the position-indexed scratch (dbg_nx) to dbg_eps[member];
+            // after every read of the scratch, pass 2 writes the counts over it.
+            group_sync(group);
+            for (int bq = gw; bq < nb; bq += kGroupWarps) {
+                float key[kBlkRegs];
+                int val[kBlkRegs];
+                block_keys(A, perm, bq, v, key, val);
+                warp_sort_block(key, val);
+#pragma unroll
+                for (int r2 = 0; r2 < kBlkRegs; ++r2)
+                    if (val[r2] < M)
+                        A.dbg_eps[perm[val[r2]]] = __int_as_float(A.dbg_nx[bq * kBlk + r2 * 32 + lane]);
+            }
+            group_sync(group);
+            for (int bq = gw; bq < nb; bq += kGroupWarps) {
+                float key[kBlkRegs];
+                int val[kBlkRegs];
+                block_keys(A, perm, bq, v, key, val);
+                warp_sort_block(key, val);
+#pragma unroll
+                for (int r2 = 0; r2 < kBlkRegs; ++r2) {
+                    if (val[r2] >= M) continue;
+                    const int mi = perm[val[r2]];
+                    const float e = A.dbg_eps[mi];
+                    const float2 me = blk[1 + bq * kBlkStride + r2 * 32 + lane];
+                    const int self = e > 0.0f ? 1 : 0;
+                    if (A.dbg_ey) A.dbg_ey[mi] = e;
+                    A.dbg_nx[mi] = count_within(xsg, M, me.y, e) - self;
+                    A.dbg_ny[mi] = count_within(ys, M, me.x, e) - self;
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+        evals_total += __reduce_add_sync(FULL, my_evals);
+        if (lane == 0) ctl->part[gw] = aborted ? __longlong_as_double(0x7ff8000000000000ll) : acc;
+        group_sync(group);
+        if (gt == 0) {
+            double tot = 0.0;
+#pragma unroll
+            for (int w = 0; w < kGroupWarps; ++w) tot += ctl->part[w];
+            const double mi = psi_k + psi_M - tot / (double)M;
+            A.out[A.paired ? (v - A.v_begin) : (int64_t)r * A.out_stride + (v - A.v_begin)] = (float)mi;
+            if (dbg && A.dbg_mi) *A.dbg_mi = mi;
+        }
+    }
+    if (A.evals && lane == 0) atomicAdd(A.evals, evals_total);
+}
+
 template <class Kern>
 static cudaError_t launch_persistent(ndf_ctx* ctx, Kern kern, const KsgArgs& A, int threads,
                                     size_t smem, int64_t items) {
@@ -824,6 +1114,30 @@ static cudaError_t launch_persistent(ndf_ctx* ctx, Kern kern, const KsgArgs& A, 
 template <int K1>
 static cudaError_t launch_ksg_k(ndf_ctx* ctx, KsgArgs A, bool prune) {
     const int M = A.M;
+    if (prune && ctx->ksg_algorithm == NDF_KSG_LANES && A.variant == 1) {
+        // two-warp groups per pair; as many groups per CTA as fit in shared memory
+        const size_t per_group = lane_group_bytes(M);
+        int gpc = (int)((227 * 1024) / per_group);
+        if (gpc > kMaxGroupsPerCta) gpc = kMaxGroupsPerCta;
+        if (gpc >= 1) {
+            const size_t smem = (size_t)gpc * per_group;
+            const int threads = 32 * kGroupWarps * gpc;
+            cudaError_t e = ctx->ksg_work.reserve(sizeof(unsigned long long));
+            if (e == cudaSuccess)
+                e = cudaMemsetAsync(ctx->ksg_work.ptr, 0, sizeof(unsigned long long), ctx->stream);
+            if (e != cudaSuccess) return e;
+            auto kern = ksg_lane_kernel<K1>;
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            const int64_t pairs = A.paired ? (A.v_end - A.v_begin) : (int64_t)A.R * (A.v_end - A.v_begin);
+            int64_t grid = (int64_t)ctx->sm_count;
+            if (grid * gpc > pairs) grid = (pairs + gpc - 1) / gpc;
+            kern<<<(unsigned)grid, threads, smem, ctx->stream>>>(A, ctx->ksg_work.as<unsigned long long>(),
+                                                                 ctx->ksg_switch_min, ctx->ksg_every);
+            ctx->launches++;
+            return cudaGetLastError();
+        }
+    }
     if (prune && ctx->ksg_algorithm == NDF_KSG_BLOCK && A.variant == 1) {
         // two-warp groups per pair; as many groups per CTA as fit in shared memory
         const size_t per_group = block_group_bytes(M);
@@ -902,7 +1216,8 @@ cudaError_t launch_ksg(ndf_ctx* ctx, const Field& rf, const Field& qf, const int
     if (e != cudaSuccess) return e;
     ksg_stage_kernel<<<R, 1024, 0, ctx->stream>>>(rf.data, M, rf.N, d_refs, ref0,
                                                    ctx->stage_x.as<float>(),
-                                                   ctx->stage_perm.as<int>());
+                                                   ctx->stage_perm.as<int>(),
+                                                   ctx->flag.as<unsigned>() + 1);
     ctx->launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     KsgArgs A;

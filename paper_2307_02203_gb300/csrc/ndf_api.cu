@@ -163,6 +163,8 @@ ndf_status check_device_status(ndf_ctx* ctx) {
     if (st == 0) return NDF_OK;
     cudaMemset(d, 0, sizeof st);
     if (st & kDevTimeout) return fail(ctx, NDF_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (st & kDevBadInput)
+        return fail(ctx, NDF_ERR_ARG, "a device-resident index was outside the field");
     return fail(ctx, NDF_ERR_CUDA, "device reported status 0x%x", st);
 }
 
@@ -279,6 +281,8 @@ void ndf_destroy(ndf_ctx* ctx) {
     ctx->evals.release();
     ctx->ksg_work.release();
     ctx->render_buf.release();
+    ctx->col_data.release();
+    ctx->col_stats.release();
     if (ctx->copy_stream) {
         cudaStreamSynchronize(ctx->copy_stream);
         cudaStreamDestroy(ctx->copy_stream);
@@ -645,7 +649,8 @@ ndf_status ndf_ksg2_debug_pair(ndf_ctx* ctx, int ref_field, int query_field, int
 
 ndf_status ndf_set_ksg_algorithm(ndf_ctx* ctx, int algorithm, int count_evals) {
     if (!ctx) return NDF_ERR_ARG;
-    if (algorithm != NDF_KSG_BRUTE && algorithm != NDF_KSG_PRUNED && algorithm != NDF_KSG_BLOCK)
+    if (algorithm != NDF_KSG_BRUTE && algorithm != NDF_KSG_PRUNED && algorithm != NDF_KSG_BLOCK &&
+        algorithm != NDF_KSG_LANES)
         return fail(ctx, NDF_ERR_ARG, "unknown KSG algorithm %d", algorithm);
     ctx->ksg_algorithm = algorithm;
     ctx->count_evals = count_evals != 0;
@@ -654,6 +659,16 @@ ndf_status ndf_set_ksg_algorithm(ndf_ctx* ctx, int algorithm, int count_evals) {
         if (e == cudaSuccess) e = cudaMemsetAsync(ctx->evals.ptr, 0, sizeof(unsigned long long), ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "evaluation counter");
     }
+    return NDF_OK;
+}
+
+ndf_status ndf_ksg_set_schedule(ndf_ctx* ctx, int switch_min, int every) {
+    if (!ctx) return NDF_ERR_ARG;
+    if (switch_min < 1 || switch_min > 32)
+        return fail(ctx, NDF_ERR_ARG, "switch_min %d outside 1..32", switch_min);
+    if (every < 1 || every > 8) return fail(ctx, NDF_ERR_ARG, "every %d outside 1..8", every);
+    ctx->ksg_switch_min = switch_min;
+    ctx->ksg_every = every;
     return NDF_OK;
 }
 
@@ -677,9 +692,11 @@ ndf_status ndf_mi_ksg_batch(ndf_ctx* ctx, int ref_field, int query_field, const 
     const Field *rf, *qf;
     ndf_status st = check_pair(ctx, ref_field, query_field, 0, &rf, &qf);
     if (st != NDF_OK) return st;
-    for (int i = 0; i < R; ++i)
-        if (ref_idx[i] < 0 || ref_idx[i] >= rf->N)
-            return fail(ctx, NDF_ERR_ARG, "ref_idx[%d] out of range", i);
+    const bool dev_refs = pointer_kind(ref_idx) == PTR_DEVICE;  // checked by the stage kernel
+    if (!dev_refs)
+        for (int i = 0; i < R; ++i)
+            if (ref_idx[i] < 0 || ref_idx[i] >= rf->N)
+                return fail(ctx, NDF_ERR_ARG, "ref_idx[%d] out of range", i);
     if ((st = check_ksg_args(ctx, rf, k)) != NDF_OK) return st;
     cudaSetDevice(ctx->device);
     if ((st = ensure_psi_table(ctx, rf->M + 1)) != NDF_OK) return st;
@@ -689,12 +706,17 @@ ndf_status ndf_mi_ksg_batch(ndf_ctx* ctx, int ref_field, int query_field, const 
     void* dev_out;
     bool is_host;
     if ((st = resolve_out(ctx, out, bytes, &dev_out, &is_host)) != NDF_OK) return st;
-    cudaError_t e = ctx->refidx.reserve(sizeof(int64_t) * (size_t)R);
+    cudaError_t e = cudaSuccess;
+    const int64_t* d_refs = ref_idx;
+    if (!dev_refs) {
+        e = ctx->refidx.reserve(sizeof(int64_t) * (size_t)R);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ctx->refidx.ptr, ref_idx, sizeof(int64_t) * (size_t)R,
+                                cudaMemcpyHostToDevice, ctx->stream);
+        d_refs = ctx->refidx.as<int64_t>();
+    }
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(ctx->refidx.ptr, ref_idx, sizeof(int64_t) * (size_t)R,
-                            cudaMemcpyHostToDevice, ctx->stream);
-    if (e == cudaSuccess)
-        e = launch_ksg(ctx, *rf, *qf, ctx->refidx.as<int64_t>(), 0, R, k, 0, qf->N,
+        e = launch_ksg(ctx, *rf, *qf, d_refs, 0, R, k, 0, qf->N,
                        static_cast<float*>(dev_out), qf->N, ctx->ksg_algorithm != NDF_KSG_BRUTE,
                        ctx->ksg_group, ctx->ksg_tile, nullptr, nullptr, nullptr, nullptr,
                        ctx->count_evals ? ctx->evals.as<unsigned long long>() : nullptr);

@@ -63,9 +63,11 @@ struct ndf_ctx {
     int64_t psi_n = 0;
     ndf::DevBuf dbg;         // KSG debug outputs
     ndf::DevBuf flag;        // small device status words
-    int ksg_algorithm = NDF_KSG_BLOCK;
+    int ksg_algorithm = NDF_KSG_LANES;
     int ksg_group = 4;       // references per CTA in batched KSG (tuned by ndf_ksg_autotune)
     int ksg_tile = 8;        // query vertices per tile
+    int ksg_switch_min = 12; // lane-refill search: waiting lanes that start a service step
+    int ksg_every = 5;       // lane-refill search: scan steps between service checks
     bool count_evals = false;
     ndf::DevBuf evals;       // KSG distance evaluations (when counting is on)
     ndf::DevBuf ksg_work;    // pruned KSG: work-item counter
@@ -73,6 +75,9 @@ struct ndf_ctx {
     std::vector<CachedBuf> cache;  // device buffers of freed fields, reused by later loads
     ndf::DevBuf zr;          // batched Pearson: standardised reference rows
     ndf::DevBuf refidx;      // batched calls: reference indices on the device
+    ndf::DevBuf col_data;    // volumes against an external reference column: the column
+    ndf::DevBuf col_stats;   //   its mean, 1/sqrt(S) and a non-finite flag
+    ndf::Field col_field;    //   the one-vertex reference field over those buffers
 };
 
 namespace ndf {

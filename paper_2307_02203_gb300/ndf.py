@@ -320,11 +320,19 @@ def ndf_ksg_take_eval_count(ctx) -> int:
 
 
 def ndf_mi_ksg_batch(ctx, ref_field: int, query_field: int, ref_idx, k: int, out) -> None:
+    """ref_idx: a sequence of host indices, or an int64 CUDA tensor (device-resident
+    indices: the call then enqueues no host copy and can be graph-captured)."""
     import numpy as _np
 
-    refs = _np.ascontiguousarray(_np.asarray(ref_idx, dtype=_np.int64))
-    _check(ctx, _lib.ndf_mi_ksg_batch(ctx, ref_field, query_field, refs.ctypes.data,
-                                      int(refs.shape[0]), int(k), _addr(out)), "ndf_mi_ksg_batch")
+    if hasattr(ref_idx, "is_cuda") and ref_idx.is_cuda:
+        if str(ref_idx.dtype) != "torch.int64":
+            raise TypeError("device reference indices must be int64")
+        ptr, R = _addr(ref_idx), int(ref_idx.numel())
+    else:
+        refs = _np.ascontiguousarray(_np.asarray(ref_idx, dtype=_np.int64))
+        ptr, R = refs.ctypes.data, int(refs.shape[0])
+    _check(ctx, _lib.ndf_mi_ksg_batch(ctx, ref_field, query_field, ptr, R, int(k), _addr(out)),
+           "ndf_mi_ksg_batch")
 
 
 def ndf_ksg_autotune(ctx, ref_field: int, query_field: int, k: int):

@@ -156,14 +156,14 @@ def test_pearson_cross_field_and_degenerate(ndf_mod, ctx):
 
 
 # ---------------------------------------------------------------- KSG algorithm 1
-@pytest.fixture(params=["brute", "pruned", "block"])
+@pytest.fixture(params=["brute", "pruned", "block", "lanes"])
 def algo(request, ndf_mod, ctx):
     """Every search must give the same bit-exact eps / counts."""
     code = {"brute": ndf_mod.NDF_KSG_BRUTE, "pruned": ndf_mod.NDF_KSG_PRUNED,
-            "block": ndf_mod.NDF_KSG_BLOCK}[request.param]
+            "block": ndf_mod.NDF_KSG_BLOCK, "lanes": ndf_mod.NDF_KSG_LANES}[request.param]
     ndf_mod.ndf_set_ksg_algorithm(ctx, code)
     yield request.param
-    ndf_mod.ndf_set_ksg_algorithm(ctx, ndf_mod.NDF_KSG_BLOCK)  # the default
+    ndf_mod.ndf_set_ksg_algorithm(ctx, ndf_mod.NDF_KSG_LANES)  # the default
 
 
 def ksg_debug(ndf, ctx, fa, fb, r, v, k, M):
@@ -346,16 +346,18 @@ def test_ksg_eval_counter(ndf_mod, ctx, tiny_field, tiny_ref):
     N = tiny_field[0].size
     out = np.empty(N, dtype=np.float32)
     counts = {}
-    for name in ("NDF_KSG_PRUNED", "NDF_KSG_BLOCK", "NDF_KSG_BRUTE"):
+    for name in ("NDF_KSG_PRUNED", "NDF_KSG_BLOCK", "NDF_KSG_LANES", "NDF_KSG_BRUTE"):
         ndf.ndf_set_ksg_algorithm(ctx, getattr(ndf, name), True)
         ndf.ndf_mi_ksg(ctx, fid, fid, tiny_ref, 4, out)
         counts[name] = ndf.ndf_ksg_take_eval_count(ctx)
         assert ndf.ndf_ksg_take_eval_count(ctx) == 0
-    ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_BLOCK, False)
+    ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_LANES, False)
     # brute force evaluates every candidate; the exact searches strict subsets, the
     # block search fewer than the x-strip scan
     assert counts["NDF_KSG_BRUTE"] == N * M * (M - 1)
     assert 0 < counts["NDF_KSG_BLOCK"] < counts["NDF_KSG_PRUNED"] < N * M * (M - 1)
+    # the lane schedule visits the same kind of windows (another side order)
+    assert 0 < counts["NDF_KSG_LANES"] < counts["NDF_KSG_PRUNED"]
     ndf.ndf_free_ensemble(ctx, fid)
 
 
@@ -431,7 +433,7 @@ def test_load_and_compute_matches_separate_calls(ndf_mod, ctx):
     ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_PRUNED)
     m3 = np.empty(N, np.float32)
     ndf.ndf_mi_ksg(ctx, fid2, fid2, ref, 8, m3)
-    ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_BLOCK)
+    ndf.ndf_set_ksg_algorithm(ctx, ndf.NDF_KSG_LANES)
     np.testing.assert_allclose(m3, m1, rtol=1e-6, atol=1e-9)
     ndf.ndf_free_ensemble(ctx, fid2)
     p4 = np.empty(N, np.float32)

@@ -92,7 +92,7 @@ def test_csens_ksg_sampled(ndf_mod, ctx, csens, csens_ksg_oracle, algorithm):
             assert abs(mi[0] - pmi[i]) <= 1e-6 * abs(pmi[i]) + 1e-9, (int(v), mi[0], pmi[i])
         assert not mism, (len(mism), mism[:5])
     finally:
-        ndf_mod.ndf_set_ksg_algorithm(ctx, ndf_mod.NDF_KSG_BLOCK)  # the default
+        ndf_mod.ndf_set_ksg_algorithm(ctx, ndf_mod.NDF_KSG_LANES)  # the default
 
 
 def test_csens_ksg2_sampled(ndf_mod, ctx, csens):
