@@ -42,6 +42,7 @@ KSG_BLOCK_TRAFFIC_PER_VOLUME = (704.332e6 + 4.026e6) * 20
 KSG_SEARCHES = {  # name: (ndf constant name, kernel at k = 8, DRAM bytes per volume)
     "pruned": ("NDF_KSG_PRUNED", "ksg_pruned_kernel<9>", KSG_PRUNED_TRAFFIC_PER_VOLUME),
     "block": ("NDF_KSG_BLOCK", "ksg_block_kernel<9>", KSG_BLOCK_TRAFFIC_PER_VOLUME),
+    "lanes": ("NDF_KSG_LANES", "ksg_lane_kernel<9>", None),
 }
 METRIC = "ms per 1.76M-voxel dependence volume (Pearson + KSG MI k=8, M=1000)"
 
@@ -148,32 +149,69 @@ def make_field(recipe, pinned, nthreads):
     return None, arr
 
 
-def cpu_baseline(field, recipe, ref, seconds_target, seed):
-    """Times the oracle (all host cores) on a bounded seeded vertex sample and
-    extrapolates to ms per full volume."""
+def cpu_baseline(field, recipe, ref, seconds_target, seed, nthreads=0, k=K_NN):
+    """Times the oracle (nthreads host cores, 0 = all) on a bounded seeded vertex
+    sample and extrapolates to ms per full volume (the full volume when the
+    sample covers the grid)."""
     import oracle
     import synth
 
-    cores = oracle.threads(0)
+    cores = oracle.threads(nthreads)
     probe = synth.sample_vertices(recipe, max(2 * cores, 32), seed=seed + 1)
     t0 = time.perf_counter()
-    oracle.ksg_volume(field, field, ref, K_NN, verts=probe)
-    oracle.pearson_volume(field, field, ref, verts=probe)
+    oracle.ksg_volume(field, field, ref, k, verts=probe, nthreads=nthreads)
+    oracle.pearson_volume(field, field, ref, verts=probe, nthreads=nthreads)
     per_vertex = (time.perf_counter() - t0) / len(probe)
     count = int(max(len(probe), min(recipe.N, seconds_target / max(per_vertex, 1e-9))))
     verts = synth.sample_vertices(recipe, count, seed=seed)
     t0 = time.perf_counter()
-    oracle.pearson_volume(field, field, ref, verts=verts)
+    oracle.pearson_volume(field, field, ref, verts=verts, nthreads=nthreads)
     tp = time.perf_counter() - t0
     t0 = time.perf_counter()
-    oracle.ksg_volume(field, field, ref, K_NN, verts=verts)
+    oracle.ksg_volume(field, field, ref, k, verts=verts, nthreads=nthreads)
     tk = time.perf_counter() - t0
     scale = recipe.N / count
     ms = (tp + tk) * scale * 1e3
+    sample = (f"Pearson + KSG at {count} seeded vertices of {recipe.N}, time x {scale:.1f} "
+              f"(extrapolated)" if count < recipe.N else f"Pearson + KSG, full volume of {recipe.N}")
     return {"value": ms, "unit": "ms per volume", "cores": cores, "kind": "oracle",
-            "sample": f"Pearson + KSG at {count} seeded vertices of {recipe.N}, "
-                      f"time x {scale:.1f} (extrapolated)",
-            "pearson_ms": tp * scale * 1e3, "ksg_ms": tk * scale * 1e3}
+            "sample": sample, "pearson_ms": tp * scale * 1e3, "ksg_ms": tk * scale * 1e3}
+
+
+def cpu_baseline_grid(field, recipe, ref, seconds_target):
+    """The oracle on all host cores and on one core, for the tiny workload (16x16x4,
+    M = 100, k = 4: full volume) and for the benchmark's workload (k = 8, bounded
+    samples, extrapolated); host CPU model stated."""
+    import synth
+
+    tiny = synth.generate(synth.TINY)
+    tref = synth.vertex_index(*synth.TINY_REF, synth.TINY)
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.lower().startswith(("model name", "cpu part")):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    import oracle
+
+    all_n = oracle.threads(0)  # the oracle's current thread count (all host cores)
+    grid = {"cpu_model": model, "nproc": os.cpu_count()}
+    try:
+        for name, fld, rec, r, secs, k in (
+                ("tiny_16x16x4_m100_k4", tiny, synth.TINY, tref, 1.0, 4),
+                ("bench_workload_k8", field, recipe, ref, seconds_target / 3, K_NN)):
+            grid[name] = {}
+            for cores in (all_n, 1):
+                d = cpu_baseline(fld, rec, r, secs, seed=11, nthreads=cores, k=k)
+                grid[name]["one_core" if cores == 1 else "all_cores"] = {
+                    "ms_per_volume": d["value"], "cores": d["cores"], "sample": d["sample"]}
+                oracle.threads(all_n)
+    finally:
+        oracle.threads(all_n)
+    return grid
 
 
 def measure_pearson_batch(ndf, ctx, fid, field, recipe, stream, rank, R=64, reps=3):
@@ -514,6 +552,206 @@ def job_ms_per_volume(total_ms, steps, world):
     return total_ms / (steps * world)
 
 
+def slab_bounds(Z, world):
+    """Contiguous z-ranges [z0, z1) of the ranks' slabs: sizes differ by at most one
+    level (a rank gets an empty slab only when there are more ranks than levels)."""
+    base, extra = divmod(Z, world)
+    out, z = [], 0
+    for r in range(world):
+        n = base + (1 if r < extra else 0)
+        out.append((z, z + n))
+        z += n
+    return out
+
+
+def slab_owner(ref, plane, bounds):
+    """Rank whose slab holds the flat vertex ref (plane = X * Y vertices per level)."""
+    z = ref // plane
+    for r, (z0, z1) in enumerate(bounds):
+        if z0 <= z < z1:
+            return r
+    raise ValueError(f"vertex {ref} outside the slabs")
+
+
+def slab_step(ref, plane, bounds, rank, column_of, broadcast, compute):
+    """One reference over a grid split into z-slabs.  The owner of the reference
+    vertex reads its member column from its own slab (local index ref - z0 * plane)
+    and broadcasts it (the one exchange: M floats); every rank then computes the
+    volumes of its own slab against that column.  Returns compute's result."""
+    owner = slab_owner(ref, plane, bounds)
+    col = column_of(ref - bounds[owner][0] * plane) if rank == owner else None
+    col = broadcast(col, owner)
+    return compute(col)
+
+
+def torch_broadcast(M, device, world):
+    """broadcast(col, owner) for slab_step over torch.distributed (M float32); the
+    identity for a single rank."""
+    import torch
+    import torch.distributed as dist
+
+    def bc(col, owner):
+        if world == 1:
+            return col
+        t = col if col is not None else torch.empty(M, dtype=torch.float32, device=device)
+        dist.broadcast(t, src=owner)
+        return t
+    return bc
+
+
+def run_slabs(args, recipe, world, rank, local_rank):
+    """Strong scaling over z-slabs: every rank holds one slab of the grid (its share
+    of the members' values and statistics); per reference the rank whose slab holds
+    the reference vertex broadcasts its member column (NCCL, M floats) and every rank
+    computes its slab's Pearson and KSG volumes against it.  value = the job's time
+    per volume (max over ranks), scaling "strong"."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2307_02203_gb300 import ndf
+
+    nthreads = max(1, (os.cpu_count() or 1) // max(1, env_int("LOCAL_WORLD_SIZE", world)))
+    _, field = make_field(recipe, pinned=False, nthreads=nthreads)
+    M, Z, Y, X = field.shape
+    plane, N = X * Y, recipe.N
+    bounds = slab_bounds(Z, world)
+    z0, z1 = bounds[rank]
+    Zs = z1 - z0
+    Ns = Zs * plane
+    slab_t = None
+    if Zs:
+        slab_t = torch.empty((M, Zs, Y, X), dtype=torch.float32, pin_memory=True)
+        slab_t.numpy()[:] = field[:, z0:z1]
+    del field
+    stream = torch.cuda.Stream()
+    ctx = ndf.ndf_create(local_rank, stream.cuda_stream)
+    ndf.ndf_set_ksg_algorithm(ctx, getattr(ndf, KSG_SEARCHES[args.ksg_search][0]))
+    if args.ksg_schedule:
+        ndf.ndf_ksg_set_schedule(ctx, *args.ksg_schedule)
+    fid = ndf.ndf_load_ensemble(ctx, slab_t, M, Zs, Y, X) if Zs else None
+    out_r = torch.empty(max(Ns, 1), dtype=torch.float32, device="cuda")
+    out_mi = torch.empty(max(Ns, 1), dtype=torch.float32, device="cuda")
+    col = torch.empty(M, dtype=torch.float32, device="cuda")
+    bc = torch_broadcast(M, "cuda", world)
+    refs = rank_references(N, args.warmup + args.steps, 0)  # one reference stream per job
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    cur = {"i": None}
+
+    def column_of(v_local):
+        ndf.ndf_field_column(ctx, fid, v_local, col)
+        return col
+
+    def compute(c):
+        i = cur["i"]
+        if i is not None:
+            ev[i][0].record(stream)
+        if fid is not None:
+            ndf.ndf_pearson_column(ctx, c, fid, out_r)
+        if i is not None:
+            ev[i][1].record(stream)
+        if fid is not None:
+            ndf.ndf_mi_ksg_column(ctx, c, fid, K_NN, out_mi)
+        if i is not None:
+            ev[i][2].record(stream)
+
+    def step(ref):
+        with torch.cuda.stream(stream):
+            slab_step(ref, plane, bounds, rank, column_of, bc, compute)
+
+    for i in range(args.warmup):
+        step(refs[i])
+    ndf.ndf_synchronize(ctx)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    launches0 = ndf.ndf_launch_count(ctx)
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for i in range(args.steps):
+            cur["i"] = i
+            step(refs[args.warmup + i])
+        cur["i"] = None
+        t_end.record(stream)
+        barrier()
+    launches = ndf.ndf_launch_count(ctx) - launches0
+    total_ms = t_start.elapsed_time(t_end)
+    pearson_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
+    ksg_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
+    total_ms, pearson_ms, ksg_ms = max_over_ranks([total_ms, pearson_ms, ksg_ms], world, "cuda")
+    ms_per_volume = total_ms / args.steps  # every step is one volume of the whole job
+
+    # end to end: each rank uploads its slab from pinned host memory, then the
+    # column exchange and both slab volumes into pinned host buffers
+    host_r = torch.empty(max(Ns, 1), dtype=torch.float32, pin_memory=True)
+    host_mi = torch.empty(max(Ns, 1), dtype=torch.float32, pin_memory=True)
+    e2e_steps = max(1, min(args.e2e_steps, args.steps))
+
+    def e2e_volume(ref):
+        nonlocal fid
+        fid_keep = fid
+        fid = ndf.ndf_load_ensemble(ctx, slab_t, M, Zs, Y, X) if Zs else None
+
+        def compute_host(c):
+            if fid is not None:
+                ndf.ndf_pearson_column(ctx, c, fid, host_r)
+                ndf.ndf_mi_ksg_column(ctx, c, fid, K_NN, host_mi)
+        with torch.cuda.stream(stream):
+            slab_step(ref, plane, bounds, rank, column_of, bc, compute_host)
+        if fid is not None:
+            ndf.ndf_free_ensemble(ctx, fid)
+        fid = fid_keep
+
+    e2e_volume(refs[0])
+    barrier()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        e2e_volume(refs[args.warmup + i])
+    barrier()
+    e2e_ms = max_over_ranks([(time.perf_counter() - t0) * 1e3], world, "cuda")[0] / e2e_steps
+
+    peaks = load_peaks()
+    sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    peak = sms * 64 / 2 * peaks["sm_max_mhz"] * 1e6 / 1e9
+    rank_evals = float(max(b[1] - b[0] for b in bounds) * plane) * M * (M - 1)
+    achieved = rank_evals / (ksg_ms * 1e-3) / 1e9
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": ms_per_volume, "unit": "ms", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_volume,
+            "higher_is_better": False, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": workload_name(recipe), "M": M, "grid_xyz": [X, Y, Z], "k": K_NN,
+                       "parallelism": f"zslabs{world}", "slabs_z": bounds,
+                       "exchange": "one M-float reference column per volume (NCCL broadcast)",
+                       "l2": "inputs larger than L2 (each slab read once per volume)"},
+            "pearson_ms": pearson_ms, "ksg_ms": ksg_ms, "mi_pairs_per_s": N / (ms_per_volume * 1e-3),
+            "ksg_search": args.ksg_search,
+            "roofline": {"bound": "alu", "kernel": KSG_SEARCHES[args.ksg_search][1],
+                         "achieved": achieved, "peak": peak, "unit": "Gdist/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_source": f"{peaks['source']} max SM clock",
+                         "algorithmic_evals_per_launch": rank_evals},
+            "e2e": {"value": e2e_ms, "unit": "ms", "call": "ndf_load_ensemble (slab) + "
+                    "ndf_field_column + broadcast + ndf_pearson_column + ndf_mi_ksg_column",
+                    "h2d_bytes_per_step": int(M * N * 4), "d2h_bytes_per_step": int(2 * N * 4)},
+            "gpu_launches": int(launches), "clocks": clk.summary(), "cpu_baseline": None,
+        }
+        print(json.dumps(line), flush=True)
+    if fid is not None:
+        ndf.ndf_free_ensemble(ctx, fid)
+    ndf.ndf_destroy(ctx)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
 def run_reference(args, recipe):
     rank = env_int("RANK", 0)
     if rank != 0:
@@ -541,6 +779,129 @@ def run_reference(args, recipe):
     return 0
 
 
+CASES = ("hash-decode", "dense-decode", "pearson-gemm", "ksg", "train-step")
+
+
+def run_case(args, recipe):
+    """One kernel path timed on its own (CUDA events around --repeat calls after
+    --warmup calls), for ncu captures and sweeps; prints one JSON line with the
+    case's figures.  Not the benchmark line.
+
+      hash-decode   the paper's NDF architecture (seeded parameters, non-zero output
+                    layer) decoded over the workload's grid, --decode-mode tc|cached|fp32,
+                    --case-refs references per call
+      dense-decode  the dense-grid NDF (seeded initialisation) decoded on tcgen05,
+                    --case-refs references per call
+      pearson-gemm  batched Pearson of --case-refs references on the loaded workload
+                    (--precision tf32|bf16x3|fp32)
+      ksg           one KSG volume (k = 8) of the loaded workload, --ksg-search
+      train-step    dense-NDF Adam steps at batch --case-batch (seeded pairs)
+    """
+    import torch
+
+    import synth
+    from paper_2307_02203_gb300 import build
+    build.build()
+    from paper_2307_02203_gb300 import ndf
+
+    X, Y, Z, N = recipe.X, recipe.Y, recipe.Z, recipe.N
+    stream = torch.cuda.Stream()
+    ctx = ndf.ndf_create(0, stream.cuda_stream)
+    R = max(1, args.case_refs)
+    rng = np.random.default_rng(2)
+    fid = None
+    if args.case in ("pearson-gemm", "ksg"):
+        synth.build()
+        field = synth.generate(recipe)
+        fid = ndf.ndf_load_ensemble(ctx, field, recipe.M, Z, Y, X)
+        del field
+    out = torch.empty((R, N), dtype=torch.float32, device="cuda")
+    info = {}
+    free = []
+    if args.case == "hash-decode":
+        arch = ndf.ndf_hash_arch_default()
+        m = ndf.ndf_hash_model_create(ctx, arch, ndf.NDF_MEASURE_PEARSON, False, 1, X, Y, Z)
+        p = np.empty(ndf.ndf_hash_model_param_count(m), np.float32)
+        ndf.ndf_hash_model_get_params(m, p)
+        p[-129:-1] = np.random.default_rng(1).uniform(-0.3, 0.3, 128)  # output layer (0 at init)
+        ndf.ndf_hash_model_set_params(m, p)
+        mode = {"tc": (ndf.NDF_HASH_DECODE_TC, False), "cached": (ndf.NDF_HASH_DECODE_TC, True),
+                "fp32": (ndf.NDF_HASH_DECODE_FP32, False)}[args.decode_mode]
+        ndf.ndf_hash_set_decode(m, *mode)
+        free.append(lambda: ndf.ndf_hash_model_free(m))
+        info["decode_mode"] = args.decode_mode
+
+        def call():
+            refs = [int(r) for r in rng.integers(0, N, size=R)]
+            if R == 1:
+                ndf.ndf_hash_infer(m, refs[0], out[0])
+            else:
+                ndf.ndf_hash_infer_batch(m, refs, out)
+    elif args.case == "dense-decode":
+        res = [int(v) for v in args.ndf_res.split(",")]
+        m = ndf.ndf_model_create(ctx, res, ndf.NDF_MEASURE_PEARSON, 1, X, Y, Z)
+        free.append(lambda: ndf.ndf_model_free(m))
+
+        def call():
+            refs = [int(r) for r in rng.integers(0, N, size=R)]
+            if R == 1:
+                ndf.ndf_infer(m, refs[0], out[0])
+            else:
+                ndf.ndf_infer_batch(m, refs, out)
+    elif args.case == "pearson-gemm":
+        prec = {"tf32": ndf.NDF_PREC_TF32, "bf16x3": ndf.NDF_PREC_BF16X3,
+                "fp32": ndf.NDF_PREC_FP32}[args.precision]
+        info["precision"] = args.precision
+        refs = [int(r) for r in rng.integers(0, N, size=R)]
+
+        def call():
+            ndf.ndf_pearson_batch(ctx, fid, fid, refs, prec, out)
+    elif args.case == "ksg":
+        ndf.ndf_set_ksg_algorithm(ctx, getattr(ndf, KSG_SEARCHES[args.ksg_search][0]))
+        if args.ksg_schedule:
+            ndf.ndf_ksg_set_schedule(ctx, *args.ksg_schedule)
+            info["schedule"] = args.ksg_schedule
+        info["search"] = args.ksg_search
+
+        def call():
+            ndf.ndf_mi_ksg(ctx, fid, fid, int(rng.integers(0, N)), K_NN, out[0])
+    else:  # train-step
+        res = [int(v) for v in args.ndf_res.split(",")]
+        m = ndf.ndf_model_create(ctx, res, ndf.NDF_MEASURE_PEARSON, 1, X, Y, Z)
+        free.append(lambda: ndf.ndf_model_free(m))
+        B = args.case_batch
+        pr = torch.rand((B, 3), device="cuda") * 2 - 1
+        pq = torch.rand((B, 3), device="cuda") * 2 - 1
+        tgt = torch.rand(B, device="cuda") * 2 - 1
+        info["batch"] = B
+        R = 1
+
+        def call():
+            ndf.ndf_model_step(m, pr, pq, tgt, 3e-4, True)
+
+    for _ in range(args.warmup):
+        call()
+    ndf.ndf_synchronize(ctx)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.repeat):
+        call()
+    e1.record(stream)
+    ndf.ndf_synchronize(ctx)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.repeat
+    line = {"case": args.case, "workload": workload_name(recipe), "grid_xyz": [X, Y, Z],
+            "refs_per_call": R, "ms_per_call": ms, "ms_per_volume": ms / R, **info}
+    print(json.dumps(line), flush=True)
+    for fn in free:
+        fn()
+    if fid is not None:
+        ndf.ndf_free_ensemble(ctx, fid)
+    ndf.ndf_destroy(ctx)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -549,9 +910,11 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-grid", type=int, default=1,
+                    help="also time the oracle on one core and on the tiny workload")
     ap.add_argument("--batch", type=int, default=1, help="also time 64-reference Pearson GEMMs")
     ap.add_argument("--ksg-batch", type=int, default=1, help="also time a 16-reference KSG launch")
-    ap.add_argument("--ksg-search", choices=["pruned", "block"], default="block",
+    ap.add_argument("--ksg-search", choices=sorted(KSG_SEARCHES), default="lanes",
                     help="exact KSG search of the timed step")
     ap.add_argument("--brute-steps", type=int, default=1,
                     help="volumes timed with the brute-force KSG search (same results)")
@@ -571,6 +934,23 @@ def main():
     ap.add_argument("--workload", choices=["csens", "csens-slab", "tiny"], default="csens",
                     help="csens: 250x352x20, M=1000 (the benchmark); csens-slab: one vertical "
                          "level of it (profiling); tiny: 16x16x4, M=100 (checks)")
+    ap.add_argument("--ksg-schedule", type=int, nargs=2, default=None, metavar=("SWITCH_MIN", "EVERY"),
+                    help="lane-refill search schedule (default: the library's or the autotuner's)")
+    ap.add_argument("--parallel", choices=["replicas", "slabs"], default=None,
+                    help="several GPUs: replicas (every rank its own references on its own copy, "
+                         "weak scaling) or slabs (the grid split into z-slabs, one reference "
+                         "column broadcast per volume, strong scaling; the default for N > 1)")
+    ap.add_argument("--case", choices=CASES, default=None,
+                    help="time one kernel path on its own (profiling; prints its own JSON line)")
+    ap.add_argument("--case-refs", type=int, default=1, help="--case: references per call")
+    ap.add_argument("--case-batch", type=int, default=1 << 18, help="--case train-step: batch")
+    ap.add_argument("--repeat", type=int, default=10, help="--case: timed calls")
+    ap.add_argument("--decode-mode", choices=["tc", "cached", "fp32"], default="tc",
+                    help="--case hash-decode: decoder")
+    ap.add_argument("--precision", choices=["tf32", "bf16x3", "fp32"], default="tf32",
+                    help="--case pearson-gemm: precision")
+    ap.add_argument("--grid", type=int, nargs=3, default=None, metavar=("X", "Y", "Z"),
+                    help="--case: grid of the decode cases (default: the workload's)")
     args = ap.parse_args()
 
     import synth
@@ -582,6 +962,10 @@ def main():
         METRIC = f"ms per {recipe.N}-voxel dependence volume (Pearson + KSG MI k=8, M={recipe.M})"
     if args.impl == "reference":
         return run_reference(args, recipe)
+    if args.case:
+        if args.grid:
+            recipe = synth.scaled(recipe, X=args.grid[0], Y=args.grid[1], Z=args.grid[2])
+        return run_case(args, recipe)
 
     import torch
     import torch.distributed as dist
@@ -589,11 +973,16 @@ def main():
     world = env_int("WORLD_SIZE", 1)
     rank = env_int("RANK", 0)
     local_rank = env_int("LOCAL_RANK", 0)
+    if args.parallel is None:
+        args.parallel = "slabs" if world > 1 else "replicas"
     if world > 1:
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local_rank)
     build_everything()
     from paper_2307_02203_gb300 import ndf
+
+    if args.parallel == "slabs":
+        return run_slabs(args, recipe, world, rank, local_rank)
 
     nthreads = max(1, (os.cpu_count() or 1) // max(1, env_int("LOCAL_WORLD_SIZE", world)))
     field_t, field = make_field(recipe, pinned=True, nthreads=nthreads)
@@ -666,8 +1055,9 @@ def main():
         return b0.elapsed_time(b1) / nb
 
     ksg_brute_ms = time_search(ndf.NDF_KSG_BRUTE)
-    other = "pruned" if args.ksg_search == "block" else "block"
-    ksg_other_ms = time_search(getattr(ndf, KSG_SEARCHES[other][0]))
+    others = {name: {"kernel": KSG_SEARCHES[name][1],
+                     "ms": time_search(getattr(ndf, KSG_SEARCHES[name][0]))}
+              for name in sorted(KSG_SEARCHES) if name != args.ksg_search}
     ndf.ndf_set_ksg_algorithm(ctx, search, False)
     # ---- batched KSG: 16 references in one launch
     ksg_batch = measure_ksg_batch(ndf, ctx, fid, recipe, stream, args) if args.ksg_batch else None
@@ -747,6 +1137,8 @@ def main():
         clocks = clk.summary()
         cpu = cpu_baseline(field, recipe, refs[args.warmup], args.cpu_seconds, seed=7) \
             if world == 1 else None
+        if cpu is not None and args.cpu_grid:
+            cpu["grid"] = cpu_baseline_grid(field, recipe, refs[args.warmup], args.cpu_seconds)
         result = {
             "metric": METRIC, "value": ms_per_volume, "unit": "ms", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -774,8 +1166,7 @@ def main():
                                              "traffic": KSG_BRUTE_TRAFFIC_PER_VOLUME,
                                              "evals_per_volume": brute_evals},
                                 "speedup_of_timed_search": ksg_brute_ms / ksg_ms},
-            "ksg_other_search": {"search": other, "kernel": KSG_SEARCHES[other][1],
-                                 "ms": ksg_other_ms},
+            "ksg_other_searches": others,
             "ksg_batch16": ksg_batch,
             "e2e": {"value": e2e_per_volume, "unit": "ms", "call": "ndf_load_and_compute",
                     "sequential_calls_ms": e2e_sequential,

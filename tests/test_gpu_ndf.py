@@ -211,6 +211,38 @@ def test_training_reduces_error(ndf_mod, ctx):
     ndf_mod.ndf_free_ensemble(ctx, fid)
 
 
+def test_mi_training_beats_constant(ndf_mod, ctx):
+    """The same for the MI network (KSG targets, k = 4, softplus output): the
+    decoded MI volumes must beat the best constant volume, i.e. the network gains
+    over the method without it (which has only a constant to offer in between
+    exact volumes)."""
+    field = synth.generate(synth.TINY)
+    M, Z, Y, X = field.shape
+    N = Z * Y * X
+    fid = ndf_mod.ndf_load_ensemble(ctx, field, M, Z, Y, X)
+    cfg = ndf_mod.ndf_train_cfg_default()
+    cfg.res[:] = [4, 8, 16, 16]
+    cfg.n_triples = 1 << 18
+    cfg.batch = 1 << 13
+    cfg.refs_per_group = 64
+    cfg.queries_per_group = 1024
+    cfg.max_passes = 30
+    cfg.lr = 3e-3
+    model = ndf_mod.ndf_train(ctx, fid, fid, ndf_mod.NDF_MEASURE_MI_KSG, 4, cfg)
+    info = ndf_mod.ndf_model_info(model)
+    assert info["passes"] >= 1 and np.isfinite(info["last_loss"])
+    refs = synth.sample_vertices(synth.TINY, 16, seed=3)
+    dec = np.empty((len(refs), N), dtype=np.float32)
+    ndf_mod.ndf_infer_batch(model, refs, dec)
+    exact = np.stack([oracle.ksg_volume(field, field, int(r), 4) for r in refs])
+    mae = np.abs(dec - exact).mean()
+    const = np.abs(exact - np.median(exact)).mean()
+    print(f"NDF MI MAE {mae:.4f} vs best-constant MAE {const:.4f}")
+    assert mae < 0.75 * const
+    ndf_mod.ndf_model_free(model)
+    ndf_mod.ndf_free_ensemble(ctx, fid)
+
+
 def test_cross_field_training(ndf_mod, ctx):
     """A network for the dependence between field A at the reference and field B
     at every vertex (B shares latent modes with A at 0.6): decoded A->B Pearson
