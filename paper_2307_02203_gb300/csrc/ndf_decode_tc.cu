@@ -1,22 +1,29 @@
 // Neural dependence field volume decoding (Sec. 5) on the 5th-generation tensor
-// cores.
+// cores, R references per launch.
 //
-// For one reference, every query vertex v needs
-//   h1 = ReLU(W1f f(v) + b1f)         (first layer with the reference folded in)
-//   h2 = ReLU(W2 h1 + b2), h3 = ReLU(W3 h2 + b3), y = act(w4 . h3 + b4).
-// A CTA decodes 128-vertex tiles (the MMA M dimension) in two slots so that the
-// encoding / epilogue work of one tile overlaps the MMAs of the other:
+// For reference r and query vertex v the network computes
+//   x  = [f(p_r) * f(v) ; f(p_r) + f(v)]          (the merge, rounded to BF16)
+//   h1 = ReLU(W1 x + b1), h2 = ReLU(W2 h1 + b2), h3 = ReLU(W3 h2 + b3),
+//   y  = act(w4 . h3 + b4)
+// -- the arithmetic of the training forward.  The reference enters only through
+// the layer-1 operand x, so W1, W2 and W3 are the same for every reference and
+// stay in shared memory for the launch, and the query encoding f(v) (the grid
+// gathers, most of a vertex's cost) is computed once per vertex for all R
+// references of the launch.
+//
+// A persistent CTA per SM decodes 128-vertex tiles (the MMA M dimension) in two
+// slots so that one slot's epilogue overlaps the other slot's MMAs:
 //   warps 0-3 (slot 0) and 4-7 (slot 1): thread i of a slot owns row i of the tile
-//     and TMEM lane i.  It gathers and interpolates its vertex's 64 grid features
-//     and writes them as BF16 into the slot's A tile in the 128-byte-swizzled
-//     K-major layout the MMA reads; after each layer it loads its row of the FP32
-//     accumulator with tcgen05.ld, adds the bias, applies ReLU and writes the next
-//     layer's A tile (or, after layer 3, the output).
+//     and TMEM lane i.  It encodes its vertex once per tile (64 FP32 features kept
+//     in registers); then for each reference it writes x into the slot's A operand
+//     (BF16, 128-byte-swizzled K-major), and after each layer loads its row of the
+//     FP32 accumulator with tcgen05.ld, adds the bias, applies ReLU and writes the
+//     next layer's operand over the same buffer (the MMA that read it has
+//     completed), or after layer 3 the output.
 //   warp 8: allocates TMEM (2 slots x 128 columns); one lane issues tcgen05.mma
-//     (M = 128, N = 128, K = 64 / 128 / 128) for whichever slot is ready and
-//     commits to that slot's mbarrier.
-// Weights (folded W1 of the reference, W2, W3) sit in shared memory in the same
-// swizzled K-major layout for the whole launch.
+//     (M = 128, N = 128, K = 128) for whichever slot is ready and commits to that
+//     slot's mbarrier.
+// The references' features f(p_r) (FP32) and the biases sit in shared memory.
 #include <cuda_bf16.h>
 
 #include "ndf_net.h"
@@ -84,49 +91,61 @@ __device__ __forceinline__ float pos_axis(int64_t i, int64_t n) {
 
 struct TcInferArgs {
     TcGrid G;
-    const __nv_bfloat16* w1f;  // [R][128][64] folded first layer per reference
-    const float* b1f;          // [R][128]
-    const __nv_bfloat16* w2;   // [128][128] ([out][in])
-    const __nv_bfloat16* w3;
+    const int64_t* refs;       // [R] reference vertices
+    int R;
+    const __nv_bfloat16* w;    // [3][128][128] W1..W3 ([out][in])
     const float* params;
-    int64_t offb2, offb3, offw4, offb4;
+    int64_t offb1, offb2, offb3, offw4, offb4;
     int64_t N, X, Y, Z;
     int measure;
     float* out;                // [R][N]
     unsigned* status;
 };
 
-// shared memory: W1f (1 atom), W2 (2 atoms), W3 (2 atoms), per slot A1 (1 atom) + A23 (2 atoms)
-constexpr uint32_t kOffW1 = 0, kOffW2 = kAtom, kOffW3 = 3 * kAtom, kOffSlot = 5 * kAtom;
-constexpr uint32_t kSlotBytes = 3 * kAtom;
-constexpr uint32_t kTcSmem = 5 * kAtom + 2 * kSlotBytes + 1024 /*align*/ + 256 /*barriers*/;
+// shared memory: W1, W2, W3 (2 atoms each), one 2-atom operand buffer per slot,
+// then biases / output weights (4 x 128 FP32), the references' features [R][64]
+// FP32 and the barriers
+constexpr int kMaxRefsPerLaunch = 64;
+constexpr uint32_t kOffW = 0, kOffSlot = 6 * kAtom, kSlotBytes = 2 * kAtom;
+constexpr uint32_t kOffVec = kOffSlot + 2 * kSlotBytes;
+constexpr uint32_t kOffFr = kOffVec + 4 * kHid * 4;
+constexpr uint32_t kOffBar = kOffFr + kMaxRefsPerLaunch * kLF * 4;
+constexpr uint32_t kTcSmem = kOffBar + 256 /*barriers*/ + 1024 /*align*/;
 
 __global__ void __launch_bounds__(kTcThreads, 1) infer_tc_kernel(const TcInferArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 5 * kAtom + 2 * kSlotBytes);
+    float* vec = reinterpret_cast<float*>(smem + kOffVec);  // b1, b2, b3, w4
+    float* fr_all = reinterpret_cast<float*>(smem + kOffFr);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kOffBar);
     uint64_t* a_ready = bars;      // [2] epilogue -> MMA (128 arrivals)
     uint64_t* d_ready = bars + 2;  // [2] MMA -> epilogue (commit)
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int r = blockIdx.y;
+    const int R = a.R;
 
-    // ---- weights into the swizzled K-major layout (rows = output features)
-    {
-        const __nv_bfloat16* w1 = a.w1f + (int64_t)r * kHid * kLF;
-        for (int i = threadIdx.x; i < kHid * 8; i += blockDim.x) {  // W1f: 128 rows x 8 chunks
-            const int row = i >> 3, c = i & 7;
-            *reinterpret_cast<uint4*>(smem + kOffW1 + swz(row, c)) =
-                reinterpret_cast<const uint4*>(w1 + row * kLF)[c];
-        }
-        for (int i = threadIdx.x; i < kHid * 16; i += blockDim.x) {  // W2, W3: 2 atoms each
-            const int row = i >> 4, c = i & 15;
-            const uint32_t o = (uint32_t)(c >> 3) * kAtom + swz(row, c & 7);
-            *reinterpret_cast<uint4*>(smem + kOffW2 + o) = reinterpret_cast<const uint4*>(a.w2 + row * kHid)[c];
-            *reinterpret_cast<uint4*>(smem + kOffW3 + o) = reinterpret_cast<const uint4*>(a.w3 + row * kHid)[c];
-        }
+    // ---- weights into the swizzled K-major layout (rows = output features),
+    // biases and output weights, the references' features
+    for (int i = threadIdx.x; i < 3 * kHid * 16; i += blockDim.x) {  // 3 layers x 128 rows x 16 chunks
+        const int l = i / (kHid * 16), row = (i >> 4) % kHid, c = i & 15;
+        const uint32_t o = (uint32_t)(2 * l + (c >> 3)) * kAtom + swz(row, c & 7);
+        *reinterpret_cast<uint4*>(smem + kOffW + o) =
+            reinterpret_cast<const uint4*>(a.w + ((size_t)l * kHid + row) * kHid)[c];
+    }
+    for (int i = threadIdx.x; i < 4 * kHid; i += blockDim.x) {
+        const int64_t off = i < kHid ? a.offb1 : i < 2 * kHid ? a.offb2 : i < 3 * kHid ? a.offb3 : a.offw4;
+        vec[i] = a.params[off + (i % kHid)];
+    }
+    for (int i = threadIdx.x; i < R * kLevels; i += blockDim.x) {
+        const int64_t v = a.refs[i / kLevels];
+        const int64_t x = v % a.X, y = (v / a.X) % a.Y, z = v / (a.X * a.Y);
+        const float p[3] = {pos_axis(x, a.X), pos_axis(y, a.Y), pos_axis(z, a.Z)};
+        float f[kFeat];
+        encode_level(a.G, i % kLevels, p, f);
+#pragma unroll
+        for (int q = 0; q < kFeat; ++q) fr_all[(i / kLevels) * kLF + (i % kLevels) * kFeat + q] = f[q];
     }
     if (threadIdx.x == 0) {
         for (int s = 0; s < 2; ++s) {
@@ -155,41 +174,36 @@ __global__ void __launch_bounds__(kTcThreads, 1) infer_tc_kernel(const TcInferAr
 
     if (warp == 8) {
         if (lane == 0) {  // ---- MMA issuer: serve whichever slot is ready
-            int64_t tile[2] = {(int64_t)blockIdx.x * 2, (int64_t)blockIdx.x * 2 + 1};
+            // operands per slot: (its tiles) x R references x 3 layers
+            int64_t left[2];
+            for (int s = 0; s < 2; ++s) {
+                const int64_t t0 = (int64_t)blockIdx.x * 2 + s;
+                left[s] = t0 < tiles ? ((tiles - 1 - t0) / step + 1) * (int64_t)R * 3 : 0;
+            }
             int layer[2] = {0, 0};
             uint32_t na[2] = {0, 0};
-            const uint32_t sw1 = smem_u32(smem + kOffW1), sw2 = smem_u32(smem + kOffW2),
-                           sw3 = smem_u32(smem + kOffW3);
+            const uint32_t sw = smem_u32(smem + kOffW);
             uint32_t polls = 0;
             uint64_t t0 = 0;
-            while ((tile[0] < tiles || tile[1] < tiles) && !*abort_flag) {
+            while ((left[0] > 0 || left[1] > 0) && !*abort_flag) {
                 bool progressed = false;
                 for (int s = 0; s < 2; ++s) {
-                    if (tile[s] >= tiles || !try_wait(&a_ready[s], na[s] & 1u)) continue;
+                    if (left[s] == 0 || !try_wait(&a_ready[s], na[s] & 1u)) continue;
                     progressed = true;
                     ++na[s];
                     tc_fence_after();
                     const uint32_t sa = smem_u32(smem + kOffSlot + s * kSlotBytes);
+                    const uint32_t wl = sw + (uint32_t)(2 * layer[s]) * kAtom;
                     const uint32_t d = tmem + (uint32_t)(s * 128);
-                    if (layer[s] == 0) {  // K = 64: one atom, 4 steps of 16
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk)
-                            tc_mma(d, desc_sw128(sa) + (uint64_t)(kk * 2), desc_sw128(sw1) + (uint64_t)(kk * 2),
-                                   idesc, kk > 0 ? 1u : 0u);
-                    } else {  // K = 128: two atoms of A23 against W2 / W3
-                        const uint32_t a23 = sa + kAtom, w = layer[s] == 1 ? sw2 : sw3;
-#pragma unroll
-                        for (int kk = 0; kk < 8; ++kk) {
-                            const uint32_t at = (uint32_t)(kk >> 2) * kAtom;
-                            tc_mma(d, desc_sw128(a23 + at) + (uint64_t)((kk & 3) * 2),
-                                   desc_sw128(w + at) + (uint64_t)((kk & 3) * 2), idesc, kk > 0 ? 1u : 0u);
-                        }
+                    for (int kk = 0; kk < 8; ++kk) {  // K = 128: two atoms, 4 steps of 16 each
+                        const uint32_t at = (uint32_t)(kk >> 2) * kAtom;
+                        tc_mma(d, desc_sw128(sa + at) + (uint64_t)((kk & 3) * 2),
+                               desc_sw128(wl + at) + (uint64_t)((kk & 3) * 2), idesc, kk > 0 ? 1u : 0u);
                     }
                     tc_commit(&d_ready[s]);
-                    if (++layer[s] == 3) {
-                        layer[s] = 0;
-                        tile[s] += step;
-                    }
+                    layer[s] = layer[s] == 2 ? 0 : layer[s] + 1;
+                    --left[s];
                 }
                 if (progressed) {
                     polls = 0;
@@ -206,74 +220,83 @@ __global__ void __launch_bounds__(kTcThreads, 1) infer_tc_kernel(const TcInferAr
     } else {  // ---- encode / epilogue: slot s, row i = TMEM lane i
         const int s = warp >> 2;
         const int i = (warp & 3) * 32 + lane;
-        unsigned char* A1 = smem + kOffSlot + s * kSlotBytes;
-        unsigned char* A23 = A1 + kAtom;
+        unsigned char* A = smem + kOffSlot + s * kSlotBytes;
         const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(s * 128);
-        const float* b1 = a.b1f + (int64_t)r * kHid;
-        const float* b2 = a.params + a.offb2;
-        const float* b3 = a.params + a.offb3;
-        const float* w4 = a.params + a.offw4;
         const float b4 = a.params[a.offb4];
-        float* out = a.out + (int64_t)r * a.N;
         uint32_t nd = 0;
         for (int64_t t = (int64_t)blockIdx.x * 2 + s; t < tiles; t += step) {
             const int64_t v = t * kTile + i;
-            // encode this row's vertex into A1 (rows past N encode position 0: harmless, unused)
-            float p[3];
+            // this row's vertex, encoded once for every reference (rows past N encode
+            // position 0: harmless, never written out)
+            float fq[kLF];
             {
                 const int64_t vv = v < a.N ? v : 0;
                 const int64_t x = vv % a.X, y = (vv / a.X) % a.Y, z = vv / (a.X * a.Y);
-                p[0] = pos_axis(x, a.X);
-                p[1] = pos_axis(y, a.Y);
-                p[2] = pos_axis(z, a.Z);
+                const float p[3] = {pos_axis(x, a.X), pos_axis(y, a.Y), pos_axis(z, a.Z)};
+#pragma unroll
+                for (int l = 0; l < kLevels; ++l) {
+                    float f[kFeat];
+                    encode_level(a.G, l, p, f);
+#pragma unroll
+                    for (int q = 0; q < kFeat; ++q) fq[l * kFeat + q] = f[q];
+                }
             }
+            for (int r = 0; r < R; ++r) {
+                const float* fr = fr_all + r * kLF;
+                // x = [fr * fq ; fr + fq]: 16-byte chunks 0-7 the products, 8-15 the sums
 #pragma unroll
-            for (int l = 0; l < kLevels; ++l) {
-                float f[kFeat];
-                encode_level(a.G, l, p, f);
-                *reinterpret_cast<uint4*>(A1 + swz(i, 2 * l)) =
-                    make_uint4(bf2(f[0], f[1]), bf2(f[2], f[3]), bf2(f[4], f[5]), bf2(f[6], f[7]));
-                *reinterpret_cast<uint4*>(A1 + swz(i, 2 * l + 1)) =
-                    make_uint4(bf2(f[8], f[9]), bf2(f[10], f[11]), bf2(f[12], f[13]), bf2(f[14], f[15]));
-            }
-            proxy_fence();
-            tc_fence_before();
-            arrive(&a_ready[s]);
-            for (int layer = 0; layer < 3; ++layer) {
-                if (!wait_bounded(&d_ready[s], nd & 1u, abort_flag)) goto done;
-                ++nd;
-                tc_fence_after();
-                const float* bias = layer == 0 ? b1 : (layer == 1 ? b2 : b3);
-                float acc = 0.0f;
+                for (int c = 0; c < 8; ++c) {
+                    const float4 r0 = *reinterpret_cast<const float4*>(fr + 8 * c);
+                    const float4 r1 = *reinterpret_cast<const float4*>(fr + 8 * c + 4);
+                    const float* q = fq + 8 * c;
+                    *reinterpret_cast<uint4*>(A + swz(i, c)) =
+                        make_uint4(bf2(r0.x * q[0], r0.y * q[1]), bf2(r0.z * q[2], r0.w * q[3]),
+                                   bf2(r1.x * q[4], r1.y * q[5]), bf2(r1.z * q[6], r1.w * q[7]));
+                    *reinterpret_cast<uint4*>(A + kAtom + swz(i, c)) =
+                        make_uint4(bf2(r0.x + q[0], r0.y + q[1]), bf2(r0.z + q[2], r0.w + q[3]),
+                                   bf2(r1.x + q[4], r1.y + q[5]), bf2(r1.z + q[6], r1.w + q[7]));
+                }
+                proxy_fence();
+                tc_fence_before();
+                arrive(&a_ready[s]);
+                for (int layer = 0; layer < 3; ++layer) {
+                    if (!wait_bounded(&d_ready[s], nd & 1u, abort_flag)) goto done;
+                    ++nd;
+                    tc_fence_after();
+                    const float* bias = vec + layer * kHid;
+                    float acc = 0.0f;
 #pragma unroll
-                for (int c0 = 0; c0 < kHid; c0 += 32) {
-                    float h[32];
-                    tmem_ld32(taddr + (uint32_t)c0, h);
+                    for (int c0 = 0; c0 < kHid; c0 += 32) {
+                        float h[32];
+                        tmem_ld32(taddr + (uint32_t)c0, h);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) h[j] = fmaxf(h[j] + bias[c0 + j], 0.0f);
-                    if (layer < 2) {  // next layer's A: columns c0..c0+31 = chunks c0/8 ..
+                        for (int j = 0; j < 32; ++j) h[j] = fmaxf(h[j] + bias[c0 + j], 0.0f);
+                        if (layer < 2) {  // next layer's operand: columns c0..c0+31
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int c = (c0 >> 3) + q;  // 16-byte chunk of the 256-byte row
-                            *reinterpret_cast<uint4*>(A23 + (uint32_t)(c >> 3) * kAtom + swz(i, c & 7)) =
-                                make_uint4(bf2(h[8 * q], h[8 * q + 1]), bf2(h[8 * q + 2], h[8 * q + 3]),
-                                           bf2(h[8 * q + 4], h[8 * q + 5]), bf2(h[8 * q + 6], h[8 * q + 7]));
-                        }
-                    } else {  // output layer on the BF16-rounded h3
+                            for (int q = 0; q < 4; ++q) {
+                                const int c = (c0 >> 3) + q;  // 16-byte chunk of the 256-byte row
+                                *reinterpret_cast<uint4*>(A + (uint32_t)(c >> 3) * kAtom + swz(i, c & 7)) =
+                                    make_uint4(bf2(h[8 * q], h[8 * q + 1]), bf2(h[8 * q + 2], h[8 * q + 3]),
+                                               bf2(h[8 * q + 4], h[8 * q + 5]), bf2(h[8 * q + 6], h[8 * q + 7]));
+                            }
+                        } else {  // output layer on the BF16-rounded h3
 #pragma unroll
-                        for (int j = 0; j < 32; j += 2) {
-                            const float2 hv = unbf2(bf2(h[j], h[j + 1]));
-                            acc = fmaf(w4[c0 + j], hv.x, fmaf(w4[c0 + j + 1], hv.y, acc));
+                            for (int j = 0; j < 32; j += 2) {
+                                const float2 hv = unbf2(bf2(h[j], h[j + 1]));
+                                acc = fmaf(vec[3 * kHid + c0 + j], hv.x,
+                                           fmaf(vec[3 * kHid + c0 + j + 1], hv.y, acc));
+                            }
                         }
                     }
-                }
-                if (layer < 2) {
-                    proxy_fence();
-                    tc_fence_before();
-                    arrive(&a_ready[s]);
-                } else {
-                    const float o = acc + b4;
-                    if (v < a.N) out[v] = a.measure == 0 ? tanhf(o) : (o > 20.f ? o : log1pf(expf(o)));
+                    if (layer < 2) {
+                        proxy_fence();
+                        tc_fence_before();
+                        arrive(&a_ready[s]);
+                    } else if (v < a.N) {
+                        const float o = acc + b4;
+                        a.out[(int64_t)r * a.N + v] =
+                            a.measure == 0 ? tanhf(o) : (o > 20.f ? o : log1pf(expf(o)));
+                    }
                 }
             }
         }
@@ -289,7 +312,7 @@ done:
     }
 }
 
-cudaError_t launch_infer_tc(ndf_model* m, int R, float* out) {
+cudaError_t launch_infer_tc(ndf_model* m, const int64_t* d_refs, int R, float* out) {
     ndf_ctx* ctx = m->ctx;
     static bool attr = false;
     if (!attr) {
@@ -304,11 +327,9 @@ cudaError_t launch_infer_tc(ndf_model* m, int R, float* out) {
         a.G.res[l] = m->L.res[l];
         a.G.off[l] = m->L.grid_off[l];
     }
-    a.w1f = m->w1f;
-    a.b1f = m->b1f;
-    a.w2 = m->wbf + (size_t)kHid * kHid;
-    a.w3 = m->wbf + (size_t)2 * kHid * kHid;
+    a.w = m->wbf;
     a.params = m->params;
+    a.offb1 = m->L.b1;
     a.offb2 = m->L.b2;
     a.offb3 = m->L.b3;
     a.offw4 = m->L.w4;
@@ -318,16 +339,21 @@ cudaError_t launch_infer_tc(ndf_model* m, int R, float* out) {
     a.Y = m->Y;
     a.Z = m->Z;
     a.measure = m->measure;
-    a.out = out;
     a.status = ctx->flag.as<unsigned>() + 1;
     const int64_t tiles = (a.N + kTile - 1) / kTile;
-    int per_ref = (ctx->sm_count + R - 1) / R;
-    const int64_t need = (tiles + 1) / 2;
-    if (per_ref > need) per_ref = (int)need;
-    if (per_ref < 1) per_ref = 1;
-    infer_tc_kernel<<<dim3(per_ref, R), kTcThreads, kTcSmem, ctx->stream>>>(a);
-    ctx->launches++;
-    return cudaGetLastError();
+    int64_t grid = ctx->sm_count;  // one persistent CTA per SM, two tiles in flight each
+    if (grid > (tiles + 1) / 2) grid = (tiles + 1) / 2;
+    if (grid < 1) grid = 1;
+    for (int r0 = 0; r0 < R; r0 += kMaxRefsPerLaunch) {
+        a.refs = d_refs + r0;
+        a.R = R - r0 < kMaxRefsPerLaunch ? R - r0 : kMaxRefsPerLaunch;
+        a.out = out + (int64_t)r0 * a.N;
+        infer_tc_kernel<<<(unsigned)grid, kTcThreads, kTcSmem, ctx->stream>>>(a);
+        ctx->launches++;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace ndf

@@ -677,7 +677,7 @@ ndf_status model_alloc(ndf_ctx* ctx, const int res[kLevels], int measure, int64_
 
 void model_free(ndf_model* m) {
     if (!m) return;
-    void* ps[] = {m->params, m->grad, m->m, m->v, m->grid_bf, m->wbf, m->wtbf, m->w1f, m->b1f};
+    void* ps[] = {m->params, m->grad, m->m, m->v, m->grid_bf, m->wbf, m->wtbf};
     for (void* q : ps)
         if (q) cudaFree(q);
     m->work.release();

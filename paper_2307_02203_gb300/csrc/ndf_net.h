@@ -63,10 +63,6 @@ struct ndf_model {
     __nv_bfloat16* wtbf = nullptr;     // [3][128][128] bf16 transposes ([in][out])
     int64_t t = 0;             // Adam steps taken
     ndf::NetWork work;
-    // inference scratch: folded first layer for one reference
-    __nv_bfloat16* w1f = nullptr;  // [R][128][64]
-    float* b1f = nullptr;          // [R][128]
-    int64_t infer_cap = 0;
     // training record
     double last_loss = 0.0;
     int passes = 0;
@@ -93,7 +89,7 @@ cudaError_t model_forward(ndf_model* m, const float* pr, const float* pq, int64_
 
 // Volume decoding for R references (vertex ids on the device): out[R][N].
 cudaError_t model_infer(ndf_model* m, const int64_t* d_refs, int R, float* out);
-// tcgen05 decoding kernel (needs m->w1f / m->b1f folded for the R references)
-cudaError_t launch_infer_tc(ndf_model* m, int R, float* out);
+// tcgen05 decoding of R references (vertex ids on the device): out[R][N]
+cudaError_t launch_infer_tc(ndf_model* m, const int64_t* d_refs, int R, float* out);
 
 }  // namespace ndf

@@ -11,11 +11,9 @@
 // every pass, Adam, L1 loss, learning rate x0.1 after `patience` passes without
 // improvement of the pass loss (Sec. 4.3), stopping after `max_decays` decays or
 // `max_passes` passes.
-// Decoding: the reference half of the merged input is folded into the first
-// layer once per reference,
-//   W1 [f_r*f_q ; f_r+f_q] + b1 = (W1a diag(f_r) + W1b) f_q + (W1b f_r + b1),
-// so each query vertex needs only its own encoding and a 64-input first layer
-// (the tensor-core decoding kernel is in ndf_decode_tc.cu).
+// Decoding: the tensor-core kernel of ndf_decode_tc.cu, which encodes every
+// query vertex once per launch and forms the merged input [f_r*f_q ; f_r+f_q]
+// for each reference of the launch in its layer-1 operand.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -223,118 +221,39 @@ cudaError_t sample_triples_dev(ndf_ctx* ctx, const Field& rf, const Field& qf, i
     return e;
 }
 
-// ---------------------------------------------------------------- decoding (Sec. 5)
-
-struct GridArgs {
-    const __nv_bfloat16* grid;
-    int res[kLevels];
-    int64_t off[kLevels];
-};
-
-__device__ __forceinline__ float2 bf2f2(uint32_t u) {
-    __nv_bfloat162 v = *reinterpret_cast<__nv_bfloat162*>(&u);
-    return __bfloat1622float2(v);
-}
-
-__device__ __forceinline__ uint32_t f2bf2(float lo, float hi) {
-    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<uint32_t*>(&v);
-}
-
-template <int L>
-__device__ __forceinline__ void encode_level_t(const GridArgs& G, const float* p, float (&out)[kFeat]) {
-    const int R = G.res[L];
-    int i[3];
-    float f[3];
+// Sum of the training targets (FP64, one atomic per block), for the MI network's
+// initial output bias.
+__global__ void __launch_bounds__(256) target_sum_kernel(const float* __restrict__ t, int64_t n,
+                                                         double* __restrict__ sum) {
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        s += (double)t[i];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        float u = (p[a] + 1.0f) * 0.5f * (float)(R - 1);
-        int k = (int)floorf(u);
-        k = k < 0 ? 0 : (k > R - 2 ? R - 2 : k);
-        i[a] = k;
-        f[a] = u - (float)k;
-    }
-#pragma unroll
-    for (int q = 0; q < kFeat; ++q) out[q] = 0.0f;
-    const uint4* base = reinterpret_cast<const uint4*>(G.grid + G.off[L]);
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
-        const int64_t idx = ((int64_t)(i[2] + dz) * R + (i[1] + dy)) * R + (i[0] + dx);
-        const float w = (dx ? f[0] : 1.0f - f[0]) * (dy ? f[1] : 1.0f - f[1]) * (dz ? f[2] : 1.0f - f[2]);
-        const uint4 u0 = __ldg(base + idx * 2), u1 = __ldg(base + idx * 2 + 1);
-        const uint32_t uu[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const float2 v = bf2f2(uu[j]);
-            out[2 * j] = fmaf(w, v.x, out[2 * j]);
-            out[2 * j + 1] = fmaf(w, v.y, out[2 * j + 1]);
-        }
-    }
-}
-
-__device__ __forceinline__ void encode_level_any(const GridArgs& G, int l, const float* p,
-                                                 float (&out)[kFeat]) {
-    switch (l) {
-        case 0: encode_level_t<0>(G, p, out); break;
-        case 1: encode_level_t<1>(G, p, out); break;
-        case 2: encode_level_t<2>(G, p, out); break;
-        default: encode_level_t<3>(G, p, out); break;
-    }
-}
-
-// one CTA (128 threads) per reference: f_ref, then the folded first layer
-__global__ void __launch_bounds__(128)
-    infer_fold_kernel(GridArgs G, const float* __restrict__ params, int64_t offW1, int64_t offb1,
-                      const int64_t* __restrict__ refs, int64_t X, int64_t Y, int64_t Z,
-                      __nv_bfloat16* __restrict__ w1f, float* __restrict__ b1f) {
-    __shared__ float fr[kLF];
-    const int r = blockIdx.x;
-    if (threadIdx.x < kLevels) {
-        float p[3];
-        vertex_pos(refs[r], X, Y, Z, p);
-        float f[kFeat];
-        encode_level_any(G, threadIdx.x, p, f);
-#pragma unroll
-        for (int q = 0; q < kFeat; ++q) fr[threadIdx.x * kFeat + q] = f[q];
-    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ double part[8];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
     __syncthreads();
-    const int o = threadIdx.x;  // output row of the first layer
-    const float* W = params + offW1 + (int64_t)o * kIn;
-    float b = params[offb1 + o];
-    __nv_bfloat16* dst = w1f + ((int64_t)r * kHid + o) * kLF;
-    for (int f = 0; f < kLF; ++f) {
-        dst[f] = __float2bfloat16_rn(fmaf(W[f], fr[f], W[kLF + f]));
-        b = fmaf(W[kLF + f], fr[f], b);
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += part[w];
+        atomicAdd(sum, b);
     }
-    b1f[(int64_t)r * kHid + o] = b;
 }
 
+// b4 = softplus^-1(max(mean target, 1e-3)) = log(expm1(.)): the untrained MI network
+// then predicts about the mean target instead of softplus(0) = 0.69
+__global__ void softplus_bias_kernel(const double* __restrict__ sum, int64_t n, float* __restrict__ b4) {
+    const double mean = fmax(*sum / (double)n, 1e-3);
+    *b4 = (float)log(expm1(mean));
+}
+
+// ---------------------------------------------------------------- decoding (Sec. 5)
+// All R references in tcgen05 launches of up to 64 references each: every query
+// vertex is encoded once per launch, the references enter through the layer-1
+// operand (ndf_decode_tc.cu).
 cudaError_t model_infer(ndf_model* m, const int64_t* d_refs, int R, float* out) {
-    ndf_ctx* ctx = m->ctx;
-    if (m->infer_cap < R) {
-        if (m->w1f) cudaFree(m->w1f);
-        if (m->b1f) cudaFree(m->b1f);
-        m->w1f = nullptr;
-        m->b1f = nullptr;
-        m->infer_cap = 0;
-        cudaError_t e = cudaMalloc(&m->w1f, (size_t)R * kHid * kLF * 2);
-        if (e == cudaSuccess) e = cudaMalloc(&m->b1f, (size_t)R * kHid * 4);
-        if (e != cudaSuccess) return e;
-        m->infer_cap = R;
-    }
-    GridArgs G;
-    G.grid = m->grid_bf;
-    for (int l = 0; l < kLevels; ++l) {
-        G.res[l] = m->L.res[l];
-        G.off[l] = m->L.grid_off[l];
-    }
-    infer_fold_kernel<<<R, kHid, 0, ctx->stream>>>(G, m->params, m->L.W1, m->L.b1, d_refs, m->X,
-                                                   m->Y, m->Z, m->w1f, m->b1f);
-    ctx->launches++;
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    return launch_infer_tc(m, R, out);
+    return launch_infer_tc(m, d_refs, R, out);
 }
 
 }  // namespace ndf
@@ -729,6 +648,22 @@ ndf_status ndf_train(ndf_ctx* ctx, int ref_field, int query_field, int measure, 
     if (e != cudaSuccess) {
         cleanup_data();
         return bail(cuda_fail(ctx, e, "training-set generation"));
+    }
+    if (e == cudaSuccess && measure == NDF_MEASURE_MI_KSG) {
+        // the output bias from the first targets (on continuous samples: the first pass's)
+        double* dsum = reinterpret_cast<double*>(ctx->flag.as<unsigned char>() + 64);
+        e = cudaMemsetAsync(dsum, 0, sizeof(double), ctx->stream);
+        if (e == cudaSuccess) {
+            target_sum_kernel<<<ctx->sm_count * 4, 256, 0, ctx->stream>>>(tgt, T, dsum);
+            softplus_bias_kernel<<<1, 1, 0, ctx->stream>>>(dsum, T, m->params + m->L.b4);
+            ctx->launches += 2;
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) {
+            cleanup_data();
+            return bail(cuda_fail(ctx, e, "output bias"));
+        }
     }
     auto t1 = std::chrono::steady_clock::now();
     m->gen_seconds = std::chrono::duration<double>(t1 - t0).count();

@@ -112,8 +112,13 @@ def test_gradients_vs_fp64_oracle(ndf_mod, ctx, measure):
         rel_terms = np.linalg.norm(a - b) / max(np.linalg.norm(g_abs[sl]), 1e-30)
         print(f"measure {measure} {name}: |g|={np.linalg.norm(b):.3e} rel err {rel:.3e} "
               f"vs terms {rel_terms:.3e}")
+        # the bound: each per-sample gradient term passes through at most ~10 BF16
+        # roundings (relative 2^-9 each) on its longest path (grid features, the merge,
+        # three layers' weights and activations, forward and backward), so the error is
+        # at most 10 x 2^-9 ~ 2e-2 of the summed term magnitude; relative to the
+        # gradient's own norm it is that times the batch sum's cancellation, which is
+        # data-dependent and not gated separately
         assert rel_terms <= 2e-2, (name, rel_terms)
-        assert rel <= 0.15, (name, rel)
     ndf_mod.ndf_model_free(m)
 
 
