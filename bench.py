@@ -257,23 +257,52 @@ def measure_pearson_batch(ndf, ctx, fid, field, recipe, stream, rank, R=64, reps
     return res
 
 
-def measure_ksg_batch(ndf, ctx, fid, recipe, stream, args, R=16):
-    """R KSG volumes in one persistent launch (the timed search; one work counter over
-    all (reference, vertex) pairs)."""
+def error_refs(N, count, seed=777):
+    """The seeded reference vertices of the learned part's error statement."""
+    rng = np.random.default_rng(seed)
+    return [int(r) for r in rng.integers(0, N, size=count)]
+
+
+def measure_ksg_batch(ndf, ctx, fid, recipe, stream, refs, out):
+    """len(refs) KSG volumes (k = 8) in one persistent launch (the context's search;
+    one work counter over all (reference, vertex) pairs), first eagerly, then the
+    same launch captured in a CUDA graph on the context's stream and replayed (device-
+    resident reference indices, so the call enqueues no host copy).  out: [R][N]
+    device tensor; holds the replay's volumes afterwards."""
     import torch
 
     N = recipe.N
-    rng = np.random.default_rng(555)
-    refs = [int(r) for r in rng.integers(0, N, size=R)]
-    out = torch.empty((R, N), dtype=torch.float32, device="cuda")
+    R = len(refs)
+    d_refs = torch.tensor(refs, dtype=torch.int64, device="cuda")
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    ndf.ndf_synchronize(ctx)
     e0.record(stream)
-    ndf.ndf_mi_ksg_batch(ctx, fid, fid, refs, K_NN, out)
+    ndf.ndf_mi_ksg_batch(ctx, fid, fid, d_refs, K_NN, out)
     e1.record(stream)
     ndf.ndf_synchronize(ctx)
     ms = e0.elapsed_time(e1)
-    return {"refs": R, "ms": ms, "ms_per_volume": ms / R, "mi_pairs_per_s": R * N / (ms * 1e-3)}
+    res = {"refs": R, "ms": ms, "ms_per_volume": ms / R, "mi_pairs_per_s": R * N / (ms * 1e-3)}
+    eager = out[:2].clone()
+    try:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream, capture_error_mode="thread_local"):
+            ndf.ndf_mi_ksg_batch(ctx, fid, fid, d_refs, K_NN, out)
+        out[:2].fill_(float("nan"))
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            g.replay()
+            e1.record(stream)
+        ndf.ndf_synchronize(ctx)
+        torch.cuda.synchronize()
+        gms = e0.elapsed_time(e1)
+        res["graph"] = {"ms": gms, "ms_per_volume": gms / R,
+                        "equals_eager": bool(torch.equal(out[:2], eager))}
+        del g
+    except Exception as exc:  # noqa: BLE001 -- reported in the line, the eager figure stands
+        res["graph"] = {"error": str(exc)[:200]}
+    return res
 
 
 def measure_render(ndf, ctx, model, refs, recipe, stream, W=1024, H=1024):
@@ -451,19 +480,77 @@ def measure_hash_ndf(ndf, ctx, fid, recipe, stream, args, grid_only=False, n_fre
     return res
 
 
-def measure_ndf(ndf, ctx, fid, recipe, stream, args, exact_ms, fid_b=None):
-    """Learned part: trains a Pearson and a KSG-MI network on the loaded field
-    (targets from the GPU estimators), then times volume decoding (1 reference
-    per launch and 16 per launch) and states MAE / max error per volume against
-    the exact estimator, beside the exact method's time on the same GPU.  With a
-    second field, the same for cross-field networks (reference in field A, query
-    in field B)."""
+def error_statement(ndf, ctx, model, fa, fb, measure, refs, N, stream, cached=None, chunk=64):
+    """Decoded volumes of `model` for every reference in refs against the exact
+    estimator on the same GPU, in chunks of `chunk` references (the exact volumes of a
+    chunk from one batched call; `cached` may hold the first chunk's).  Decoding is
+    timed one reference per launch and 16 per launch.  Reports the MAE over all
+    vertices of all volumes, the max error per volume, and the MAE of the best
+    constant volume (the median of the exact values) beside it, both of the latter
+    from a seeded subsample of 2^18 values per chunk."""
     import torch
 
+    exact = torch.empty((chunk, N), dtype=torch.float32, device="cuda")
+    dec = torch.empty((chunk, N), dtype=torch.float32, device="cuda")
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(5)
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    for _ in range(3):  # warm-up of both decode paths
+        ndf.ndf_infer(model, refs[0], dec[0])
+        ndf.ndf_infer_batch(model, refs[:16], dec[:16])
+    ndf.ndf_synchronize(ctx)
+    abs_sum, n_vals, max_per_ref, ms_one, ms_16, samples = 0.0, 0, [], 0.0, 0.0, []
+    net_samples = []
+    for c0 in range(0, len(refs), chunk):
+        rs = refs[c0:c0 + chunk]
+        R = len(rs)
+        if cached is not None and c0 == 0:
+            exact[:R].copy_(cached[:R])
+        elif measure == ndf.NDF_MEASURE_PEARSON:
+            ndf.ndf_pearson_batch(ctx, fa, fb, rs, ndf.NDF_PREC_FP32, exact[:R])
+        else:
+            ndf.ndf_mi_ksg_batch(ctx, fa, fb, rs, K_NN, exact[:R])
+        ndf.ndf_synchronize(ctx)
+        e0.record(stream)
+        for i, r in enumerate(rs):
+            ndf.ndf_infer(model, r, dec[i])
+        e1.record(stream)
+        for b0 in range(0, R, 16):
+            ndf.ndf_infer_batch(model, rs[b0:b0 + 16], dec[b0:b0 + 16])
+        e2.record(stream)
+        ndf.ndf_synchronize(ctx)
+        ms_one += e0.elapsed_time(e1)
+        ms_16 += e1.elapsed_time(e2)
+        err = (dec[:R] - exact[:R]).abs()
+        abs_sum += float(err.double().sum())
+        n_vals += R * N
+        max_per_ref += err.amax(dim=1).tolist()
+        idx = torch.randint(0, R * N, (1 << 18,), generator=gen, device="cuda")
+        samples.append(exact[:R].reshape(-1)[idx])
+        net_samples.append(dec[:R].reshape(-1)[idx])
+    s = torch.cat(samples)
+    med = s.median()
+    return {"error_refs": len(refs), "mae": abs_sum / n_vals,
+            "max_err_mean_over_refs": float(np.mean(max_per_ref)), "max_err": float(max(max_per_ref)),
+            "const_value": float(med), "const_mae": float((s - med).abs().mean()),
+            "mae_on_const_sample": float((torch.cat(net_samples) - s).abs().mean()),
+            "exact_mean_abs_value": float(s.abs().mean()),
+            "decode_ms_per_volume_1ref": ms_one / len(refs),
+            "decode_ms_per_volume_16refs": ms_16 / len(refs)}
+
+
+def measure_ndf(ndf, ctx, fid, recipe, stream, args, exact_ms, fid_b=None, mi_first_chunk=None):
+    """Learned part: trains a Pearson and a KSG-MI network on the loaded field
+    (targets from the GPU estimators), then states the error of the decoded volumes
+    against the exact estimator over --ndf-err-refs seeded references (one and 16
+    per decode launch), with the best constant volume's error beside it and the
+    exact method's time on the same GPU.  With a second field, the same for
+    cross-field networks (reference in field A, query in field B).
+    mi_first_chunk: exact A->A MI volumes of the first 64 error references, if
+    already computed (the batched KSG measurement)."""
     N = recipe.N
     out = {}
-    rng = np.random.default_rng(777)
-    refs = [int(r) for r in rng.integers(0, N, size=16)]
+    refs = error_refs(N, args.ndf_err_refs)
     runs = [("pearson", ndf.NDF_MEASURE_PEARSON, 0, args.ndf_triples, fid, fid),
             ("mi", ndf.NDF_MEASURE_MI_KSG, K_NN, args.ndf_mi_triples, fid, fid)]
     if fid_b is not None:
@@ -479,33 +566,10 @@ def measure_ndf(ndf, ctx, fid, recipe, stream, args, exact_ms, fid_b=None):
         ndf.ndf_synchronize(ctx)
         wall = time.perf_counter() - t0
         info = ndf.ndf_model_info(model)
-        one = torch.empty(N, dtype=torch.float32, device="cuda")
-        many = torch.empty((16, N), dtype=torch.float32, device="cuda")
-        for _ in range(3):
-            ndf.ndf_infer(model, refs[0], one)
-            ndf.ndf_infer_batch(model, refs, many)
-        ndf.ndf_synchronize(ctx)
-        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        e0.record(stream)
-        for r in refs:
-            ndf.ndf_infer(model, r, one)
-        e1.record(stream)
-        ndf.ndf_infer_batch(model, refs, many)
-        e2.record(stream)
-        ndf.ndf_synchronize(ctx)
-        ms_one = e0.elapsed_time(e1) / len(refs)
-        ms_batch = e1.elapsed_time(e2) / len(refs)
         render = measure_render(ndf, ctx, model, refs, recipe, stream) if name == "pearson" else None
-        # exact volumes of the same references for the error statement
-        n_err = 16 if measure == ndf.NDF_MEASURE_PEARSON else args.ndf_mi_err_refs
-        exact = torch.empty((n_err, N), dtype=torch.float32, device="cuda")
-        if measure == ndf.NDF_MEASURE_PEARSON:
-            ndf.ndf_pearson_batch(ctx, fa, fb, refs[:n_err], ndf.NDF_PREC_FP32, exact)
-        else:
-            for i in range(n_err):
-                ndf.ndf_mi_ksg(ctx, fa, fb, refs[i], K_NN, exact[i])
-        ndf.ndf_synchronize(ctx)
-        err = (many[:n_err] - exact).abs()
+        cached = mi_first_chunk if name == "mi" else None
+        err = error_statement(ndf, ctx, model, fa, fb, measure, refs, N, stream, cached=cached)
+        exact = exact_ms[name.split("_")[0]]
         out[name] = {
             "triples": info["n_triples"], "triples_per_s": info["n_triples"] / max(info["gen_seconds"], 1e-9),
             "train_seconds": info["train_seconds"], "adam_steps": info["adam_steps"],
@@ -513,13 +577,9 @@ def measure_ndf(ndf, ctx, fid, recipe, stream, args, exact_ms, fid_b=None):
             "passes": info["passes"], "last_pass_l1": info["last_loss"], "batch": int(cfg.batch),
             "train_wall_s": wall,
             "network_bytes": info["network_bytes"], "training_bytes": info["training_bytes"],
-            "decode_ms_per_volume_1ref": ms_one, "decode_ms_per_volume_16refs": ms_batch,
-            "exact_ms_per_volume": exact_ms[name.split("_")[0]],
-            "speedup_vs_exact_16refs": exact_ms[name.split("_")[0]] / ms_batch,
-            "fields": "A->B" if fb != fa else "A->A",
-            "mae": float(err.mean()), "max_err_mean_over_refs": float(err.amax(dim=1).mean()),
-            "max_err": float(err.max()), "error_refs": n_err,
-            "exact_mean_abs_value": float(exact.abs().mean()),
+            "exact_ms_per_volume": exact,
+            "speedup_vs_exact_16refs": exact / err["decode_ms_per_volume_16refs"],
+            "fields": "A->B" if fb != fa else "A->A", **err,
         }
         if render is not None:
             out[name]["render"] = render
@@ -913,7 +973,10 @@ def main():
     ap.add_argument("--cpu-grid", type=int, default=1,
                     help="also time the oracle on one core and on the tiny workload")
     ap.add_argument("--batch", type=int, default=1, help="also time 64-reference Pearson GEMMs")
-    ap.add_argument("--ksg-batch", type=int, default=1, help="also time a 16-reference KSG launch")
+    ap.add_argument("--ksg-batch", type=int, default=1,
+                    help="also time a 64-reference KSG launch (eager and graph-replayed)")
+    ap.add_argument("--ksg-autotune", type=int, default=1,
+                    help="pick the exact search and its schedule with ndf_ksg_autotune_search")
     ap.add_argument("--ksg-search", choices=sorted(KSG_SEARCHES), default="lanes",
                     help="exact KSG search of the timed step")
     ap.add_argument("--brute-steps", type=int, default=1,
@@ -927,8 +990,9 @@ def main():
     ap.add_argument("--ndf-cross", type=int, default=1,
                     help="also train cross-field networks (reference in A, query in a second field B)")
     ap.add_argument("--ndf-triples", type=int, default=1 << 26, help="Pearson training triples")
-    ap.add_argument("--ndf-mi-triples", type=int, default=1 << 24, help="KSG-MI training triples")
-    ap.add_argument("--ndf-mi-err-refs", type=int, default=4, help="exact KSG volumes for MI error")
+    ap.add_argument("--ndf-mi-triples", type=int, default=1 << 26, help="KSG-MI training triples")
+    ap.add_argument("--ndf-err-refs", type=int, default=256,
+                    help="references of the learned part's error statement (exact volumes each)")
     ap.add_argument("--ndf-res", default="32,64,128,256",
                     help="dense grid points per axis of the 4 levels (smaller only for profiling)")
     ap.add_argument("--workload", choices=["csens", "csens-slab", "tiny"], default="csens",
@@ -997,6 +1061,16 @@ def main():
 
     search = getattr(ndf, KSG_SEARCHES[args.ksg_search][0])
     ndf.ndf_set_ksg_algorithm(ctx, search)
+    if args.ksg_schedule:
+        ndf.ndf_ksg_set_schedule(ctx, *args.ksg_schedule)
+    tuned = None
+    if args.ksg_autotune:
+        t0 = time.perf_counter()
+        alg, sw, every = ndf.ndf_ksg_autotune_search(ctx, fid, fid, K_NN)
+        args.ksg_search = next(n for n, v in KSG_SEARCHES.items() if getattr(ndf, v[0]) == alg)
+        search = alg
+        tuned = {"search": args.ksg_search, "switch_min": sw, "every": every,
+                 "seconds": time.perf_counter() - t0}
 
     def step(ref):
         ndf.ndf_pearson(ctx, fid, fid, ref, out_r)
@@ -1060,7 +1134,14 @@ def main():
               for name in sorted(KSG_SEARCHES) if name != args.ksg_search}
     ndf.ndf_set_ksg_algorithm(ctx, search, False)
     # ---- batched KSG: 16 references in one launch
-    ksg_batch = measure_ksg_batch(ndf, ctx, fid, recipe, stream, args) if args.ksg_batch else None
+    ksg_batch, mi_first_chunk = None, None
+    if args.ksg_batch:
+        # 64 references in one persistent launch, eager and graph-replayed; they are the
+        # first 64 references of the learned part's error statement, whose exact A->A MI
+        # volumes they provide
+        refs64 = error_refs(N, 64)
+        mi_first_chunk = torch.empty((64, N), dtype=torch.float32, device="cuda")
+        ksg_batch = measure_ksg_batch(ndf, ctx, fid, recipe, stream, refs64, mi_first_chunk)
 
     # ---- batched multi-reference Pearson (64 references per call) per precision
     batch = measure_pearson_batch(ndf, ctx, fid, field, recipe, stream, rank) if args.batch else None
@@ -1073,7 +1154,9 @@ def main():
         fid_b = ndf.ndf_load_ensemble(ctx, field_b, M, Z, Y, X)
         del field_b
     ndf_res = measure_ndf(ndf, ctx, fid, recipe, stream, args,
-                          {"pearson": pearson_ms, "mi": ksg_ms}, fid_b) if args.ndf else None
+                          {"pearson": pearson_ms, "mi": ksg_ms}, fid_b,
+                          mi_first_chunk=mi_first_chunk) if args.ndf else None
+    mi_first_chunk = None
     if fid_b is not None:
         ndf.ndf_free_ensemble(ctx, fid_b)
         ndf.ndf_trim_cache(ctx)
@@ -1146,6 +1229,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": workload_name(recipe), "M": M, "grid_xyz": [X, Y, Z], "k": K_NN,
                        "refs_per_rank": args.steps, "parallelism": f"replicas{world}",
+                       "ksg_autotune": tuned,
                        "l2": "inputs larger than L2 (7.04 GB field, read once per volume)"},
             "pearson_ms": pearson_ms, "ksg_ms": ksg_ms,
             "mi_pairs_per_s": N / (ksg_ms * 1e-3),
@@ -1167,7 +1251,7 @@ def main():
                                              "evals_per_volume": brute_evals},
                                 "speedup_of_timed_search": ksg_brute_ms / ksg_ms},
             "ksg_other_searches": others,
-            "ksg_batch16": ksg_batch,
+            "ksg_batch64": ksg_batch,
             "e2e": {"value": e2e_per_volume, "unit": "ms", "call": "ndf_load_and_compute",
                     "sequential_calls_ms": e2e_sequential,
                     "h2d_bytes_per_step": int(field.nbytes),

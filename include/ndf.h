@@ -243,11 +243,21 @@ ndf_status ndf_mi_ksg_batch(ndf_ctx* ctx, int ref_field, int query_field, const 
                             int R, int k, float* out);
 
 /* Times a few (references per CTA, vertices per tile) shapes of the batched
- * brute-force KSG kernel on a sample (8 references x up to 32768 query vertices) and keeps the
+ * brute-force KSG kernel on a sample (8 references x up to 16384 query vertices) and keeps the
  * fastest for later ndf_mi_ksg_batch / ndf_train calls on this context.  The
  * chosen shape is written to *best_group / *best_tile (either may be NULL). */
 ndf_status ndf_ksg_autotune(ndf_ctx* ctx, int ref_field, int query_field, int k, int* best_group,
                             int* best_tile);
+
+/* Autotuner of the exact search itself (row a7's "autotuned tiles" for the
+ * exact searches): times NDF_KSG_BLOCK and NDF_KSG_LANES under a grid of
+ * (switch_min, every) schedules on a sample of the given fields (8 references,
+ * 24,576 query vertices; about 0.3 s at M = 1000) and sets the fastest as the
+ * context's search and schedule.  Outputs may be NULL.  Results of every search
+ * are identical, so only speed depends on the choice.  Errors as ndf_mi_ksg, and
+ * NDF_ERR_OOM / NDF_ERR_CUDA for its scratch or launches. */
+ndf_status ndf_ksg_autotune_search(ndf_ctx* ctx, int ref_field, int query_field, int k,
+                                   int* algorithm, int* switch_min, int* every);
 
 /* Test hook for one (reference, query) pair of the KSG path above: writes, in
  * member order, eps[M] (k-th-neighbour distance), nx[M], ny[M] (marginal
@@ -327,8 +337,8 @@ typedef struct {
     int32_t continuous;       /* 0: grid-vertex pairs, generated once; 1: uniform random
                                  positions with trilinear samples (ndf_sample_triples),
                                  n_triples fresh pairs every pass (Sec. 4.3) [0] */
-    int32_t hash_tf32;        /* ndf_hash_train: dense layers as TF32 tensor-core GEMMs
-                                 (10-bit mantissa operands, FP32 accumulation); 0: FP32 [1] */
+    int32_t hash_tf32;        /* kept for layout compatibility and ignored: ndf_hash_train's
+                                 dense layers are the library's own FP32 products [1] */
 } ndf_train_cfg;
 
 /* What a model is and how it was trained. */

@@ -1269,6 +1269,88 @@ cudaError_t launch_ksg(ndf_ctx* ctx, const Field& rf, const Field& qf, const int
 
 using namespace ndf;
 
+// Picks the exact search for algorithm 1 and the lane schedule: times the block
+// search and the lane-refill search under several (switch_min, every) schedules on
+// a sample (8 references spread over the reference field, 24,576 consecutive query
+// vertices from the middle of the grid, one warm-up launch each) and keeps the
+// fastest in the context.  Results do not depend on the choice.
+extern "C" ndf_status ndf_ksg_autotune_search(ndf_ctx* ctx, int ref_field, int query_field, int k,
+                                              int* algorithm, int* switch_min, int* every) {
+    if (!ctx) return NDF_ERR_ARG;
+    const Field *rf, *qf;
+    ndf_status st = check_pair(ctx, ref_field, query_field, 0, &rf, &qf);
+    if (st != NDF_OK) return st;
+    if (k < 1 || k >= rf->M || k > kKsgMaxK || rf->M > kKsgMaxM)
+        return fail(ctx, NDF_ERR_ARG, "bad k or M");
+    cudaSetDevice(ctx->device);
+    if ((st = ensure_psi_table(ctx, rf->M + 1)) != NDF_OK) return st;
+    cudaError_t es = ensure_sorted_columns(ctx, ctx->fields[query_field]);
+    if (es != cudaSuccess) return cuda_fail(ctx, es, "sorted columns");
+    const int R = 8;
+    const int64_t nv = qf->N < 24576 ? qf->N : 24576;
+    const int64_t v0 = (qf->N - nv) / 2;
+    int64_t refs[R];
+    for (int i = 0; i < R; ++i) refs[i] = (int64_t)((double)(i + 0.5) / R * (double)(rf->N - 1));
+    float* out = nullptr;
+    int64_t* d_refs = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&out, sizeof(float) * (size_t)R * (size_t)nv);
+    if (e == cudaSuccess) e = cudaMalloc(&d_refs, sizeof refs);
+    if (e == cudaSuccess) e = cudaMemcpy(d_refs, refs, sizeof refs, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const int cand[][3] = {{NDF_KSG_BLOCK, 0, 0},  {NDF_KSG_LANES, 8, 4},  {NDF_KSG_LANES, 12, 4},
+                           {NDF_KSG_LANES, 16, 4}, {NDF_KSG_LANES, 12, 5}, {NDF_KSG_LANES, 16, 5},
+                           {NDF_KSG_LANES, 12, 6}, {NDF_KSG_LANES, 16, 6}, {NDF_KSG_LANES, 20, 5}};
+    const int keep_alg = ctx->ksg_algorithm, keep_sw = ctx->ksg_switch_min, keep_ev = ctx->ksg_every;
+    const bool keep_count = ctx->count_evals;
+    ctx->count_evals = false;
+    float best = 3.4e38f;
+    int ba = keep_alg, bs = keep_sw, be = keep_ev;
+    for (const auto& c : cand) {
+        if (e != cudaSuccess) break;
+        ctx->ksg_algorithm = c[0];
+        if (c[0] == NDF_KSG_LANES) {
+            ctx->ksg_switch_min = c[1];
+            ctx->ksg_every = c[2];
+        }
+        e = launch_ksg(ctx, *rf, *qf, d_refs, 0, R, k, v0, v0 + nv, out, nv, true, 1, 1, nullptr,
+                       nullptr, nullptr, nullptr, nullptr);  // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+        if (e == cudaSuccess)
+            e = launch_ksg(ctx, *rf, *qf, d_refs, 0, R, k, v0, v0 + nv, out, nv, true, 1, 1, nullptr,
+                           nullptr, nullptr, nullptr, nullptr);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best) {
+            best = ms;
+            ba = c[0];
+            bs = c[0] == NDF_KSG_LANES ? c[1] : keep_sw;
+            be = c[0] == NDF_KSG_LANES ? c[2] : keep_ev;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (out) cudaFree(out);
+    if (d_refs) cudaFree(d_refs);
+    ctx->count_evals = keep_count;
+    if (e != cudaSuccess) {
+        ctx->ksg_algorithm = keep_alg;
+        ctx->ksg_switch_min = keep_sw;
+        ctx->ksg_every = keep_ev;
+        return cuda_fail(ctx, e, "ksg search autotune");
+    }
+    ctx->ksg_algorithm = ba;
+    ctx->ksg_switch_min = bs;
+    ctx->ksg_every = be;
+    if (algorithm) *algorithm = ba;
+    if (switch_min) *switch_min = bs;
+    if (every) *every = be;
+    return NDF_OK;
+}
+
 extern "C" ndf_status ndf_ksg_autotune(ndf_ctx* ctx, int ref_field, int query_field, int k,
                                        int* best_group, int* best_tile) {
     if (!ctx) return NDF_ERR_ARG;

@@ -119,6 +119,10 @@ _sig("ndf_ksg_set_schedule", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int])
 _sig("ndf_ksg_take_eval_count", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64)])
 _sig("ndf_mi_ksg_batch", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int,
                                         ctypes.c_int, _vp])
+_sig("ndf_ksg_autotune_search", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_int),
+                                               ctypes.POINTER(ctypes.c_int),
+                                               ctypes.POINTER(ctypes.c_int)])
 _sig("ndf_ksg_autotune", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)])
 _sig("ndf_pearson_noalloc", ctypes.c_int, [_vp, _vp, _i64, _i64, _i64, _vp, _vp])
@@ -333,6 +337,15 @@ def ndf_mi_ksg_batch(ctx, ref_field: int, query_field: int, ref_idx, k: int, out
         ptr, R = refs.ctypes.data, int(refs.shape[0])
     _check(ctx, _lib.ndf_mi_ksg_batch(ctx, ref_field, query_field, ptr, R, int(k), _addr(out)),
            "ndf_mi_ksg_batch")
+
+
+def ndf_ksg_autotune_search(ctx, ref_field: int, query_field: int, k: int):
+    """Sets the fastest exact search and lane schedule; returns (algorithm, switch_min, every)."""
+    a, sw, ev = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    _check(ctx, _lib.ndf_ksg_autotune_search(ctx, ref_field, query_field, k, ctypes.byref(a),
+                                             ctypes.byref(sw), ctypes.byref(ev)),
+           "ndf_ksg_autotune_search")
+    return a.value, sw.value, ev.value
 
 
 def ndf_ksg_autotune(ctx, ref_field: int, query_field: int, k: int):

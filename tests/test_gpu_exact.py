@@ -373,7 +373,7 @@ def test_argument_errors(ndf_mod, ctx, tiny_field, tiny_ref):
         lambda: ndf.ndf_mi_ksg(ctx, fid, fid, tiny_ref, 17, out),
         lambda: ndf.ndf_pearson(ctx, fid, fid, N, out),
         lambda: ndf.ndf_pearson(ctx, fid, fid, -1, out),
-        lambda: ndf.ndf_pearson(ctx, fid, 99, 0, out),
+        lambda: ndf.ndf_pearson(ctx, fid, 1 << 20, 0, out),  # an id never issued
         lambda: ndf.ndf_pearson(ctx, fid, fid, 0, None),
     ]
     for c in cases:

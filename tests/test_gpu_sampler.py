@@ -62,7 +62,7 @@ def test_sampler_argument_errors(ndf_mod, ctx, tiny_field):
     pr = np.empty((4, 3), np.float32)
     t = np.empty(4, np.float32)
     for args in ((fid, fid, 9, 0, 4), (fid, fid, ndf_mod.NDF_MEASURE_MI_KSG, 0, 4),
-                 (fid, fid, ndf_mod.NDF_MEASURE_PEARSON, 0, 0), (fid, 77, 0, 0, 4)):
+                 (fid, fid, ndf_mod.NDF_MEASURE_PEARSON, 0, 0), (fid, 1 << 20, 0, 0, 4)):
         with pytest.raises(ndf_mod.NdfError):
             ndf_mod.ndf_sample_triples(ctx, *args, 1, pr, pr, t)
     ndf_mod.ndf_free_ensemble(ctx, fid)

@@ -77,7 +77,7 @@ def test_column_calls_reject_bad_arguments(ndf_mod, ctx, tiny_field):
     out = np.empty(Z * Y * X, np.float32)
     for call in (lambda: ndf.ndf_field_column(ctx, fid, Z * Y * X, col),
                  lambda: ndf.ndf_field_column(ctx, fid, -1, col),
-                 lambda: ndf.ndf_field_column(ctx, 99, 0, col),
+                 lambda: ndf.ndf_field_column(ctx, 1 << 20, 0, col),
                  lambda: ndf.ndf_pearson_column(ctx, None, fid, out),
                  lambda: ndf.ndf_mi_ksg_column(ctx, col, fid, M, out),
                  lambda: ndf.ndf_mi_ksg_column(ctx, col, fid, 0, out)):
