@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) infer_tc_kernel(const TcInferAr
                 tc_fence_before();
                 arrive(&a_ready[s]);
                 for (int layer = 0; layer < 3; ++layer) {
-                    if (!wait_bounded(&d_ready[s], nd & 1u, abort_flag)) goto done;
+                    if (!__all_sync(0xffffffffu, wait_bounded(&d_ready[s], nd & 1u, abort_flag))) goto done;
                     ++nd;
                     tc_fence_after();
                     const float* bias = vec + layer * kHid;

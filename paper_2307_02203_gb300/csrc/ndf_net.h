@@ -30,14 +30,19 @@ struct NetLayout {
     void init(const int r[kLevels]);
 };
 
-// Per-batch work buffers (grown on demand).
+// chunks of the batch summed by separate CTAs in the weight gradient
+constexpr int kMlpMaxChunks = 64;
+
+// Per-batch work buffers (grown on demand).  The transposed matrices have a row
+// pitch of Bs = B rounded up to 8 samples.
 struct NetWork {
     int64_t cap = 0;
     float* fr = nullptr;          // [B][64] reference features
     float* fq = nullptr;          // [B][64] query features
     __nv_bfloat16* x = nullptr;   // [B][128] merged input
-    __nv_bfloat16* h = nullptr;   // [3][B][128] hidden activations
-    __nv_bfloat16* dz = nullptr;  // [3][B][128] pre-activation gradients
+    __nv_bfloat16* hT = nullptr;  // [4][128][Bs] x^T and the hidden activations h1^T..h3^T
+    __nv_bfloat16* dzT = nullptr; // [3][128][Bs] pre-activation gradients dz1^T..dz3^T
+    float* wpart = nullptr;       // [3][kMlpMaxChunks][128][128] weight-gradient chunks
     float* dx = nullptr;          // [B][128] input gradient
     float* o = nullptr;           // [B] pre-activation output
     float* dout = nullptr;        // [B] dL/do
@@ -86,6 +91,14 @@ cudaError_t model_step(ndf_model* m, const float* pr, const float* pq, const flo
                        int64_t B, float lr, float beta1, float beta2, float eps, bool update);
 cudaError_t net_set_attributes();
 cudaError_t model_forward(ndf_model* m, const float* pr, const float* pq, int64_t B, float* out);
+
+// The MLP on tcgen05 (ndf_mlp_tc.cu), over the merged input in m->work.x:
+// forward (with target: also the transposed activations, the output gradient and
+// the loss sum; without: y = the network output), and the backward (gradients of
+// the three layers and of the output layer added into m->grad; the input gradient
+// in m->work.dx).
+cudaError_t mlp_tc_forward(ndf_model* m, int64_t B, const float* target, float* y);
+cudaError_t mlp_tc_backward(ndf_model* m, int64_t B);
 
 // Volume decoding for R references (vertex ids on the device): out[R][N].
 cudaError_t model_infer(ndf_model* m, const int64_t* d_refs, int R, float* out);
