@@ -81,7 +81,7 @@ def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = N
     if force or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
         cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + [
-            "-lcublas", "-Xlinker", "-rpath", "-Xlinker", _cuda_lib_dir(nvcc)]
+            "-Xlinker", "-rpath", "-Xlinker", _cuda_lib_dir(nvcc)]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

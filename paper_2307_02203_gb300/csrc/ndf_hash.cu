@@ -12,12 +12,11 @@
 //            the decoder layers.  One encoder (self field, symmetric by
 //            construction) or two (cross field: 0 reference, 1 query).
 //
-// GPU design: activations are feature-major per sample ([B][c] row-major, which
-// is a column-major [c][B] matrix), the dense layers are FP32 cuBLAS GEMMs (plain
-// library GEMMs; FP32 for parity with the oracle), and everything between them
-// (embedding, bias + activation, merge, output + loss, the hash-table scatter of
-// the backward, Adam) is in the kernels below.
-#include <cublas_v2.h>
+// GPU design: activations are feature-major per sample ([B][c] row-major), the
+// dense layers are this library's FP32 matrix products (gemm_f32.cu: FP32 for
+// parity with the oracle, deterministic weight-gradient sums), and everything
+// between them (embedding, bias + activation, merge, output + loss, the
+// hash-table scatter of the backward, Adam) is in the kernels below.
 #include <math.h>
 #include <string.h>
 
@@ -27,6 +26,7 @@
 #include <numeric>
 #include <vector>
 
+#include "gemm_f32.h"
 #include "hash_common.cuh"
 #include "ndf_hash_tc.h"
 #include "ndf_internal.h"
@@ -204,14 +204,14 @@ struct ndf_hash_model {
     HashLayout Ly;
     float *params = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
     int64_t t = 0;
-    cublasHandle_t blas = nullptr;
-    // workspace for a batch of up to cap samples
+    // workspace for a batch of up to cap samples, and of the weight-gradient products
+    float* gemm_work = nullptr;
     int64_t cap = 0;
     float* ws = nullptr;
     float *x0[2] = {}, *pre_e[2][kHashMaxLayers] = {}, *post_e[2][kHashMaxLayers] = {};
     float *z = nullptr, *pre_d[kHashMaxLayers] = {}, *post_d[kHashMaxLayers] = {};
     float *ga = nullptr, *gb = nullptr, *gr = nullptr, *gq = nullptr;
-    float *ones = nullptr, *graw = nullptr, *tgt = nullptr, *pos = nullptr;
+    float *graw = nullptr, *tgt = nullptr, *pos = nullptr;
     double* loss = nullptr;
     // tensor-core decoding: packed BF16 weight images and biases of the parameter
     // version tc_ver, reference latents, per-axis Fourier features of the decode
@@ -231,15 +231,22 @@ namespace ndf {
 static cudaError_t hash_workspace(ndf_hash_model* m, int64_t B) {
     if (B <= m->cap) return cudaSuccess;
     if (m->ws) cudaFree(m->ws);
+    if (m->gemm_work) cudaFree(m->gemm_work);
     m->ws = nullptr;
+    m->gemm_work = nullptr;
     m->cap = 0;
     const HashLayout& L = m->Ly;
     const int64_t c = L.c, wmax = std::max<int64_t>(std::max<int64_t>(L.din, c), L.ddec);
     // loss (2 doubles), x0 x2, encoder pre/post x2 sides, z, decoder pre/post,
-    // ga, gb (ping-pong), gr, gq (merge gradients), ones, graw, tgt, positions
+    // ga, gb (ping-pong), gr, gq (merge gradients), graw, tgt, positions
     const int64_t floats = 4 + 2 * B * L.din + 2 * 2 * L.le * B * c + B * L.ddec +
-                           2 * L.ld * B * c + 2 * B * wmax + 2 * B * L.dlat + 3 * B + 6 * B;
+                           2 * L.ld * B * c + 2 * B * wmax + 2 * B * L.dlat + 2 * B + 6 * B;
     cudaError_t e = cudaMalloc(&m->ws, sizeof(float) * (size_t)floats);
+    if (e != cudaSuccess) return e;
+    // partial products of the weight gradients (at most c x wmax per slice) and of the
+    // bias gradients
+    const int64_t wf = std::max<int64_t>(gemm_f32_tn_work_floats(c, wmax, B), kSplitK * wmax);
+    e = cudaMalloc(&m->gemm_work, sizeof(float) * (size_t)wf);
     if (e != cudaSuccess) return e;
     float* o = m->ws;
     auto take = [&](int64_t n) {
@@ -263,36 +270,28 @@ static cudaError_t hash_workspace(ndf_hash_model* m, int64_t B) {
     m->gb = take(B * wmax);
     m->gr = take(B * L.dlat);
     m->gq = take(B * L.dlat);
-    m->ones = take(B);
     m->graw = take(B);
     m->tgt = take(B);
     m->pos = take(6 * B);
-    fill_kernel<<<blocks_for(B), 256, 0, m->ctx->stream>>>(m->ones, B, 1.0f);
     m->cap = B;
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
-static bool blas_ok(cublasStatus_t s) { return s == CUBLAS_STATUS_SUCCESS; }
-
-// Y[c_out][B] = W x X[c_in][B] (W row-major [c_out][c_in])
-static bool gemm_fwd(cublasHandle_t h, const float* W, const float* X, float* Y, int c_out,
+// Activations are sample-major, [B][c]; W is [c_out][c_in].
+// Y[B][c_out] = X[B][c_in] W^T
+static bool gemm_fwd(ndf_hash_model* m, const float* W, const float* X, float* Y, int c_out,
                      int c_in, int64_t B) {
-    const float one = 1.0f, zero = 0.0f;
-    return blas_ok(cublasSgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, c_out, (int)B, c_in, &one, W, c_in, X,
-                               c_in, &zero, Y, c_out));
+    return gemm_f32_nt(m->ctx->stream, X, W, Y, B, c_out, c_in) == cudaSuccess;
 }
 
-// dX = W^T dY; dW += X dY^T; db += dY 1
-static bool gemm_bwd(cublasHandle_t h, const float* W, const float* X, const float* dY, float* dX,
-                     float* dW, float* db, const float* ones, int c_out, int c_in, int64_t B) {
-    const float one = 1.0f, zero = 0.0f;
-    if (dX && !blas_ok(cublasSgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, c_in, (int)B, c_out, &one, W, c_in,
-                                   dY, c_out, &zero, dX, c_in)))
-        return false;
-    if (!blas_ok(cublasSgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, c_in, c_out, (int)B, &one, X, c_in, dY,
-                             c_out, &one, dW, c_in)))
-        return false;
-    return blas_ok(cublasSgemv(h, CUBLAS_OP_N, c_out, (int)B, &one, dY, c_out, ones, 1, &one, db, 1));
+// dX = dY W (when dX is wanted); dW += dY^T X; db += the column sums of dY
+static bool gemm_bwd(ndf_hash_model* m, const float* W, const float* X, const float* dY, float* dX,
+                     float* dW, float* db, int c_out, int c_in, int64_t B) {
+    cudaStream_t s = m->ctx->stream;
+    if (dX && gemm_f32_nn(s, dY, W, dX, B, c_in, c_out) != cudaSuccess) return false;
+    if (gemm_f32_tn_acc(s, dY, X, dW, c_out, c_in, B, m->gemm_work) != cudaSuccess) return false;
+    m->ctx->launches += 5;
+    return colsum_f32_acc(s, dY, db, B, c_out, m->gemm_work) == cudaSuccess;
 }
 
 // encoder e over the positions pos[B][3]: fills x0 / pre / post of side s
@@ -306,7 +305,7 @@ static cudaError_t encode_side(ndf_hash_model* m, int e, int s, const float* pos
     const float* in = m->x0[s];
     for (int k = 0; k < L.le; ++k) {
         const int cin = k == 0 ? L.din : L.c;
-        if (!gemm_fwd(m->blas, enc + L.ew[k], in, m->pre_e[s][k], L.c, cin, B))
+        if (!gemm_fwd(m, enc + L.ew[k], in, m->pre_e[s][k], L.c, cin, B))
             return cudaErrorUnknown;
         bias_act_kernel<<<blocks_for((int64_t)L.c * B), 256, 0, ctx->stream>>>(
             m->pre_e[s][k], enc + L.eb[k], L.c, B, k < L.le - 1 ? L.act : -1, m->post_e[s][k]);
@@ -328,7 +327,7 @@ static cudaError_t decode_z(ndf_hash_model* m, int64_t B) {
     const float* in = m->z;
     for (int k = 0; k < L.ld; ++k) {
         const int cout = k == L.ld - 1 ? 1 : L.c, cin = k == 0 ? L.ddec : L.c;
-        if (!gemm_fwd(m->blas, m->params + L.dw[k], in, m->pre_d[k], cout, cin, B))
+        if (!gemm_fwd(m, m->params + L.dw[k], in, m->pre_d[k], cout, cin, B))
             return cudaErrorUnknown;
         bias_act_kernel<<<blocks_for((int64_t)cout * B), 256, 0, ctx->stream>>>(
             m->pre_d[k], m->params + L.db[k], cout, B, k < L.ld - 1 ? L.act : -1, m->post_d[k]);
@@ -365,8 +364,8 @@ static cudaError_t hash_forward_backward(ndf_hash_model* m, const float* pr, con
         const int cout = k == L.ld - 1 ? 1 : L.c, cin = k == 0 ? L.ddec : L.c;
         const float* in = k == 0 ? m->z : m->post_d[k - 1];
         float* gin = pp[cur];
-        if (!gemm_bwd(m->blas, m->params + L.dw[k], in, g, gin, m->grad + L.dw[k], m->grad + L.db[k],
-                      m->ones, cout, cin, B))
+        if (!gemm_bwd(m, m->params + L.dw[k], in, g, gin, m->grad + L.dw[k], m->grad + L.db[k],
+                      cout, cin, B))
             return cudaErrorUnknown;
         if (k > 0) {
             dact_mul_kernel<<<blocks_for((int64_t)L.c * B), 256, 0, ctx->stream>>>(
@@ -389,8 +388,8 @@ static cudaError_t hash_forward_backward(ndf_hash_model* m, const float* pr, con
             const int cin = k == 0 ? L.din : L.c;
             const float* in = k == 0 ? m->x0[s] : m->post_e[s][k - 1];
             float* gin = pp[t];
-            if (!gemm_bwd(m->blas, enc + L.ew[k], in, gs, gin, genc + L.ew[k], genc + L.eb[k],
-                          m->ones, L.c, cin, B))
+            if (!gemm_bwd(m, enc + L.ew[k], in, gs, gin, genc + L.ew[k], genc + L.eb[k],
+                          L.c, cin, B))
                 return cudaErrorUnknown;
             if (k > 0) {
                 dact_mul_kernel<<<blocks_for((int64_t)L.c * B), 256, 0, ctx->stream>>>(
@@ -624,11 +623,9 @@ ndf_status ndf_hash_model_create(ndf_ctx* ctx, const ndf_hash_arch* arch, int me
     if (e == cudaSuccess) e = cudaMalloc(&m->v, bytes);
     if (e == cudaSuccess) e = cudaMemsetAsync(m->m, 0, bytes, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(m->v, 0, bytes, ctx->stream);
-    if (e != cudaSuccess || cublasCreate(&m->blas) != CUBLAS_STATUS_SUCCESS ||
-        cublasSetStream(m->blas, ctx->stream) != CUBLAS_STATUS_SUCCESS) {
+    if (e != cudaSuccess) {
         ndf_hash_model_free(m);
-        return e != cudaSuccess ? cuda_fail(ctx, e, "hash model allocation")
-                                : fail(ctx, NDF_ERR_CUDA, "cuBLAS set-up failed");
+        return cuda_fail(ctx, e, "hash model allocation");
     }
     // initialisation: tables U(-0.1, 0.1), weights U(-sqrt(6/in), sqrt(6/in)), biases 0, and a
     // zero last decoder layer (the untrained field is constant: without it, the sin^2 term
@@ -672,11 +669,10 @@ ndf_status ndf_hash_model_create(ndf_ctx* ctx, const ndf_hash_arch* arch, int me
 void ndf_hash_model_free(ndf_hash_model* m) {
     if (!m) return;
     if (m->ctx) cudaStreamSynchronize(m->ctx->stream);
-    void* ps[] = {m->params, m->grad, m->m, m->v, m->ws, m->tc_w, m->tc_bias, m->tc_zr, m->tc_lat,
-                  m->tc_ftab};
+    void* ps[] = {m->params, m->grad, m->m, m->v, m->ws, m->gemm_work, m->tc_w, m->tc_bias,
+                  m->tc_zr, m->tc_lat, m->tc_ftab};
     for (void* q : ps)
         if (q) cudaFree(q);
-    if (m->blas) cublasDestroy(m->blas);
     delete m;
 }
 
@@ -848,7 +844,6 @@ ndf_status ndf_hash_train(ndf_ctx* ctx, int ref_field, int query_field, int meas
         return st;
     }
     const int64_t T = cfg.n_triples, B = std::min(cfg.batch, T);
-    if (cfg.hash_tf32) cublasSetMathMode(m->blas, CUBLAS_TF32_TENSOR_OP_MATH);
     float *pref = nullptr, *pq = nullptr, *tgt = nullptr;
     cudaError_t e = cudaMalloc(&pref, sizeof(float) * 3 * (size_t)T);
     if (e == cudaSuccess) e = cudaMalloc(&pq, sizeof(float) * 3 * (size_t)T);
@@ -896,7 +891,6 @@ ndf_status ndf_hash_train(ndf_ctx* ctx, int ref_field, int query_field, int meas
     m->train_seconds =
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count() - m->gen_seconds;
     m->n_triples = T;
-    cublasSetMathMode(m->blas, CUBLAS_DEFAULT_MATH);  // the step / forward calls stay FP32
     cleanup();
     if (e != cudaSuccess) {
         ndf_hash_model_free(m);
