@@ -6,10 +6,11 @@
 //
 // Columns of up to 1024 members: a CTA per tile of kSortTile consecutive
 // vertices.  The tile's rows (kSortTile floats of one member, contiguous in the
-// field) are read and written whole, through shared memory; there each column is
-// stored with one skip every 32 elements and an odd column stride, so that the
-// warps' column accesses are free of bank conflicts and the row accesses (two
-// rows of 16 per warp instruction) at most 2-way conflicted.  A warp
+// field) are read and written whole, 16 bytes per thread where the tile is aligned,
+// through shared memory; there each column is stored with one skip every 32
+// elements and a column stride of 2 mod 32, so that the warps' column accesses and
+// the row accesses (eight rows of four 16-byte quads per warp instruction: banks
+// 2p + m) are free of bank conflicts.  A warp
 // sorts one column at a time in registers (R = 1024 / 32 values per lane at most,
 // padded with +inf), lane-major element order e = lane * R + r, by the bitonic
 // network in its "mirror" form (each merge of size kk first compares e with
@@ -27,8 +28,8 @@ constexpr int kSortTile = 16;     // vertices per CTA
 constexpr int kSortThreads = 256;
 
 // shared-memory floats of one column: 32 R elements with a skip after every 32,
-// rounded up to an odd count
-__host__ __device__ constexpr int sort_col_stride(int R) { return 33 * R + 1 - (R & 1); }
+// rounded up to 2 mod 32
+__host__ __device__ constexpr int sort_col_stride(int R) { return 33 * R + ((34 - (33 * R) % 32) % 32); }
 __device__ __forceinline__ int sort_col_slot(int e) { return e + (e >> 5); }
 
 // the network on a warp's column in registers (element e = lane * R + r)
@@ -86,11 +87,26 @@ __global__ void __launch_bounds__(kSortThreads, 3) sort_columns_tile_kernel(cons
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t v0 = v_begin + (int64_t)blockIdx.x * kSortTile;
     const int vc = v_end - v0 < kSortTile ? (int)(v_end - v0) : kSortTile;
-    // rows in: thread t takes member t / kSortTile, vertex t % kSortTile
+    // rows in: with a whole, 16-byte aligned tile thread t takes member t / 4 and the
+    // quad of vertices 4 (t % 4) ..; otherwise member t / kSortTile, vertex t % kSortTile
+    const bool quads = vc == kSortTile && (N & 3) == 0 && (v0 & 3) == 0;
+    if (quads) {
+#pragma unroll 4
+        for (int idx = threadIdx.x; idx < M * 4; idx += kSortThreads) {
+            const int m = idx >> 2, p = (idx & 3) * 4;
+            const float4 q = __ldcs(reinterpret_cast<const float4*>(field + (int64_t)m * N + v0 + p));
+            const int sl = sort_col_slot(m);
+            tile[p * S + sl] = q.x;
+            tile[(p + 1) * S + sl] = q.y;
+            tile[(p + 2) * S + sl] = q.z;
+            tile[(p + 3) * S + sl] = q.w;
+        }
+    } else {
 #pragma unroll 8
-    for (int idx = threadIdx.x; idx < M * kSortTile; idx += kSortThreads) {
-        const int m = idx / kSortTile, p = idx - m * kSortTile;
-        if (p < vc) tile[p * S + sort_col_slot(m)] = __ldcs(field + (int64_t)m * N + v0 + p);
+        for (int idx = threadIdx.x; idx < M * kSortTile; idx += kSortThreads) {
+            const int m = idx / kSortTile, p = idx - m * kSortTile;
+            if (p < vc) tile[p * S + sort_col_slot(m)] = __ldcs(field + (int64_t)m * N + v0 + p);
+        }
     }
     __syncthreads();
     for (int p = warp; p < vc; p += kSortThreads / 32) {
@@ -110,10 +126,21 @@ __global__ void __launch_bounds__(kSortThreads, 3) sort_columns_tile_kernel(cons
         }
     }
     __syncthreads();
+    if (quads) {
+#pragma unroll 4
+        for (int idx = threadIdx.x; idx < M * 4; idx += kSortThreads) {
+            const int m = idx >> 2, p = (idx & 3) * 4;
+            const int sl = sort_col_slot(m);
+            __stcs(reinterpret_cast<float4*>(sorted + (int64_t)m * N + v0 + p),
+                   make_float4(tile[p * S + sl], tile[(p + 1) * S + sl], tile[(p + 2) * S + sl],
+                               tile[(p + 3) * S + sl]));
+        }
+    } else {
 #pragma unroll 8
-    for (int idx = threadIdx.x; idx < M * kSortTile; idx += kSortThreads) {
-        const int m = idx / kSortTile, p = idx - m * kSortTile;
-        if (p < vc) __stcs(sorted + (int64_t)m * N + v0 + p, tile[p * S + sort_col_slot(m)]);
+        for (int idx = threadIdx.x; idx < M * kSortTile; idx += kSortThreads) {
+            const int m = idx / kSortTile, p = idx - m * kSortTile;
+            if (p < vc) __stcs(sorted + (int64_t)m * N + v0 + p, tile[p * S + sort_col_slot(m)]);
+        }
     }
 }
 
