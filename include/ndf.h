@@ -452,8 +452,9 @@ typedef struct ndf_hash_model ndf_hash_model;
  * cross = 1: separate encoders (0 reference, 1 query).  Parameters follow the
  * layout of the oracle (per encoder: level tables, then W[out][in], b per layer;
  * then the decoder layers), FP32, with Adam moments.  Initialisation: tables
- * U(-0.1, 0.1), weights U(+-sqrt(6 / fan_in)), biases 0, the last decoder
- * layer 0 (seeded). */
+ * U(-0.1, 0.1), weights U(+-sqrt(6 / fan_in)) except the first encoder layer's
+ * weights on the Fourier columns, which start at 0.1 of that scale, biases 0,
+ * the last decoder layer 0 (seeded). */
 ndf_status ndf_hash_model_create(ndf_ctx* ctx, const ndf_hash_arch* arch, int measure, int cross,
                                  uint64_t seed, int64_t X, int64_t Y, int64_t Z,
                                  ndf_hash_model** out);

@@ -33,6 +33,10 @@
 
 namespace ndf {
 
+// initial scale of the first encoder layer's weights on the Fourier columns,
+// relative to the He-uniform scale of the other weights (see ndf_hash_model_create)
+constexpr double kFourierInit = 0.1;
+
 // x0[b][din] = embed(pos[b]) with the tables of one encoder
 __global__ void hash_embed_kernel(const float* __restrict__ pos, int64_t B,
                                   const float* __restrict__ enc, EmbedArgs E,
@@ -629,7 +633,12 @@ ndf_status ndf_hash_model_create(ndf_ctx* ctx, const ndf_hash_arch* arch, int me
     }
     // initialisation: tables U(-0.1, 0.1), weights U(-sqrt(6/in), sqrt(6/in)), biases 0, and a
     // zero last decoder layer (the untrained field is constant: without it, the sin^2 term
-    // of Snake-family activations drifts the output and L1 training collapses it)
+    // of Snake-family activations drifts the output and L1 training collapses it).  The
+    // first encoder layer's weights on the Fourier columns start at kFourierInit of that
+    // scale: at full scale the frequencies up to 2^(L-1) pi reach every latent feature, the
+    // untrained encoder maps positions a cell apart to unrelated latents, the product merge
+    // carries no dependence signal, and on a field whose pairs are mostly uncorrelated the
+    // L1 loss keeps the network at the constant predictor
     std::vector<float> h((size_t)m->Ly.total, 0.0f);
     uint64_t st = seed * 0x9e3779b97f4a7c15ULL + 0x1234567ULL;
     auto unif = [&]() {
@@ -647,7 +656,11 @@ ndf_status ndf_hash_model_create(ndf_ctx* ctx, const ndf_hash_arch* arch, int me
         for (int k = 0; k < L.le; ++k) {
             const int64_t cin = k == 0 ? L.din : L.c;
             const double a = sqrt(6.0 / (double)cin);
-            for (int64_t i = 0; i < cin * L.c; ++i) h[(size_t)(base + L.ew[k] + i)] = (float)(a * unif());
+            for (int64_t i = 0; i < cin * L.c; ++i) {
+                const int64_t col = i % cin;  // W[out][in]
+                const bool fourier = k == 0 && col >= 3 && col < 3 + 6 * (int64_t)L.L;
+                h[(size_t)(base + L.ew[k] + i)] = (float)((fourier ? kFourierInit : 1.0) * a * unif());
+            }
         }
     }
     for (int k = 0; k < L.ld - 1; ++k) {
