@@ -36,7 +36,7 @@ void NetLayout::init(const int r[kLevels]) {
 }
 
 void NetWork::release() {
-    void* ps[] = {fr, fq, x, hT, dzT, wpart, dx, o, dout, pos, target, loss};
+    void* ps[] = {fr, fq, x, wpart, cpart, dx, pos, target, loss};
     for (void* q : ps)
         if (q) cudaFree(q);
     *this = NetWork();
@@ -242,15 +242,12 @@ __global__ void __launch_bounds__(256)
 }
 
 __global__ void refresh_mlp_kernel(const float* __restrict__ p, int64_t offW1, int64_t offW2,
-                                   int64_t offW3, __nv_bfloat16* __restrict__ w,
-                                   __nv_bfloat16* __restrict__ wt) {
+                                   int64_t offW3, __nv_bfloat16* __restrict__ w) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 3 * kHid * kHid) return;
     const int l = i / (kHid * kHid), r = (i / kHid) % kHid, c = i % kHid;
     const int64_t off = l == 0 ? offW1 : (l == 1 ? offW2 : offW3);
-    const __nv_bfloat16 b = __float2bfloat16_rn(p[off + (int64_t)r * kHid + c]);
-    w[(size_t)l * kHid * kHid + r * kHid + c] = b;
-    wt[(size_t)l * kHid * kHid + c * kHid + r] = b;
+    w[(size_t)l * kHid * kHid + r * kHid + c] = __float2bfloat16_rn(p[off + (int64_t)r * kHid + c]);
 }
 
 __global__ void grid_to_bf16_kernel(const float* __restrict__ p, int64_t n,
@@ -315,7 +312,6 @@ ndf_status model_alloc(ndf_ctx* ctx, const int res[kLevels], int measure, int64_
     if (e == cudaSuccess) e = cudaMalloc(&m->v, n * 4);
     if (e == cudaSuccess) e = cudaMalloc(&m->grid_bf, (size_t)m->L.n_grid * 2);
     if (e == cudaSuccess) e = cudaMalloc(&m->wbf, (size_t)3 * kHid * kHid * 2);
-    if (e == cudaSuccess) e = cudaMalloc(&m->wtbf, (size_t)3 * kHid * kHid * 2);
     if (e == cudaSuccess) e = cudaMemsetAsync(m->params, 0, n * 4, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(m->grad, 0, n * 4, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(m->m, 0, n * 4, ctx->stream);
@@ -330,7 +326,7 @@ ndf_status model_alloc(ndf_ctx* ctx, const int res[kLevels], int measure, int64_
 
 void model_free(ndf_model* m) {
     if (!m) return;
-    void* ps[] = {m->params, m->grad, m->m, m->v, m->grid_bf, m->wbf, m->wtbf};
+    void* ps[] = {m->params, m->grad, m->m, m->v, m->grid_bf, m->wbf};
     for (void* q : ps)
         if (q) cudaFree(q);
     m->work.release();
@@ -342,7 +338,7 @@ cudaError_t model_refresh_bf16(ndf_model* m) {
     grid_to_bf16_kernel<<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(m->params, m->L.n_grid,
                                                                       m->grid_bf);
     refresh_mlp_kernel<<<(3 * kHid * kHid + 255) / 256, 256, 0, ctx->stream>>>(
-        m->params, m->L.W1, m->L.W2, m->L.W3, m->wbf, m->wtbf);
+        m->params, m->L.W1, m->L.W2, m->L.W3, m->wbf);
     ctx->launches += 2;
     return cudaGetLastError();
 }
@@ -370,14 +366,10 @@ ndf_status ensure_work(ndf_model* m, int64_t B) {
     const size_t b = (size_t)B;
     al((void**)&w.fr, b * kLF * 4);
     al((void**)&w.fq, b * kLF * 4);
-    const size_t bs = (b + 7) & ~size_t(7);
     al((void**)&w.x, b * kIn * 2);
-    al((void**)&w.hT, 4 * bs * kHid * 2);
-    al((void**)&w.dzT, 3 * bs * kHid * 2);
-    al((void**)&w.wpart, (size_t)3 * kMlpMaxChunks * kHid * kHid * 4);
+    al((void**)&w.wpart, (size_t)3 * kMlpMaxParts * kHid * kHid * 4);
+    al((void**)&w.cpart, (size_t)kMlpMaxParts * 4 * 5 * kHid * 4);
     al((void**)&w.dx, b * kIn * 4);
-    al((void**)&w.o, b * 4);
-    al((void**)&w.dout, b * 4);
     al((void**)&w.pos, 6 * b * 4);
     al((void**)&w.target, b * 4);
     al((void**)&w.loss, 8);
@@ -403,8 +395,7 @@ cudaError_t model_step(ndf_model* m, const float* pr, const float* pq, const flo
                                                                                  w.fq, w.x);
     ctx->launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = mlp_tc_forward(m, B, target, nullptr)) != cudaSuccess) return e;
-    if ((e = mlp_tc_backward(m, B)) != cudaSuccess) return e;
+    if ((e = mlp_tc_train(m, B, target)) != cudaSuccess) return e;
     encode_bwd_kernel<<<(unsigned)((B * kLevels * 2 * 4 + 255) / 256), 256, 0, s>>>(
         G, pr, pq, B, w.fr, w.fq, w.dx, m->grad);
     ctx->launches++;
@@ -417,7 +408,7 @@ cudaError_t model_step(ndf_model* m, const float* pr, const float* pq, const flo
                                                         m->L.n_grid, m->grid_bf, lr, beta1, beta2,
                                                         eps, c1, c2);
         refresh_mlp_kernel<<<(3 * kHid * kHid + 255) / 256, 256, 0, s>>>(
-            m->params, m->L.W1, m->L.W2, m->L.W3, m->wbf, m->wtbf);
+            m->params, m->L.W1, m->L.W2, m->L.W3, m->wbf);
         ctx->launches += 2;
         e = cudaGetLastError();
     }
@@ -434,7 +425,7 @@ cudaError_t model_forward(ndf_model* m, const float* pr, const float* pq, int64_
     ctx->launches++;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return mlp_tc_forward(m, B, nullptr, out);
+    return mlp_tc_forward(m, B, out);
 }
 
 cudaError_t net_set_attributes() { return cudaSuccess; }  // the tcgen05 kernels set their own

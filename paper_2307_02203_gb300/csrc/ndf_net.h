@@ -30,22 +30,18 @@ struct NetLayout {
     void init(const int r[kLevels]);
 };
 
-// chunks of the batch summed by separate CTAs in the weight gradient
-constexpr int kMlpMaxChunks = 64;
+// CTAs of the training kernel whose weight-gradient sums are kept (at most)
+constexpr int kMlpMaxParts = 256;
 
-// Per-batch work buffers (grown on demand).  The transposed matrices have a row
-// pitch of Bs = B rounded up to 8 samples.
+// Per-batch work buffers (grown on demand).
 struct NetWork {
     int64_t cap = 0;
     float* fr = nullptr;          // [B][64] reference features
     float* fq = nullptr;          // [B][64] query features
     __nv_bfloat16* x = nullptr;   // [B][128] merged input
-    __nv_bfloat16* hT = nullptr;  // [4][128][Bs] x^T and the hidden activations h1^T..h3^T
-    __nv_bfloat16* dzT = nullptr; // [3][128][Bs] pre-activation gradients dz1^T..dz3^T
-    float* wpart = nullptr;       // [3][kMlpMaxChunks][128][128] weight-gradient chunks
+    float* wpart = nullptr;       // [3][kMlpMaxParts][128][128] the training CTAs' weight gradients
+    float* cpart = nullptr;       // [kMlpMaxParts][4][5][128] their bias / output-layer column sums
     float* dx = nullptr;          // [B][128] input gradient
-    float* o = nullptr;           // [B] pre-activation output
-    float* dout = nullptr;        // [B] dL/do
     float* pos = nullptr;         // [2][B][3] positions (when the caller passes host memory)
     float* target = nullptr;      // [B]
     double* loss = nullptr;       // [1]
@@ -65,7 +61,6 @@ struct ndf_model {
     float* v = nullptr;        // Adam second moment
     __nv_bfloat16* grid_bf = nullptr;  // bf16 copy of the grid part
     __nv_bfloat16* wbf = nullptr;      // [3][128][128] bf16 W1..W3 ([out][in])
-    __nv_bfloat16* wtbf = nullptr;     // [3][128][128] bf16 transposes ([in][out])
     int64_t t = 0;             // Adam steps taken
     ndf::NetWork work;
     // training record
@@ -92,13 +87,12 @@ cudaError_t model_step(ndf_model* m, const float* pr, const float* pq, const flo
 cudaError_t net_set_attributes();
 cudaError_t model_forward(ndf_model* m, const float* pr, const float* pq, int64_t B, float* out);
 
-// The MLP on tcgen05 (ndf_mlp_tc.cu), over the merged input in m->work.x:
-// forward (with target: also the transposed activations, the output gradient and
-// the loss sum; without: y = the network output), and the backward (gradients of
-// the three layers and of the output layer added into m->grad; the input gradient
-// in m->work.dx).
-cudaError_t mlp_tc_forward(ndf_model* m, int64_t B, const float* target, float* y);
-cudaError_t mlp_tc_backward(ndf_model* m, int64_t B);
+// The MLP on tcgen05 (ndf_mlp_tc.cu), over the merged input in m->work.x: the
+// forward alone (y = the network output), and the training pass (the L1 loss sum
+// into m->work.loss, the gradients of the three layers and of the output layer
+// added into m->grad, the input gradient in m->work.dx).
+cudaError_t mlp_tc_forward(ndf_model* m, int64_t B, float* y);
+cudaError_t mlp_tc_train(ndf_model* m, int64_t B, const float* target);
 
 // Volume decoding for R references (vertex ids on the device): out[R][N].
 cudaError_t model_infer(ndf_model* m, const int64_t* d_refs, int R, float* out);

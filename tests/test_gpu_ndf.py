@@ -122,6 +122,38 @@ def test_gradients_vs_fp64_oracle(ndf_mod, ctx, measure):
     ndf_mod.ndf_model_free(m)
 
 
+def test_gradient_after_update_steps(ndf_mod, ctx):
+    """Every step starts from a zero gradient: after three update steps (gradient not
+    read back), a fourth step's gradient is checked against the FP64 oracle at the
+    updated parameters with the bound of the test above; a gradient carried over from
+    an earlier step (or a weight-gradient partial of an earlier launch) would add to
+    it."""
+    m = ndf_mod.ndf_model_create(ctx, RES_SMALL, 0, 1, 8, 8, 8)
+    p0 = make_params(40)
+    ndf_mod.ndf_model_set_params(m, p0)
+    rng = np.random.default_rng(41)
+    B = 2048
+    for k in range(3):
+        pr, pq = batch(B, 50 + k)
+        t = rng.uniform(-0.9, 0.9, B).astype(np.float32)
+        ndf_mod.ndf_model_step(m, pr, pq, t, 1e-3, True)
+    p = np.empty_like(p0)
+    ndf_mod.ndf_model_get_params(m, p)
+    assert not np.array_equal(p, p0)
+    pr, pq = batch(B, 60)
+    t = rng.uniform(-0.9, 0.9, B).astype(np.float32)
+    g_gpu = np.empty_like(p)
+    ndf_mod.ndf_model_step(m, pr, pq, t, 0.0, False, g_gpu)
+    shape = oracle.net_shape(RES_SMALL, 16, 128, 0)
+    _, g_ref, g_abs = oracle.ndf_loss_grad_abs(shape, p.astype(np.float64), pr.astype(np.float64),
+                                               pq.astype(np.float64), t.astype(np.float64))
+    gs, _ = groups(RES_SMALL)
+    for name, sl in gs.items():
+        rel_terms = np.linalg.norm(g_gpu[sl] - g_ref[sl]) / max(np.linalg.norm(g_abs[sl]), 1e-30)
+        assert rel_terms <= 2e-2, (name, rel_terms)
+    ndf_mod.ndf_model_free(m)
+
+
 def test_adam_first_step_closed_form(ndf_mod, ctx):
     m = ndf_mod.ndf_model_create(ctx, RES_SMALL, 0, 1, 8, 8, 8)
     p = make_params(30)
