@@ -36,13 +36,16 @@ K_NN = 8
 # one-level slab capture (ncu dram__bytes_read.sum + dram__bytes_write.sum for
 # 88,000 vertices) scaled by the vertices processed (x20): the kernels stream each
 # query column and its sorted copy once (algorithmic 14.08 GB + 7 MB output).
+KSG_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on the "
+                      "250x352x1 slab (88,000 vertices, profiles/), x20 vertices")
 KSG_PRUNED_TRAFFIC_PER_VOLUME = (705.641e6 + 4.142e6) * 20
 KSG_BRUTE_TRAFFIC_PER_VOLUME = (705.845e6 + 4.089e6) * 20
-KSG_BLOCK_TRAFFIC_PER_VOLUME = (704.332e6 + 4.026e6) * 20
+KSG_BLOCK_TRAFFIC_PER_VOLUME = (704.816e6 + 4.344e6) * 20
+KSG_LANES_TRAFFIC_PER_VOLUME = (705.611e6 + 4.147e6) * 20
 KSG_SEARCHES = {  # name: (ndf constant name, kernel at k = 8, DRAM bytes per volume)
     "pruned": ("NDF_KSG_PRUNED", "ksg_pruned_kernel<9>", KSG_PRUNED_TRAFFIC_PER_VOLUME),
     "block": ("NDF_KSG_BLOCK", "ksg_block_kernel<9>", KSG_BLOCK_TRAFFIC_PER_VOLUME),
-    "lanes": ("NDF_KSG_LANES", "ksg_lane_kernel<9>", None),
+    "lanes": ("NDF_KSG_LANES", "ksg_lane_kernel<9>", KSG_LANES_TRAFFIC_PER_VOLUME),
 }
 METRIC = "ms per 1.76M-voxel dependence volume (Pearson + KSG MI k=8, M=1000)"
 
@@ -369,11 +372,16 @@ def measure_sampler(ndf, ctx, fid, stream):
     return res
 
 
-def measure_hash_ndf(ndf, ctx, fid, recipe, stream, args, grid_only=False, n_freq=None):
+def measure_hash_ndf(ndf, ctx, fid, recipe, stream, args, grid_only=False, n_freq=None,
+                     merge=None, paper_recipe=False, act=None, enc_layers=None):
     """The paper's architecture (hash grid, Fourier features, SnakeAlt MLPs, product
     merge) trained on continuous samples renewed every pass (Pearson, self field);
-    decode time per volume and MAE against the exact estimator.  grid_only: the
-    ablation without encoder MLPs (Sec. 6.4)."""
+    decode time per volume and MAE against the exact estimator, beside the best
+    constant volume's.  grid_only: the ablation without encoder MLPs (Sec. 6.4);
+    merge: another merge operator (Sec. 4.1); paper_recipe: the training recipe of
+    Sec. 4.3 run to its end (batch 1000, learning rate 3e-4, 200 passes of 10^6
+    fresh pairs, x0.1 after 5 passes without improvement, stop after 2 decays)
+    instead of the bench's time-boxed one."""
     import torch
 
     N = recipe.N
@@ -382,13 +390,27 @@ def measure_hash_ndf(ndf, ctx, fid, recipe, stream, args, grid_only=False, n_fre
         arch.enc_layers = 0
     if n_freq is not None:
         arch.n_freq = n_freq
+    if merge is not None:
+        arch.merge = merge
+    if act is not None:
+        arch.act = act
+    if enc_layers is not None:
+        arch.enc_layers = enc_layers
     cfg = ndf.ndf_train_cfg_default()
     cfg.n_triples = 1 << 19
     cfg.batch = 1 << 13
     cfg.lr = 1e-3
     cfg.max_decays = 100
     cfg.time_budget_s = float(args.ndf_seconds)
-    # warm-up: the first training steps of a process load kernels and pick GEMM algorithms
+    if paper_recipe:
+        cfg.n_triples = 1000000
+        cfg.batch = 1000
+        cfg.lr = 3e-4
+        cfg.max_passes = 200
+        cfg.patience = 5
+        cfg.max_decays = 2
+        cfg.time_budget_s = 0.0
+    # warm-up: the first training steps of a process load the kernels
     warm = ndf.ndf_hash_model_create(ctx, arch, ndf.NDF_MEASURE_PEARSON, False, 1, recipe.X, recipe.Y,
                                      recipe.Z)
     wp = torch.rand((cfg.batch, 3), device="cuda") * 2 - 1
@@ -427,7 +449,9 @@ def measure_hash_ndf(ndf, ctx, fid, recipe, stream, args, grid_only=False, n_fre
     tc = ndf.ndf_hash_get_decode(model) == ndf.NDF_HASH_DECODE_TC
     paths = [("fp32", ndf.NDF_HASH_DECODE_FP32, False)]
     if tc:
-        paths += [("tc", ndf.NDF_HASH_DECODE_TC, False), ("tc_cached", ndf.NDF_HASH_DECODE_TC, True)]
+        paths += [("tc", ndf.NDF_HASH_DECODE_TC, False)]
+        if arch.enc_layers > 0 and arch.dec_layers >= 2:  # the query-latent cache needs both
+            paths += [("tc_cached", ndf.NDF_HASH_DECODE_TC, True)]
     for name, mode, cache in paths:
         ndf.ndf_hash_set_decode(model, mode, cache)
         first = timed(lambda: ndf.ndf_hash_infer(model, refs[0], dec[0]))  # warm-up (builds a cache)
@@ -445,7 +469,8 @@ def measure_hash_ndf(ndf, ctx, fid, recipe, stream, args, grid_only=False, n_fre
         diff = (vols["tc"] - vols["fp32"]).abs()
         decode["tc"]["vs_fp32_mean_abs"] = float(diff.mean())
         decode["tc"]["vs_fp32_max_abs"] = float(diff.max())
-        decode["tc_cached"]["equals_tc"] = bool(torch.equal(vols["tc_cached"], vols["tc"]))
+        if "tc_cached" in vols:
+            decode["tc_cached"]["equals_tc"] = bool(torch.equal(vols["tc_cached"], vols["tc"]))
         # tensor-core roofline: algorithmic flops of the dense layers per volume
         # multiply-adds per vertex: encoder (din -> c, then c -> c), decoder hidden
         # layers (latent -> c, then c -> c), output layer (c -> 1)
@@ -461,13 +486,22 @@ def measure_hash_ndf(ndf, ctx, fid, recipe, stream, args, grid_only=False, n_fre
         peak = peaks["bf16_tflops"]
         for name, fl, key in (("tc", flop_full, "ms_per_volume_batched"),
                               ("tc_cached", flop_cached, "ms_per_volume_batched")):
+            if name not in decode:
+                continue
             ach = fl / (decode[name][key] * 1e-3) / 1e12
             decode[name]["tensor_tflops"] = ach
             decode[name]["tensor_frac_of_bf16_peak"] = ach / peak
             decode[name]["peak_source"] = peaks["source"]
             decode[name]["algorithmic_gflop_per_volume"] = fl / 1e9
     ndf.ndf_hash_set_decode(model, ndf.NDF_HASH_DECODE_TC if tc else ndf.NDF_HASH_DECODE_FP32)
-    res = {"arch": {n: getattr(arch, n) for n, _ in arch._fields_},
+    ex = exact.reshape(-1)
+    idx = torch.randint(0, ex.numel(), (1 << 20,), device="cuda",
+                        generator=torch.Generator(device="cuda").manual_seed(3))
+    smp = ex[idx]
+    const_mae = float((smp - smp.median()).abs().mean())
+    res = {"arch": {n: getattr(arch, n) for n, _ in arch._fields_}, "const_mae": const_mae,
+           "recipe": "Sec. 4.3 (batch 1000, lr 3e-4, 200 x 1e6 pairs, plateau x0.1)"
+           if paper_recipe else "time-boxed (--ndf-seconds)",
            "params": ndf.ndf_hash_model_param_count(model), "triples_per_pass": int(cfg.n_triples),
            "batch": int(cfg.batch), "passes": info["passes"], "adam_steps": info["adam_steps"],
            "train_seconds": info["train_seconds"], "sample_seconds": info["gen_seconds"],
@@ -539,6 +573,13 @@ def error_statement(ndf, ctx, model, fa, fb, measure, refs, N, stream, cached=No
             "decode_ms_per_volume_16refs": ms_16 / len(refs)}
 
 
+def train_step_bytes(param_count, grid_params):
+    """Algorithmic HBM bytes of one Adam step: the gradient zeroed (4 per parameter),
+    FP32 master, gradient and both moments read (16), master and moments written
+    (12), the grid's BF16 copy written (2 per grid parameter)."""
+    return 32.0 * param_count + 2.0 * grid_params
+
+
 def measure_ndf(ndf, ctx, fid, recipe, stream, args, exact_ms, fid_b=None, mi_first_chunk=None):
     """Learned part: trains a Pearson and a KSG-MI network on the loaded field
     (targets from the GPU estimators), then states the error of the decoded volumes
@@ -570,6 +611,24 @@ def measure_ndf(ndf, ctx, fid, recipe, stream, args, exact_ms, fid_b=None, mi_fi
         cached = mi_first_chunk if name == "mi" else None
         err = error_statement(ndf, ctx, model, fa, fb, measure, refs, N, stream, cached=cached)
         exact = exact_ms[name.split("_")[0]]
+        peaks = load_peaks()
+        # a10 roofline: the network's multiply-adds per (vertex, reference) -- three
+        # 128 x 128 layers (the first on the 128-wide merged input) and the 128-input
+        # output -- against the measured BF16 peak
+        flop = 2.0 * N * (3 * 128 * 128 + 128)
+        tfl = flop / (err["decode_ms_per_volume_16refs"] * 1e-3) / 1e12
+        decode_roofline = {"bound": "tensor", "kernel": "infer_tc_kernel", "achieved": tfl,
+                           "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                           "frac": tfl / peaks["bf16_tflops"], "flop_per_volume": flop,
+                           "peak_source": peaks["source"]}
+        # a9 roofline: the Adam step's algorithmic bytes (train_step_bytes) over the
+        # whole step's time
+        step_ms = 1e3 * max(info["train_seconds"], 1e-9) / max(info["adam_steps"], 1)
+        step_bytes = train_step_bytes(info["param_count"], info["grid_params"])
+        gbs = step_bytes / (step_ms * 1e-3) / 1e9
+        train_roofline = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                          "frac": gbs / peaks["hbm_gbs"], "bytes_per_step": step_bytes,
+                          "ms_per_step": step_ms, "peak_source": peaks["source"]}
         out[name] = {
             "triples": info["n_triples"], "triples_per_s": info["n_triples"] / max(info["gen_seconds"], 1e-9),
             "train_seconds": info["train_seconds"], "adam_steps": info["adam_steps"],
@@ -580,6 +639,7 @@ def measure_ndf(ndf, ctx, fid, recipe, stream, args, exact_ms, fid_b=None, mi_fi
             "exact_ms_per_volume": exact,
             "speedup_vs_exact_16refs": exact / err["decode_ms_per_volume_16refs"],
             "fields": "A->B" if fb != fa else "A->A", **err,
+            "decode_roofline": decode_roofline, "train_roofline": train_roofline,
         }
         if render is not None:
             out[name]["render"] = render
@@ -951,6 +1011,11 @@ def run_case(args, recipe):
     ndf.ndf_synchronize(ctx)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.repeat
+    if args.case == "train-step":
+        mi = ndf.ndf_model_info(m)
+        step_bytes = train_step_bytes(mi["param_count"], mi["grid_params"])
+        info["step_bytes"] = step_bytes
+        info["hbm_frac"] = step_bytes / (ms * 1e-3) / 1e9 / load_peaks()["hbm_gbs"]
     line = {"case": args.case, "workload": workload_name(recipe), "grid_xyz": [X, Y, Z],
             "refs_per_call": R, "ms_per_call": ms, "ms_per_volume": ms / R, **info}
     print(json.dumps(line), flush=True)
@@ -986,7 +1051,11 @@ def main():
     ap.add_argument("--ndf-hash", type=int, default=1,
                     help="also train the paper's hash-grid architecture (continuous samples)")
     ap.add_argument("--ndf-hash-variants", type=int, default=0,
-                    help="also train the L = 4 and grid-only variants of the hash-grid architecture")
+                    help="also train the ablations of the hash-grid architecture: the sum, "
+                         "|difference| and concatenation merges, ReLU encoders, two-layer "
+                         "encoders, L = 4, grid-only")
+    ap.add_argument("--ndf-hash-recipe", type=int, default=0,
+                    help="also train the hash-grid network with the paper's full recipe (minutes)")
     ap.add_argument("--ndf-cross", type=int, default=1,
                     help="also train cross-field networks (reference in A, query in a second field B)")
     ap.add_argument("--ndf-triples", type=int, default=1 << 26, help="Pearson training triples")
@@ -1162,11 +1231,22 @@ def main():
         ndf.ndf_trim_cache(ctx)
     if ndf_res is not None:
         ndf_res["continuous_sampler"] = measure_sampler(ndf, ctx, fid, stream)
-    if args.ndf_hash or args.ndf_hash_variants:
+    if args.ndf_hash or args.ndf_hash_variants or args.ndf_hash_recipe:
         ndf_res = {} if ndf_res is None else ndf_res
         if args.ndf_hash:
             ndf_res["hash_grid_pearson"] = measure_hash_ndf(ndf, ctx, fid, recipe, stream, args)
+        if args.ndf_hash_recipe:
+            ndf_res["hash_grid_pearson_paper_recipe"] = measure_hash_ndf(
+                ndf, ctx, fid, recipe, stream, args, paper_recipe=True)
         if args.ndf_hash_variants:
+            for name, code in (("sum", ndf.NDF_MERGE_SUM), ("absdiff", ndf.NDF_MERGE_ABSDIFF),
+                               ("concat", ndf.NDF_MERGE_CONCAT)):
+                ndf_res[f"hash_grid_pearson_merge_{name}"] = measure_hash_ndf(
+                    ndf, ctx, fid, recipe, stream, args, merge=code)
+            ndf_res["hash_grid_pearson_relu"] = measure_hash_ndf(ndf, ctx, fid, recipe, stream, args,
+                                                                 act=ndf.NDF_ACT_RELU)
+            ndf_res["hash_grid_pearson_enc2"] = measure_hash_ndf(ndf, ctx, fid, recipe, stream, args,
+                                                                 enc_layers=2)
             ndf_res["hash_grid_pearson_L4"] = measure_hash_ndf(ndf, ctx, fid, recipe, stream, args,
                                                                n_freq=4)
             ndf_res["hash_grid_only_pearson"] = measure_hash_ndf(ndf, ctx, fid, recipe, stream,
@@ -1239,10 +1319,11 @@ def main():
             "roofline": {"bound": "alu", "kernel": KSG_SEARCHES[args.ksg_search][1],
                          "achieved": achieved, "peak": peak, "unit": "Gdist/s",
                          "frac": achieved / peak, "traffic": KSG_SEARCHES[args.ksg_search][2],
+                         "traffic_source": KSG_TRAFFIC_SOURCE,
                          "peak_source": f"{peaks['source']} max SM clock",
                          "algorithmic_evals_per_volume": brute_evals,
                          "evals_performed_per_volume": search_evals,
-                         "performed_gdist_s": performed},
+                         "performed_gdist_s": performed, "performed_frac": performed / peak},
             "ksg_brute_force": {"ms": ksg_brute_ms, "kernel": "ksg_volume_kernel<9>",
                                 "roofline": {"bound": "alu", "achieved": brute_achieved,
                                              "peak": peak, "unit": "Gdist/s",
