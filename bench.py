@@ -1279,6 +1279,16 @@ def main():
 
     e2e_per_volume = time_e2e(e2e_volume)
     e2e_sequential = time_e2e(e2e_volume_sequential)
+    # the host link the end-to-end number depends on: one plain copy of the pinned field
+    h2d_dev = torch.empty(field_t.shape, dtype=torch.float32, device="cuda")
+    h2d_gbs = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h2d_dev.copy_(field_t, non_blocking=True)
+        torch.cuda.synchronize()
+        h2d_gbs.append(field.nbytes / (time.perf_counter() - t0) / 1e9)
+    del h2d_dev
 
     # ---- roofline of the dominant kernel (KSG: ALU-bound distance evaluations)
     peaks = load_peaks()
@@ -1335,6 +1345,8 @@ def main():
             "ksg_batch64": ksg_batch,
             "e2e": {"value": e2e_per_volume, "unit": "ms", "call": "ndf_load_and_compute",
                     "sequential_calls_ms": e2e_sequential,
+                    "host_link_gbs": max(h2d_gbs),
+                    "host_link_note": "one pinned-host to device copy of the field, this box",
                     "h2d_bytes_per_step": int(field.nbytes),
                     "d2h_bytes_per_step": int(2 * N * 4)},
             "gpu_launches": int(launches),

@@ -87,13 +87,24 @@ def positions(X, Y, Z):
 
 
 def check(got, want_bf16, want_fp64, what):
+    """The kernel does the BF16-operand oracle's roundings; it differs from it only by
+    its FP32 summation order and by the BF16 rounding flips that order causes, each
+    an error of the same kind and size as the format's own rounding (a flip in the
+    reference latent shifts a whole volume).  So the deviation is gated against the
+    format's own error on the same vertices, |BF16-operand oracle - FP64 oracle|: at
+    most half of it on average and no larger than its largest value, plus the FP32
+    summation-order noise where no flip occurs (1e-6 on the mean, 1e-5 at a vertex;
+    measured ~1e-7).  Against the FP64 oracle the kernel is then within 1.5x the mean
+    and 2x the largest BF16 error by the triangle inequality."""
     e1 = np.abs(got - want_bf16)
     e2 = np.abs(got - want_fp64)
+    ebf = np.abs(want_bf16 - want_fp64)
     print(f"{what}: vs bf16 oracle median {np.median(e1):.2e} mean {e1.mean():.2e} max "
           f"{e1.max():.2e} (within 1e-5: {(e1 <= 1e-5).mean():.0%}); vs fp64 mean {e2.mean():.2e} "
-          f"max {e2.max():.2e}; output std {want_fp64.std():.3f}")
-    assert np.median(e1) <= 1e-2 and e1.mean() <= 1e-2 and e1.max() <= 0.1
-    assert e2.mean() <= 3e-2 and e2.max() <= 0.2
+          f"max {e2.max():.2e}; bf16 oracle vs fp64 mean {ebf.mean():.2e} max {ebf.max():.2e}; "
+          f"output std {want_fp64.std():.3f}")
+    assert e1.mean() <= 0.5 * ebf.mean() + 1e-6
+    assert e1.max() <= ebf.max() + 1e-5
 
 
 def oracle_pair(s, p, pos, r, idx):
