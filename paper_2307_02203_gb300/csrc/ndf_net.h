@@ -57,6 +57,7 @@ struct ndf_model {
     int64_t X = 0, Y = 0, Z = 0;  // ensemble grid the positions refer to
     float* params = nullptr;   // FP32 master [total]
     float* grad = nullptr;     // [total]
+    bool grad_zero = true;     // grad is all zero (cleared by the last Adam step or at allocation)
     float* m = nullptr;        // Adam first moment
     float* v = nullptr;        // Adam second moment
     __nv_bfloat16* grid_bf = nullptr;  // bf16 copy of the grid part
@@ -82,8 +83,10 @@ ndf_status ensure_work(ndf_model* m, int64_t B);
 
 // One step on a batch of device positions (pr, pq: [B][3]) and targets: loss
 // (accumulated in work.loss) and gradients; with update, one Adam step.
+// keep_grad: leave this step's gradient in m->grad after the update (a caller reads it)
 cudaError_t model_step(ndf_model* m, const float* pr, const float* pq, const float* target,
-                       int64_t B, float lr, float beta1, float beta2, float eps, bool update);
+                       int64_t B, float lr, float beta1, float beta2, float eps, bool update,
+                       bool keep_grad = false);
 cudaError_t net_set_attributes();
 cudaError_t model_forward(ndf_model* m, const float* pr, const float* pq, int64_t B, float* out);
 

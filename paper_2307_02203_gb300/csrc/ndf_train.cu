@@ -382,7 +382,8 @@ ndf_status ndf_model_step(ndf_model* m, const float* p_ref, const float* p_query
     ndf_status st = stage_batch(m, p_ref, p_query, target, B, &dpr, &dpq, &dt);
     if (st != NDF_OK) return st;
     cudaError_t e = cudaMemsetAsync(m->work.loss, 0, 8, ctx->stream);
-    if (e == cudaSuccess) e = model_step(m, dpr, dpq, dt, B, lr, 0.9f, 0.999f, 1e-8f, update != 0);
+    if (e == cudaSuccess)
+        e = model_step(m, dpr, dpq, dt, B, lr, 0.9f, 0.999f, 1e-8f, update != 0, grad_out != nullptr);
     if (e == cudaSuccess && grad_out)
         e = cudaMemcpyAsync(grad_out, m->grad, (size_t)m->L.total * 4, cudaMemcpyDefault,
                             ctx->stream);
