@@ -399,14 +399,16 @@ cudaError_t model_step(ndf_model* m, const float* pr, const float* pq, const flo
         m->t += 1;
         const float c1 = (float)(1.0 - pow((double)beta1, (double)m->t));
         const float c2 = (float)(1.0 - pow((double)beta2, (double)m->t));
+        // 64 CTAs per SM, or one thread per group of four parameters if that is fewer
+        const int64_t groups_ctas = ((m->L.total + 3) / 4 + 255) / 256;
+        const unsigned ctas = (unsigned)(groups_ctas < (int64_t)ctx->sm_count * 64 ? groups_ctas
+                                                                                   : (int64_t)ctx->sm_count * 64);
         if (keep_grad)
-            adam_kernel<false><<<ctx->sm_count * 64, 256, 0, s>>>(m->params, m->grad, m->m, m->v, m->L.total,
-                                                                   m->L.n_grid, m->grid_bf, lr, beta1, beta2,
-                                                                   eps, c1, c2);
+            adam_kernel<false><<<ctas, 256, 0, s>>>(m->params, m->grad, m->m, m->v, m->L.total, m->L.n_grid,
+                                                    m->grid_bf, lr, beta1, beta2, eps, c1, c2);
         else
-            adam_kernel<true><<<ctx->sm_count * 64, 256, 0, s>>>(m->params, m->grad, m->m, m->v, m->L.total,
-                                                                  m->L.n_grid, m->grid_bf, lr, beta1, beta2,
-                                                                  eps, c1, c2);
+            adam_kernel<true><<<ctas, 256, 0, s>>>(m->params, m->grad, m->m, m->v, m->L.total, m->L.n_grid,
+                                                   m->grid_bf, lr, beta1, beta2, eps, c1, c2);
         refresh_mlp_kernel<<<(3 * kHid * kHid + 255) / 256, 256, 0, s>>>(
             m->params, m->L.W1, m->L.W2, m->L.W3, m->wbf);
         ctx->launches += 2;
