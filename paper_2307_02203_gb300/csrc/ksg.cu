@@ -755,8 +755,10 @@ __global__ void __launch_bounds__(32 * kGroupWarps * kMaxGroupsPerCta, 1)
             if (valid) {
                 const float e = best[KK - 1];
                 const int self = e > 0.0f ? 1 : 0;
-                const int cx = count_within(xs, M, xi, e) - self;
-                const int cy = count_within(ys, M, yi, e) - self;
+                int cx, cy;
+                count_within_pair(xs, ys, M, pow2_floor(M), xi, yi, e, cx, cy);
+                cx -= self;
+                cy -= self;
                 acc += A.psi[cx + 1] + A.psi[cy + 1];
                 // debug pair: eps by block position (scratch), put in member order below
                 if (dbg) A.dbg_nx[b * kBlk + p] = __float_as_int(e);
@@ -899,15 +901,41 @@ __global__ void __launch_bounds__(32 * kGroupWarps * kMaxGroupsPerCta, 1)
         const int64_t v = A.v_begin + (int64_t)(A.paired ? item : item - (unsigned long long)r * nv);
         const float* xsg = A.xs_all + (int64_t)r * M;  // reference values, x-sorted (global)
         const int* perm = A.perm_all + (int64_t)r * M;
-        for (int s = gt; s < M; s += GT) ys[s] = A.sorted[(int64_t)s * N + v];
+        // ---- the query column in member order (into eps_s, scratch until the search) and
+        // in sorted order; each thread has eight of its strided loads of both in flight
+        // before their stores, so the column costs two memory round trips, not M / 64
+        float* ycol = eps_s;  // nb * kBlk >= M floats
+        for (int s0 = 0; s0 < M; s0 += 8 * GT) {
+            float c8[8], s8[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int s = s0 + j * GT + gt;
+                c8[j] = s < M ? A.field[(int64_t)s * N + v] : 0.0f;
+                s8[j] = s < M ? A.sorted[(int64_t)s * N + v] : 0.0f;
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int s = s0 + j * GT + gt;
+                if (s < M) {
+                    ycol[s] = c8[j];
+                    ys[s] = s8[j];
+                }
+            }
+        }
         // ---- blocks of kBlk x-ranks, each sorted by y; pads (y = x = +inf) sort last
         for (int b = gt; b <= nb; b += GT) blk[b * kBlkStride] = make_float2(INFINITY, INFINITY);
         for (int b = gt; b < nb; b += GT)
             bx[b] = make_float2(xsg[b * kBlk], xsg[min(b * kBlk + kBlk - 1, M - 1)]);
+        group_sync(group);  // the member-order column is complete
         for (int b = gw; b < nb; b += kGroupWarps) {
             float key[kBlkRegs];
             int val[kBlkRegs];
-            block_keys(A, perm, b, v, key, val);
+#pragma unroll
+            for (int r2 = 0; r2 < kBlkRegs; ++r2) {  // the sort keys of block b (shared memory)
+                const int rank = b * kBlk + r2 * 32 + lane;
+                key[r2] = rank < M ? ycol[perm[rank]] : INFINITY;
+                val[r2] = rank;
+            }
             warp_sort_block(key, val);
 #pragma unroll
             for (int r2 = 0; r2 < kBlkRegs; ++r2)
@@ -1033,14 +1061,17 @@ __global__ void __launch_bounds__(32 * kGroupWarps * kMaxGroupsPerCta, 1)
         // ---- marginal counts and the digamma sum, evenly split over the group
         const bool dbg = A.dbg_eps && r == 0 && v == A.v_begin;
         double acc = 0.0;
+        const int top = pow2_floor(M);
         for (int pos = gt; pos < nb * kBlk; pos += GT) {
             const int b = pos / kBlk, p = pos - b * kBlk;
             if (p >= min(kBlk, M - b * kBlk)) continue;
             const float e = eps_s[pos];
             const float2 me = blk[1 + b * kBlkStride + p];
             const int self = e > 0.0f ? 1 : 0;
-            const int cx = count_within(xsg, M, me.y, e) - self;
-            const int cy = count_within(ys, M, me.x, e) - self;
+            int cx, cy;
+            count_within_pair(xsg, ys, M, top, me.y, me.x, e, cx, cy);
+            cx -= self;
+            cy -= self;
             acc += A.psi[cx + 1] + A.psi[cy + 1];
             if (dbg) A.dbg_nx[pos] = __float_as_int(e);  // eps by block position (scratch)
         }

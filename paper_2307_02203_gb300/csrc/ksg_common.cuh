@@ -40,6 +40,30 @@ __device__ __forceinline__ int count_within(const float* a, int n, float c, floa
     return hi > lo ? hi - lo : 0;
 }
 
+// count_within for two arrays at once: na = #{p : |fl(a[p] - c)| < e} in the
+// ascending a[0..n), nb = the same for (b, d).  The four bounds are found by
+// interleaved branchless binary searches over powers of two (top = the largest power
+// of two <= n): each step moves a bound by `step` while the predicate is still false
+// there, so the four dependent load chains overlap.  The predicates are those of
+// count_within and monotone in p, so the counts are identical.
+__device__ __forceinline__ void count_within_pair(const float* __restrict__ a, const float* __restrict__ b,
+                                                  int n, int top, float c, float d, float e, int& na,
+                                                  int& nb) {
+    int la = 0, ha = 0, lb = 0, hb = 0;
+    for (int step = top; step > 0; step >>= 1) {
+        const int i1 = la + step, i2 = ha + step, i3 = lb + step, i4 = hb + step;
+        if (i1 <= n && !((c - a[i1 - 1]) < e)) la = i1;   // first p with fl(c - a[p]) < e
+        if (i2 <= n && !((a[i2 - 1] - c) >= e)) ha = i2;  // first p with fl(a[p] - c) >= e
+        if (i3 <= n && !((d - b[i3 - 1]) < e)) lb = i3;
+        if (i4 <= n && !((b[i4 - 1] - d) >= e)) hb = i4;
+    }
+    na = ha > la ? ha - la : 0;
+    nb = hb > lb ? hb - lb : 0;
+}
+
+// the largest power of two <= n (n >= 1)
+__device__ __forceinline__ int pow2_floor(int n) { return 1 << (31 - __clz(n)); }
+
 // #{p : |fl(a[p] - c)| <= e} in the ascending sequence at(0..n) (non-strict, as
 // KSG algorithm 2 counts), by two binary searches on monotone predicates.
 template <class Get>
