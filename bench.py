@@ -40,8 +40,8 @@ KSG_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one l
                       "250x352x1 slab (88,000 vertices, profiles/), x20 vertices")
 KSG_PRUNED_TRAFFIC_PER_VOLUME = (705.641e6 + 4.142e6) * 20
 KSG_BRUTE_TRAFFIC_PER_VOLUME = (705.845e6 + 4.089e6) * 20
-KSG_BLOCK_TRAFFIC_PER_VOLUME = (704.816e6 + 4.344e6) * 20
-KSG_LANES_TRAFFIC_PER_VOLUME = (705.611e6 + 4.147e6) * 20
+KSG_BLOCK_TRAFFIC_PER_VOLUME = (705.26e6 + 3.64e6) * 20
+KSG_LANES_TRAFFIC_PER_VOLUME = (704.32e6 + 3.37e6) * 20
 KSG_SEARCHES = {  # name: (ndf constant name, kernel at k = 8, DRAM bytes per volume)
     "pruned": ("NDF_KSG_PRUNED", "ksg_pruned_kernel<9>", KSG_PRUNED_TRAFFIC_PER_VOLUME),
     "block": ("NDF_KSG_BLOCK", "ksg_block_kernel<9>", KSG_BLOCK_TRAFFIC_PER_VOLUME),
