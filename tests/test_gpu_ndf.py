@@ -154,6 +154,29 @@ def test_gradient_after_update_steps(ndf_mod, ctx):
     ndf_mod.ndf_model_free(m)
 
 
+def test_mlp_gradients_deterministic(ndf_mod, ctx):
+    """The MLP's weight, bias and output-layer gradients are sums over CTAs and row
+    quarters added in a fixed order, so two identical steps give bit-identical values
+    (the grid gradient is scattered with FP32 atomics and may differ in the last
+    bits; it is checked against the oracle elsewhere)."""
+    m = ndf_mod.ndf_model_create(ctx, RES_SMALL, 0, 1, 8, 8, 8)
+    p = make_params(50)
+    ndf_mod.ndf_model_set_params(m, p)
+    B = 40000  # 313 tiles: several per CTA, a ragged last tile
+    pr, pq = batch(B, 70)
+    t = np.random.default_rng(71).uniform(-0.9, 0.9, B).astype(np.float32)
+    g1 = np.empty_like(p)
+    g2 = np.empty_like(p)
+    l1 = ndf_mod.ndf_model_step(m, pr, pq, t, 0.0, False, g1)
+    l2 = ndf_mod.ndf_model_step(m, pr, pq, t, 0.0, False, g2)
+    gs, _ = groups(RES_SMALL)
+    mlp = slice(gs["W1"].start, gs["b4"].stop)
+    np.testing.assert_array_equal(g1[mlp], g2[mlp])
+    assert np.abs(g1[mlp]).max() > 0.0
+    assert l1 == pytest.approx(l2, rel=1e-12, abs=1e-12)
+    ndf_mod.ndf_model_free(m)
+
+
 def test_adam_first_step_closed_form(ndf_mod, ctx):
     m = ndf_mod.ndf_model_create(ctx, RES_SMALL, 0, 1, 8, 8, 8)
     p = make_params(30)
