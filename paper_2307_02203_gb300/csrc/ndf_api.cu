@@ -4,6 +4,9 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <utility>
+#include <vector>
+
 #include "device_common.cuh"
 #include "ndf_internal.h"
 
@@ -349,14 +352,18 @@ ndf_status ndf_load_ensemble(ndf_ctx* ctx, const float* field, int64_t M, int64_
                                                             : cudaMemcpyHostToDevice;
     int* d_flag = ctx->flag.as<int>();
     // Upload in vertex ranges on the copy stream; the statistics and the column sort of
-    // each range run on the context's stream as soon as that range has arrived.
+    // each range run on the context's stream as soon as that range has arrived.  The
+    // ranges double from the first (short, so the statistics start early) up to 8x its
+    // length: a range is M strided rows, and longer rows copy closer to the link's
+    // contiguous rate.
     int64_t chunk = ((int64_t)(64 << 20) / M + 31) / 32 * 32;
     if (chunk < 1024) chunk = 1024;
     e = cudaMemsetAsync(d_flag, 0, sizeof(int), ctx->stream);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->copy_event, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->copy_stream, ctx->copy_event, 0);
-    for (int64_t v0 = 0; v0 < N && e == cudaSuccess; v0 += chunk) {
-        const int64_t v1 = v0 + chunk < N ? v0 + chunk : N;
+    int64_t len = chunk;
+    for (int64_t v0 = 0; v0 < N && e == cudaSuccess; v0 += len, len = len * 2 < 8 * chunk ? len * 2 : 8 * chunk) {
+        const int64_t v1 = v0 + len < N ? v0 + len : N;
         e = cudaMemcpy2DAsync(f.data + v0, sizeof(float) * (size_t)N, field + v0,
                               sizeof(float) * (size_t)N, sizeof(float) * (size_t)(v1 - v0),
                               (size_t)M, kind, ctx->copy_stream);
@@ -383,7 +390,10 @@ ndf_status ndf_load_ensemble(ndf_ctx* ctx, const float* field, int64_t M, int64_
 
 // Upload, statistics, column sorts and the KSG search pipelined over vertex ranges:
 // range r's search runs on the context's stream while range r + 1 is copied on the
-// copy stream.  The reference's range goes first (both searches stage its column).
+// copy stream.  The reference's range goes first (both searches stage its column)
+// and is short, so the search starts early; the rest of the grid follows in ranges
+// that double up to 8x that length (a range is M strided rows, and longer rows copy
+// closer to the link's contiguous rate; fewer ranges also mean fewer search launches).
 ndf_status ndf_load_and_compute(ndf_ctx* ctx, const float* field, int64_t M, int64_t Z, int64_t Y,
                                 int64_t X, int64_t ref_idx, int k, float* pearson_out,
                                 float* mi_out, int* field_id_out) {
@@ -426,13 +436,27 @@ ndf_status ndf_load_and_compute(ndf_ctx* ctx, const float* field, int64_t M, int
     int* d_flag = ctx->flag.as<int>();
     int64_t chunk = ((int64_t)(64 << 20) / M + 31) / 32 * 32;
     if (chunk < 1024) chunk = 1024;
-    const int64_t nchunks = (N + chunk - 1) / chunk, cref = ref_idx / chunk;
+    std::vector<std::pair<int64_t, int64_t>> ranges;
+    {
+        const int64_t r0 = ref_idx / chunk * chunk, r1 = r0 + chunk < N ? r0 + chunk : N;
+        ranges.push_back({r0, r1});
+        int64_t len = 2 * chunk;
+        auto cover = [&](int64_t lo, int64_t hi) {
+            for (int64_t v = lo; v < hi;) {
+                const int64_t w = v + len < hi ? v + len : hi;
+                ranges.push_back({v, w});
+                v = w;
+                len = len * 2 < 8 * chunk ? len * 2 : 8 * chunk;
+            }
+        };
+        cover(r1, N);
+        cover(0, r0);
+    }
     e = cudaMemsetAsync(d_flag, 0, sizeof(int), ctx->stream);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->copy_event, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->copy_stream, ctx->copy_event, 0);
-    for (int64_t q = 0; q < nchunks && e == cudaSuccess; ++q) {
-        const int64_t c = q == 0 ? cref : (q <= cref ? q - 1 : q);  // the reference's range first
-        const int64_t v0 = c * chunk, v1 = v0 + chunk < N ? v0 + chunk : N;
+    for (size_t q = 0; q < ranges.size() && e == cudaSuccess; ++q) {
+        const int64_t v0 = ranges[q].first, v1 = ranges[q].second;
         e = cudaMemcpy2DAsync(f.data + v0, sizeof(float) * (size_t)N, field + v0, sizeof(float) * (size_t)N,
                               sizeof(float) * (size_t)(v1 - v0), (size_t)M, kind, ctx->copy_stream);
         if (e == cudaSuccess) e = cudaEventRecord(ctx->copy_event, ctx->copy_stream);

@@ -58,18 +58,19 @@ def test_load_statistics(ndf_mod, ctx, tiny_field):
 
 
 def test_chunked_upload_statistics_and_sorted_columns(ndf_mod, ctx):
-    """M = 4096 uploads in ranges of 16384 vertices: three ranges with a ragged
-    tail.  Statistics and KSG counts (which search the sorted columns) must hold
-    at the range boundaries."""
-    M, N = 4096, 2 * 16384 + 77
+    """M = 4096 uploads in ranges that double from 16384 vertices: 16384, 32768
+    and a ragged tail of 77.  Statistics and KSG counts (which search the sorted
+    columns) must hold at the range boundaries."""
+    M, N = 4096, 16384 + 32768 + 77
     rng = np.random.default_rng(99)
     f = rng.normal(size=(M, 1, 1, N)).astype(np.float32)
     f[:, 0, 0, 16383:16386] += 2.0 * f[:, 0, 0, 5:8]  # dependence across a boundary
+    f[:, 0, 0, 49150:49153] += 2.0 * f[:, 0, 0, 9:12]
     fid = load(ndf_mod, ctx, f)
     mean = np.empty(N)
     inv = np.empty(N)
     ndf_mod.ndf_field_stats(ctx, fid, mean, inv)
-    cols = [0, 16383, 16384, 32767, 32768, N - 1]
+    cols = [0, 16383, 16384, 49151, 49152, N - 1]
     f64 = f.reshape(M, N)[:, cols].astype(np.float64)
     mu = f64.mean(axis=0)
     np.testing.assert_allclose(mean[cols], mu, rtol=0, atol=1e-5 * np.abs(f64).max())
