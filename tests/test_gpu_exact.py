@@ -443,6 +443,33 @@ def test_load_and_compute_matches_separate_calls(ndf_mod, ctx):
     ndf.ndf_free_ensemble(ctx, fid3)
 
 
+def test_load_and_compute_growing_ranges(ndf_mod, ctx):
+    """Ranges that double after the reference's: at M = 1024 (base range 65,536
+    vertices) and 458,752 vertices with the reference in the fourth base range, the
+    call uploads [196,608, 262,144), then 131,072 and 65,536 vertices above it and
+    196,608 below; the volumes must be bit-equal to a plain load and the separate
+    calls."""
+    ndf = ndf_mod
+    shape = (1024, 7, 256, 256)
+    f = rand_field(shape, 33)
+    M, Z, Y, X = shape
+    N = Z * Y * X
+    ref = 3 * 65536 + 1234
+    fid = load(ndf, ctx, f)
+    p1 = torch.empty(N, dtype=torch.float32, device="cuda")
+    m1 = torch.empty(N, dtype=torch.float32, device="cuda")
+    ndf.ndf_pearson(ctx, fid, fid, ref, p1)
+    ndf.ndf_mi_ksg(ctx, fid, fid, ref, 8, m1)
+    ndf.ndf_free_ensemble(ctx, fid)
+    p2 = torch.empty(N, dtype=torch.float32, device="cuda")
+    m2 = torch.empty(N, dtype=torch.float32, device="cuda")
+    fid2 = ndf.ndf_load_and_compute(ctx, f, M, Z, Y, X, ref, 8, p2, m2)
+    ndf.ndf_synchronize(ctx)
+    assert torch.equal(p1, p2)
+    assert torch.equal(m1, m2)
+    ndf.ndf_free_ensemble(ctx, fid2)
+
+
 def test_load_and_compute_rejects_bad_input(ndf_mod, ctx, tiny_field, tiny_ref):
     ndf = ndf_mod
     f = tiny_field.copy()
