@@ -1202,6 +1202,17 @@ def main():
                      "ms": time_search(getattr(ndf, KSG_SEARCHES[name][0]))}
               for name in sorted(KSG_SEARCHES) if name != args.ksg_search}
     ndf.ndf_set_ksg_algorithm(ctx, search, False)
+    # KSG algorithm 2 (non-strict counts within the k-NN set's marginal extents): one
+    # volume per reference, after a warm-up call
+    ndf.ndf_mi_ksg2(ctx, fid, fid, refs[args.warmup], K_NN, out_mi)
+    b0 = torch.cuda.Event(enable_timing=True)
+    b1 = torch.cuda.Event(enable_timing=True)
+    b0.record(stream)
+    for i in range(nb):
+        ndf.ndf_mi_ksg2(ctx, fid, fid, refs[args.warmup + i], K_NN, out_mi)
+    b1.record(stream)
+    ndf.ndf_synchronize(ctx)
+    ksg2_ms = b0.elapsed_time(b1) / nb
     # ---- batched KSG: 16 references in one launch
     ksg_batch, mi_first_chunk = None, None
     if args.ksg_batch:
@@ -1342,6 +1353,7 @@ def main():
                                              "evals_per_volume": brute_evals},
                                 "speedup_of_timed_search": ksg_brute_ms / ksg_ms},
             "ksg_other_searches": others,
+            "ksg2_ms": ksg2_ms,
             "ksg_batch64": ksg_batch,
             "e2e": {"value": e2e_per_volume, "unit": "ms", "call": "ndf_load_and_compute",
                     "sequential_calls_ms": e2e_sequential,
