@@ -642,6 +642,44 @@ __device__ __forceinline__ int block_lower_bound(const float2* blk, float y) {
     return pos;
 }
 
+// KSG algorithm 2 over the block layout: the largest fl(|x_j - xi|) and fl(|y_j - yi|)
+// over the members j whose max-norm distance to (xi, yi) is <= e (the member itself adds
+// zeros).  Blocks from the member's own block b0 outward in x while the block's nearest
+// x-rank is within e (fl(x_j - xi) is monotone in x_j); inside a block, outward in y
+// from the lower bound of yi while |dy| <= e (the +inf separators stop both scans).
+__device__ __forceinline__ void block_extents(const float2* blk, const float2* bx, int nb, int b0, float xi,
+                                              float yi, float e, float& ex, float& ey) {
+    ex = 0.0f;
+    ey = 0.0f;
+    auto scan = [&](int bb) {
+        const float2* B = blk + 1 + bb * kBlkStride;  // (y, x), ascending y
+        const int pos = block_lower_bound(B, yi);
+        for (int u = pos;; ++u) {
+            const float2 c = B[u];
+            const float dy = fabsf(c.x - yi);
+            if (!(dy <= e)) break;
+            const float dx = fabsf(c.y - xi);
+            if (dx <= e) {
+                ex = fmaxf(ex, dx);
+                ey = fmaxf(ey, dy);
+            }
+        }
+        for (int u = pos - 1;; --u) {
+            const float2 c = B[u];
+            const float dy = fabsf(yi - c.x);
+            if (!(dy <= e)) break;
+            const float dx = fabsf(c.y - xi);
+            if (dx <= e) {
+                ex = fmaxf(ex, dx);
+                ey = fmaxf(ey, dy);
+            }
+        }
+    };
+    scan(b0);
+    for (int bb = b0 + 1; bb < nb && bx[bb].x - xi <= e; ++bb) scan(bb);
+    for (int bb = b0 - 1; bb >= 0 && xi - bx[bb].y <= e; --bb) scan(bb);
+}
+
 template <int K1>
 __global__ void __launch_bounds__(32 * kGroupWarps * kMaxGroupsPerCta, 1)
     ksg_block_kernel(KsgArgs A, unsigned long long* work) {
@@ -835,7 +873,8 @@ __global__ void __launch_bounds__(32 * kGroupWarps * kMaxGroupsPerCta, 1)
 //     or no lane is scanning, so the divergent code runs for many lanes at once;
 //   - every other lock step is the scan step of the block kernel for all lanes;
 //   - the marginal counts and the digamma sum follow in an evenly split pass over
-//     the stored eps.
+//     the stored eps (for KSG algorithm 2 after the marginal extents of each member's
+//     k-NN set, found over the same blocks: block_extents).
 // A lock-step model of both schedules on csens-like pairs (M = 1000, k = 8) counts
 // about 600 lock steps per pair here against about 1300 for the block kernel (lane
 // utilisation 0.70 against 0.33).  Members are handed out in the block kernel's task
@@ -1067,12 +1106,19 @@ __global__ void __launch_bounds__(32 * kGroupWarps * kMaxGroupsPerCta, 1)
             if (p >= min(kBlk, M - b * kBlk)) continue;
             const float e = eps_s[pos];
             const float2 me = blk[1 + b * kBlkStride + p];
-            const int self = e > 0.0f ? 1 : 0;
             int cx, cy;
-            count_within_pair(xsg, ys, M, top, me.y, me.x, e, cx, cy);
-            cx -= self;
-            cy -= self;
-            acc += A.psi[cx + 1] + A.psi[cy + 1];
+            if (A.variant == 2) {  // non-strict counts within the k-NN set's marginal extents
+                float ex, ey;
+                block_extents(blk, bx, nb, b, me.y, me.x, e, ex, ey);
+                count_le_pair(xsg, ys, M, top, me.y, ex, me.x, ey, cx, cy);
+                acc += A.psi[cx - 1] + A.psi[cy - 1];  // the member itself excluded
+            } else {
+                const int self = e > 0.0f ? 1 : 0;
+                count_within_pair(xsg, ys, M, top, me.y, me.x, e, cx, cy);
+                cx -= self;
+                cy -= self;
+                acc += A.psi[cx + 1] + A.psi[cy + 1];
+            }
             if (dbg) A.dbg_nx[pos] = __float_as_int(e);  // eps by block position (scratch)
         }
         if (dbg) {
@@ -1102,6 +1148,15 @@ __global__ void __launch_bounds__(32 * kGroupWarps * kMaxGroupsPerCta, 1)
                     const int mi = perm[val[r2]];
                     const float e = A.dbg_eps[mi];
                     const float2 me = blk[1 + bq * kBlkStride + r2 * 32 + lane];
+                    if (A.variant == 2) {  // extents, then non-strict counts (self excluded)
+                        float ex, ey;
+                        block_extents(blk, bx, nb, bq, me.y, me.x, e, ex, ey);
+                        A.dbg_eps[mi] = ex;
+                        if (A.dbg_ey) A.dbg_ey[mi] = ey;
+                        A.dbg_nx[mi] = count_le([&](int j) { return xsg[j]; }, M, me.y, ex) - 1;
+                        A.dbg_ny[mi] = count_le([&](int j) { return ys[j]; }, M, me.x, ey) - 1;
+                        continue;
+                    }
                     const int self = e > 0.0f ? 1 : 0;
                     if (A.dbg_ey) A.dbg_ey[mi] = e;
                     A.dbg_nx[mi] = count_within(xsg, M, me.y, e) - self;
@@ -1118,7 +1173,7 @@ __global__ void __launch_bounds__(32 * kGroupWarps * kMaxGroupsPerCta, 1)
             double tot = 0.0;
 #pragma unroll
             for (int w = 0; w < kGroupWarps; ++w) tot += ctl->part[w];
-            const double mi = psi_k + psi_M - tot / (double)M;
+            const double mi = psi_k - (A.variant == 2 ? 1.0 / A.k : 0.0) + psi_M - tot / (double)M;
             A.out[A.paired ? (v - A.v_begin) : (int64_t)r * A.out_stride + (v - A.v_begin)] = (float)mi;
             if (dbg && A.dbg_mi) *A.dbg_mi = mi;
         }
@@ -1145,7 +1200,7 @@ static cudaError_t launch_persistent(ndf_ctx* ctx, Kern kern, const KsgArgs& A, 
 template <int K1>
 static cudaError_t launch_ksg_k(ndf_ctx* ctx, KsgArgs A, bool prune) {
     const int M = A.M;
-    if (prune && ctx->ksg_algorithm == NDF_KSG_LANES && A.variant == 1) {
+    if (prune && ctx->ksg_algorithm == NDF_KSG_LANES && (A.variant == 1 || A.variant == 2)) {
         // two-warp groups per pair; as many groups per CTA as fit in shared memory
         const size_t per_group = lane_group_bytes(M);
         int gpc = (int)((227 * 1024) / per_group);

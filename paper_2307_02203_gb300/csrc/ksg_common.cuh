@@ -61,6 +61,24 @@ __device__ __forceinline__ void count_within_pair(const float* __restrict__ a, c
     nb = hb > lb ? hb - lb : 0;
 }
 
+// The non-strict counts of KSG algorithm 2 for two arrays at once, by the same
+// interleaved searches: na = #{p : |fl(a[p] - c)| <= ea}, nb = #{p : |fl(b[p] - d)| <= eb}
+// (the predicates of count_le).
+__device__ __forceinline__ void count_le_pair(const float* __restrict__ a, const float* __restrict__ b, int n,
+                                              int top, float c, float ea, float d, float eb, int& na,
+                                              int& nb) {
+    int la = 0, ha = 0, lb = 0, hb = 0;
+    for (int step = top; step > 0; step >>= 1) {
+        const int i1 = la + step, i2 = ha + step, i3 = lb + step, i4 = hb + step;
+        if (i1 <= n && !((c - a[i1 - 1]) <= ea)) la = i1;  // first p with fl(c - a[p]) <= ea
+        if (i2 <= n && !((a[i2 - 1] - c) > ea)) ha = i2;   // first p with fl(a[p] - c) > ea
+        if (i3 <= n && !((d - b[i3 - 1]) <= eb)) lb = i3;
+        if (i4 <= n && !((b[i4 - 1] - d) > eb)) hb = i4;
+    }
+    na = ha > la ? ha - la : 0;
+    nb = hb > lb ? hb - lb : 0;
+}
+
 // the largest power of two <= n (n >= 1)
 __device__ __forceinline__ int pow2_floor(int n) { return 1 << (31 - __clz(n)); }
 
