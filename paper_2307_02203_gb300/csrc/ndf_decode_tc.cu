@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) infer_tc_kernel(const TcInferAr
             while ((left[0] > 0 || left[1] > 0) && !*abort_flag) {
                 bool progressed = false;
                 for (int s = 0; s < 2; ++s) {
-                    if (left[s] == 0 || !try_wait(&a_ready[s], na[s] & 1u)) continue;
+                    if (left[s] == 0 || !test_wait(&a_ready[s], na[s] & 1u)) continue;
                     progressed = true;
                     ++na[s];
                     tc_fence_after();

@@ -90,7 +90,7 @@ __device__ void mma_loop(unsigned char* smem, uint32_t tmem, uint64_t* a_ready, 
     while ((left[0] > 0 || left[1] > 0) && !*abort_flag) {
         bool progressed = false;
         for (int s = 0; s < 2; ++s) {
-            if (left[s] == 0 || !try_wait(&a_ready[s], na[s] & 1u)) continue;
+            if (left[s] == 0 || !test_wait(&a_ready[s], na[s] & 1u)) continue;
             progressed = true;
             ++na[s];
             tc_fence_after();

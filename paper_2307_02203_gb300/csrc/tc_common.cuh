@@ -69,6 +69,21 @@ __device__ __forceinline__ bool try_wait(uint64_t* bar, uint32_t parity) {
     return done != 0;
 }
 
+// non-blocking probe of an mbarrier phase: returns at once (try_wait may suspend the
+// thread for a system-dependent time, which a loop serving several barriers must avoid:
+// one barrier's wait would delay another that is already complete)
+__device__ __forceinline__ bool test_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
 __device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
     uint64_t t0 = 0;
     for (uint32_t i = 0; i < kWaitPolls; ++i) {
