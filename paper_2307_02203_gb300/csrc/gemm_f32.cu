@@ -109,16 +109,31 @@ __global__ void reduce_parts_kernel(const float* __restrict__ part, int64_t S, i
     }
 }
 
-// part[z][n] = sum of A[k][n] over the k of chunk z (threads along n: coalesced)
-__global__ void colsum_parts_kernel(const float* __restrict__ A, int64_t K, int64_t N,
-                                    int64_t k_chunk, float* __restrict__ part) {
-    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
+// part[z][n] = sum of A[k][n] over the k of chunk z: a CTA of 32 columns x kColLanes
+// row lanes (a warp reads 32 consecutive columns of one row); lane y sums the rows
+// k_begin + y, + kColLanes, ... in order, then the lanes' sums are added in order
+constexpr int kColLanes = 8;
+__global__ void __launch_bounds__(32 * kColLanes)
+    colsum_parts_kernel(const float* __restrict__ A, int64_t K, int64_t N, int64_t k_chunk,
+                        float* __restrict__ part) {
+    __shared__ float red[kColLanes][32];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t n = (int64_t)blockIdx.x * 32 + tx;
     const int64_t k_begin = (int64_t)blockIdx.y * k_chunk;
     const int64_t k_end = k_begin + k_chunk < K ? k_begin + k_chunk : K;
     float s = 0.0f;
-    for (int64_t k = k_begin; k < k_end; ++k) s += A[k * N + n];
-    part[(int64_t)blockIdx.y * N + n] = s;
+    if (n < N) {
+#pragma unroll 8
+        for (int64_t k = k_begin + ty; k < k_end; k += kColLanes) s += A[k * N + n];
+    }
+    red[ty][tx] = s;
+    __syncthreads();
+    if (ty == 0 && n < N) {
+        float t = 0.0f;
+#pragma unroll
+        for (int y = 0; y < kColLanes; ++y) t += red[y][tx];
+        part[(int64_t)blockIdx.y * N + n] = t;
+    }
 }
 
 template <bool TA, bool TB>
@@ -168,7 +183,7 @@ cudaError_t colsum_f32_acc(cudaStream_t s, const float* A, float* out, int64_t K
     int64_t splits = K < kSplitK * 256 ? (K + 255) / 256 : kSplitK;
     const int64_t k_chunk = (K + splits - 1) / splits;
     splits = (K + k_chunk - 1) / k_chunk;
-    colsum_parts_kernel<<<dim3((unsigned)((N + 127) / 128), (unsigned)splits), 128, 0, s>>>(
+    colsum_parts_kernel<<<dim3((unsigned)((N + 31) / 32), (unsigned)splits), 32 * kColLanes, 0, s>>>(
         A, K, N, k_chunk, work);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
