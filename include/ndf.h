@@ -85,12 +85,16 @@ int64_t ndf_index(int64_t x, int64_t y, int64_t z, int64_t X, int64_t Y, int64_t
 
 /* Copy field[M][Z][Y][X] (host or device) into context-owned device memory and
  * compute the per-vertex statistics used by Eq. 1: the FP64 mean mu_v and
- * 1/sqrt(S_v) with S_v = sum_m (e_m(v) - mu_v)^2 (two passes, FP64 across
- * member blocks).  For M <= 4096 every vertex column is also sorted into a
+ * 1/sqrt(S_v) with S_v = sum_m (e_m(v) - mu_v)^2 (FP32 sums over blocks of
+ * at most 32 members, centred on the column's median member for M <= 1024 and on
+ * its FP32 mean above, the blocks combined in double-float or FP64; relative
+ * error of order 1e-7).  For M <= 4096 every vertex column is also sorted into a
  * second M*N*4-byte buffer (the KSG marginal counts of Algorithm 1 search it).
- * The copy runs in vertex ranges on an internal stream, the statistics and sorts
- * of each range follow on the context's stream; the call returns when all is
- * done.  Requires M >= 2 and finite values (NDF_ERR_ARG otherwise; the check
+ * A host field is copied in vertex ranges on an internal stream, the statistics
+ * and sorts of each range following on the context's stream; a device field is
+ * read in place by one kernel that writes the copy, the statistics and the sorted
+ * columns (M <= 1024; a contiguous copy first above that).  The call returns when
+ * all is done.  Requires M >= 2 and finite values (NDF_ERR_ARG otherwise; the check
  * reads the copied field).  Writes the new field's id. */
 ndf_status ndf_load_ensemble(ndf_ctx* ctx, const float* field, int64_t M, int64_t Z, int64_t Y,
                              int64_t X, int* field_id_out);
@@ -103,10 +107,11 @@ ndf_status ndf_free_ensemble(ndf_ctx* ctx, int field_id);
 
 /* Load an ensemble (as ndf_load_ensemble) and compute one reference vertex's
  * Pearson volume (Sec. 3.1) and KSG-MI volume (algorithm 1, Sec. 3.2) with the
- * upload pipelined against the computation: the field is copied in vertex ranges
- * (the reference's range first) on the context's copy stream, and each range's
- * statistics, column sort and KSG search run on the context's stream as soon as
- * it has arrived; Pearson follows the last range.  The same kernels as
+ * upload pipelined against the computation: a host field is copied in vertex
+ * ranges (the reference's range first) on the context's copy stream, and each
+ * range's statistics, column sort and KSG search run on the context's stream as
+ * soon as it has arrived (a device field is read in place, range by range, the
+ * sorts writing the copy); Pearson follows the last range.  The same kernels as
  * ndf_load_ensemble + ndf_pearson + ndf_mi_ksg, so the same results.  Outputs
  * (host or device, N floats each) may be NULL to skip that measure.  The field
  * stays loaded (*field_id_out).  Errors as ndf_load_ensemble, ndf_pearson and
@@ -134,6 +139,15 @@ ndf_status ndf_field_shape(const ndf_ctx* ctx, int field_id, int64_t* M, int64_t
 /* Copy the per-vertex statistics (N doubles each, host or device; either may
  * be NULL): mean_out = mu_v, inv_norm_out = 1/sqrt(S_v) (0 where S_v = 0). */
 ndf_status ndf_field_stats(ndf_ctx* ctx, int field_id, double* mean_out, double* inv_norm_out);
+
+/* Copy the sorted member columns of vertices [v_begin, v_end) into out (host or
+ * device, caller-owned): out[m * (v_end - v_begin) + (v - v_begin)] is the m-th
+ * smallest of e_1(v) .. e_M(v), the order the KSG marginal counts of Algorithm 1
+ * search.  Needs 0 <= v_begin <= v_end <= N (NDF_ERR_ARG otherwise) and a field
+ * with M <= 4096, whose sorted copy is made on load (NDF_ERR_STATE above that).
+ * Synchronizes the context's stream. */
+ndf_status ndf_field_sorted_columns(ndf_ctx* ctx, int field_id, int64_t v_begin, int64_t v_end,
+                                    float* out);
 
 /* ---- exact estimators ---------------------------------------------------- */
 

@@ -326,6 +326,19 @@ int64_t ndf_index(int64_t x, int64_t y, int64_t z, int64_t X, int64_t Y, int64_t
     return (z * Y + y) * X + x;
 }
 
+// The statistics of vertices [v0, v1) and, when wanted, their sorted columns: up to
+// 1024 members one sort launch writes both (reading src when given, a device field
+// that it also copies into f.data), above that the statistics kernel and the
+// shared-memory sort read f.data.
+static cudaError_t stats_and_sorts(ndf_ctx* ctx, const Field& f, int64_t v0, int64_t v1, bool want_sorted,
+                                   const float* src, int* d_flag) {
+    if (want_sorted && f.M <= kSortTileMaxM) return launch_sort_columns(ctx, f, v0, v1, ctx->stream, src, d_flag);
+    if (src) return cudaErrorInvalidValue;
+    cudaError_t e = launch_field_stats(ctx, f, v0, v1, d_flag);
+    if (e == cudaSuccess && want_sorted) e = launch_sort_columns(ctx, f, v0, v1, ctx->stream);
+    return e;
+}
+
 ndf_status ndf_load_ensemble(ndf_ctx* ctx, const float* field, int64_t M, int64_t Z, int64_t Y,
                              int64_t X, int* field_id_out) {
     if (!ctx) return NDF_ERR_ARG;
@@ -351,26 +364,34 @@ ndf_status ndf_load_ensemble(ndf_ctx* ctx, const float* field, int64_t M, int64_
     cudaMemcpyKind kind = pointer_kind(field) == PTR_DEVICE ? cudaMemcpyDeviceToDevice
                                                             : cudaMemcpyHostToDevice;
     int* d_flag = ctx->flag.as<int>();
-    // Upload in vertex ranges on the copy stream; the statistics and the column sort of
-    // each range run on the context's stream as soon as that range has arrived.  The
-    // ranges double from the first (short, so the statistics start early) up to 8x its
-    // length: a range is M strided rows, and longer rows copy closer to the link's
-    // contiguous rate.
+    // A host field is uploaded in vertex ranges on the copy stream; the statistics and
+    // the column sort of each range run on the context's stream as soon as that range
+    // has arrived.  The ranges double from the first (short, so the statistics start
+    // early) up to 8x its length: a range is M strided rows, and longer rows copy closer
+    // to the link's contiguous rate.  A device field needs no ranges (below).
     int64_t chunk = ((int64_t)(64 << 20) / M + 31) / 32 * 32;
     if (chunk < 1024) chunk = 1024;
     e = cudaMemsetAsync(d_flag, 0, sizeof(int), ctx->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(ctx->copy_event, ctx->stream);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->copy_stream, ctx->copy_event, 0);
-    int64_t len = chunk;
-    for (int64_t v0 = 0; v0 < N && e == cudaSuccess; v0 += len, len = len * 2 < 8 * chunk ? len * 2 : 8 * chunk) {
-        const int64_t v1 = v0 + len < N ? v0 + len : N;
-        e = cudaMemcpy2DAsync(f.data + v0, sizeof(float) * (size_t)N, field + v0,
-                              sizeof(float) * (size_t)N, sizeof(float) * (size_t)(v1 - v0),
-                              (size_t)M, kind, ctx->copy_stream);
-        if (e == cudaSuccess) e = cudaEventRecord(ctx->copy_event, ctx->copy_stream);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->copy_event, 0);
-        if (e == cudaSuccess) e = launch_field_stats(ctx, f, v0, v1, d_flag);
-        if (e == cudaSuccess && want_sorted) e = launch_sort_columns(ctx, f, v0, v1, ctx->stream);
+    if (e == cudaSuccess && kind == cudaMemcpyDeviceToDevice) {
+        // A device-resident field needs no ranges: up to 1024 members one sort launch
+        // reads it in place and writes the copy, the statistics and the sorted columns;
+        // above that one contiguous copy comes first.
+        const bool fused = want_sorted && M <= kSortTileMaxM;
+        if (!fused) e = cudaMemcpyAsync(f.data, field, bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+        if (e == cudaSuccess) e = stats_and_sorts(ctx, f, 0, N, want_sorted, fused ? field : nullptr, d_flag);
+    } else {
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->copy_event, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->copy_stream, ctx->copy_event, 0);
+        int64_t len = chunk;
+        for (int64_t v0 = 0; v0 < N && e == cudaSuccess; v0 += len, len = len * 2 < 8 * chunk ? len * 2 : 8 * chunk) {
+            const int64_t v1 = v0 + len < N ? v0 + len : N;
+            e = cudaMemcpy2DAsync(f.data + v0, sizeof(float) * (size_t)N, field + v0,
+                                  sizeof(float) * (size_t)N, sizeof(float) * (size_t)(v1 - v0),
+                                  (size_t)M, kind, ctx->copy_stream);
+            if (e == cudaSuccess) e = cudaEventRecord(ctx->copy_event, ctx->copy_stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->copy_event, 0);
+            if (e == cudaSuccess) e = stats_and_sorts(ctx, f, v0, v1, want_sorted, nullptr, d_flag);
+        }
     }
     int nonfinite = 0;
     if (e == cudaSuccess)
@@ -452,17 +473,26 @@ ndf_status ndf_load_and_compute(ndf_ctx* ctx, const float* field, int64_t M, int
         cover(r1, N);
         cover(0, r0);
     }
+    // A device-resident field is not copied range by range: up to 1024 members each
+    // range's sort launch reads the source and writes the copy as it goes; otherwise
+    // one contiguous copy comes first.
+    const bool dev = kind == cudaMemcpyDeviceToDevice;
+    const bool dev_fused = dev && want_sorted && M <= kSortTileMaxM;
     e = cudaMemsetAsync(d_flag, 0, sizeof(int), ctx->stream);
+    if (e == cudaSuccess && dev && !dev_fused)
+        e = cudaMemcpyAsync(f.data, field, bytes, cudaMemcpyDeviceToDevice, ctx->stream);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->copy_event, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->copy_stream, ctx->copy_event, 0);
     for (size_t q = 0; q < ranges.size() && e == cudaSuccess; ++q) {
         const int64_t v0 = ranges[q].first, v1 = ranges[q].second;
-        e = cudaMemcpy2DAsync(f.data + v0, sizeof(float) * (size_t)N, field + v0, sizeof(float) * (size_t)N,
-                              sizeof(float) * (size_t)(v1 - v0), (size_t)M, kind, ctx->copy_stream);
-        if (e == cudaSuccess) e = cudaEventRecord(ctx->copy_event, ctx->copy_stream);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->copy_event, 0);
-        if (e == cudaSuccess) e = launch_field_stats(ctx, f, v0, v1, d_flag);
-        if (e == cudaSuccess && want_sorted) e = launch_sort_columns(ctx, f, v0, v1, ctx->stream);
+        if (!dev) {
+            e = cudaMemcpy2DAsync(f.data + v0, sizeof(float) * (size_t)N, field + v0, sizeof(float) * (size_t)N,
+                                  sizeof(float) * (size_t)(v1 - v0), (size_t)M, kind, ctx->copy_stream);
+            if (e == cudaSuccess) e = cudaEventRecord(ctx->copy_event, ctx->copy_stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->copy_event, 0);
+        }
+        if (e == cudaSuccess)
+            e = stats_and_sorts(ctx, f, v0, v1, want_sorted, dev_fused ? field : nullptr, d_flag);
         if (e == cudaSuccess && mi_out)
             e = launch_ksg(ctx, f, f, nullptr, ref_idx, 1, k, v0, v1, dm + v0, 0,
                            ctx->ksg_algorithm != NDF_KSG_BRUTE, 1, ctx->ksg_tile, nullptr, nullptr,
@@ -547,6 +577,30 @@ ndf_status ndf_field_stats(ndf_ctx* ctx, int field_id, double* mean_out, double*
         e = cudaMemcpyAsync(inv_norm_out, f.inv_norm, bytes, cudaMemcpyDefault, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "statistics copy");
+    return NDF_OK;
+}
+
+ndf_status ndf_field_sorted_columns(ndf_ctx* ctx, int field_id, int64_t v_begin, int64_t v_end,
+                                    float* out) {
+    if (!ctx) return NDF_ERR_ARG;
+    if (field_id < 0 || field_id >= (int)ctx->fields.size())
+        return fail(ctx, NDF_ERR_ARG, "field id out of range");
+    Field& f = ctx->fields[field_id];
+    if (!f.live) return fail(ctx, NDF_ERR_STATE, "field has been freed");
+    if (v_begin < 0 || v_begin > v_end || v_end > f.N)
+        return fail(ctx, NDF_ERR_ARG, "vertex range [%lld, %lld) outside [0, %lld)", (long long)v_begin,
+                    (long long)v_end, (long long)f.N);
+    if (f.M > kKsgMaxM) return fail(ctx, NDF_ERR_STATE, "no sorted columns above M = %d", kKsgMaxM);
+    if (v_end == v_begin) return NDF_OK;
+    if (!out) return fail(ctx, NDF_ERR_ARG, "null pointer");
+    cudaSetDevice(ctx->device);
+    cudaError_t e = ensure_sorted_columns(ctx, f);
+    const size_t w = sizeof(float) * (size_t)(v_end - v_begin);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(out, w, f.sorted + v_begin, sizeof(float) * (size_t)f.N, w, (size_t)f.M,
+                              cudaMemcpyDefault, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "sorted columns copy");
     return NDF_OK;
 }
 

@@ -114,8 +114,9 @@ ndf_status ensure_psi_table(ndf_ctx* ctx, int64_t n_max);
 double digamma_int_host(int64_t n);
 
 // kernels (launch wrappers; each returns the launch error)
+// (on `stream`, the context's stream when null)
 cudaError_t launch_field_stats(ndf_ctx* ctx, const Field& f, int64_t v_begin, int64_t v_end,
-                               int* d_nonfinite);
+                               int* d_nonfinite, cudaStream_t stream = nullptr);
 cudaError_t launch_pearson(ndf_ctx* ctx, const Field& rf, const Field& qf, int64_t ref_idx,
                            float* out);
 // KSG MI for R references (d_refs on the device, or references ref0, ref0 + 1, ...
@@ -133,8 +134,21 @@ cudaError_t launch_ksg(ndf_ctx* ctx, const Field& rf, const Field& qf, const int
 // Builds Field::sorted (one sort per vertex column, kept with the field).
 cudaError_t ensure_sorted_columns(ndf_ctx* ctx, Field& f);
 // Sorts the columns of vertices [v_begin, v_end) into the allocated Field::sorted.
+// Up to kSortTileMaxM members the kernel can do two more things on the way:
+//  - with src (a device field of f's shape) the columns are read from src and also
+//    written unsorted into f.data: the copy of a device-resident field;
+//  - with d_nonfinite it writes the statistics of launch_field_stats (f.mean,
+//    f.inv_norm, the flag set on a non-finite member) from the same registers.
+// Either above kSortTileMaxM: cudaErrorInvalidValue.
+constexpr int kSortTileMaxM = 1024;
+struct ColumnStats {
+    double* mean;
+    double* inv_norm;
+    int* nonfinite;
+};
 cudaError_t launch_sort_columns(ndf_ctx* ctx, const Field& f, int64_t v_begin, int64_t v_end,
-                                cudaStream_t stream);
+                                cudaStream_t stream, const float* src = nullptr,
+                                int* d_nonfinite = nullptr);
 
 // Scratch of the continuous sampler: position, column and statistics blocks for
 // up to `cap` pairs, reused across calls.

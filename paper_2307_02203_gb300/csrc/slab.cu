@@ -21,9 +21,11 @@ __global__ void gather_column_kernel(const float* __restrict__ field, int64_t M,
 }
 
 // The context's one-vertex reference field, filled from `column` (M floats,
-// host or device) with its statistics.
+// host or device) with its statistics: from the kernel that a load of the whole
+// field takes them from (the column sort up to 1024 members, which needs M more
+// floats for the sorted copy), so that they are the same bits.
 static ndf_status stage_column(ndf_ctx* ctx, const float* column, int64_t M, Field** out) {
-    cudaError_t e = ctx->col_data.reserve(sizeof(float) * (size_t)M);
+    cudaError_t e = ctx->col_data.reserve(sizeof(float) * 2 * (size_t)M);
     if (e == cudaSuccess) e = ctx->col_stats.reserve(2 * sizeof(double) + sizeof(int));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "reference column staging");
     e = cudaMemcpyAsync(ctx->col_data.ptr, column, sizeof(float) * (size_t)M, cudaMemcpyDefault,
@@ -37,7 +39,13 @@ static ndf_status stage_column(ndf_ctx* ctx, const float* column, int64_t M, Fie
     f.mean = ctx->col_stats.as<double>();
     f.inv_norm = ctx->col_stats.as<double>() + 1;
     int* nonfinite = reinterpret_cast<int*>(ctx->col_stats.as<double>() + 2);
-    e = launch_field_stats(ctx, f, 0, 1, nonfinite);
+    if (M <= kSortTileMaxM) {
+        f.sorted = ctx->col_data.as<float>() + M;
+        e = launch_sort_columns(ctx, f, 0, 1, ctx->stream, nullptr, nonfinite);
+    } else {
+        f.sorted = nullptr;
+        e = launch_field_stats(ctx, f, 0, 1, nonfinite);
+    }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "reference column statistics");
     *out = &f;
     return NDF_OK;

@@ -2,7 +2,9 @@
 // FP64 mean mu_v and 1/sqrt(S_v), S_v = sum_m (e_m(v) - mu_v)^2.  Two passes over
 // the member-major field; within a block of 32 members the sums run in FP32,
 // across blocks in FP64.  Constant columns are detected exactly (min == max) so
-// that their S_v is exactly 0.  HBM-bound: 2 * M * N * 4 bytes read.
+// that their S_v is exactly 0.  HBM-bound: 2 * M * N * 4 bytes read.  Loads of up to
+// 1024 members take the same statistics from the column-sort kernel instead, which
+// holds each column in registers anyway.
 #include "ndf_internal.h"
 
 namespace ndf {
@@ -65,10 +67,10 @@ __global__ void __launch_bounds__(256) field_stats_kernel(const float* __restric
 }
 
 cudaError_t launch_field_stats(ndf_ctx* ctx, const Field& f, int64_t v_begin, int64_t v_end,
-                               int* d_nonfinite) {
+                               int* d_nonfinite, cudaStream_t stream) {
     if (v_end <= v_begin) return cudaSuccess;
     int64_t blocks = (v_end - v_begin + 255) / 256;
-    field_stats_kernel<<<(unsigned)blocks, 256, 0, ctx->stream>>>(f.data, f.M, f.N, v_begin, v_end,
+    field_stats_kernel<<<(unsigned)blocks, 256, 0, stream ? stream : ctx->stream>>>(f.data, f.M, f.N, v_begin, v_end,
                                                                   f.mean, f.inv_norm, d_nonfinite);
     ctx->launches++;
     return cudaGetLastError();

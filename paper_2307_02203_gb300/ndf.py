@@ -85,6 +85,7 @@ _sig("ndf_trim_cache", ctypes.c_int, [_vp])
 _sig("ndf_selftest_timeout", ctypes.c_int, [_vp])
 _sig("ndf_field_shape", ctypes.c_int, [_vp, ctypes.c_int] + [ctypes.POINTER(_i64)] * 4)
 _sig("ndf_field_stats", ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp])
+_sig("ndf_field_sorted_columns", ctypes.c_int, [_vp, ctypes.c_int, _i64, _i64, _vp])
 _sig("ndf_pearson", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, _vp])
 _sig("ndf_mi_ksg", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, ctypes.c_int, _vp])
 _sig("ndf_mi_ksg2", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, ctypes.c_int, _vp])
@@ -282,6 +283,12 @@ def ndf_field_shape(ctx, field_id: int):
 def ndf_field_stats(ctx, field_id: int, mean_out, inv_norm_out) -> None:
     _check(ctx, _lib.ndf_field_stats(ctx, field_id, _addr(mean_out), _addr(inv_norm_out)),
            "ndf_field_stats")
+
+
+def ndf_field_sorted_columns(ctx, field_id: int, v_begin: int, v_end: int, out) -> None:
+    """out: [M][v_end - v_begin] floats (host or device), each vertex's members ascending."""
+    _check(ctx, _lib.ndf_field_sorted_columns(ctx, field_id, v_begin, v_end, _addr(out)),
+           "ndf_field_sorted_columns")
 
 
 def ndf_pearson(ctx, ref_field: int, query_field: int, ref_idx: int, out) -> None:

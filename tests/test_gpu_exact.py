@@ -79,6 +79,82 @@ def test_chunked_upload_statistics_and_sorted_columns(ndf_mod, ctx):
     ndf_mod.ndf_free_ensemble(ctx, fid)
 
 
+@pytest.mark.parametrize("M,N", [(1000, 640), (1000, 643), (20, 70), (64, 33), (100, 37),
+                                 (300, 52), (513, 96), (3000, 41)])
+def test_sorted_columns_bit_equal(ndf_mod, ctx, M, N):
+    """Every loaded column ascending, bit for bit as numpy sorts it: tiles of 16 vertices
+    read as 16-byte quads (N % 4 == 0) or one float at a time (ragged N), each lane count
+    of the register network (R = 1, 2, 4, 16, 32), and the shared-memory network above
+    1024 members; a column with ties and a constant column included."""
+    rng = np.random.default_rng(M * 7 + N)
+    f = rng.normal(size=(M, N)).astype(np.float32)
+    f[:, 1] = np.round(f[:, 1] * 2.0) / 2.0
+    f[:, 2] = 0.75
+    f = f + np.float32(0.0)  # no negative zeros: equal keys may leave in either order
+    fid = load(ndf_mod, ctx, f.reshape(M, 1, 1, N))
+    out = np.empty((M, N), dtype=np.float32)
+    ndf_mod.ndf_field_sorted_columns(ctx, fid, 0, N, out)
+    assert np.array_equal(out.view(np.uint32), np.sort(f, axis=0).view(np.uint32))
+    v0, v1 = 3, N - 2  # a sub-range, into device memory
+    dev = torch.empty((M, v1 - v0), dtype=torch.float32, device="cuda")
+    ndf_mod.ndf_field_sorted_columns(ctx, fid, v0, v1, dev)
+    assert np.array_equal(dev.cpu().numpy().view(np.uint32), out[:, v0:v1].view(np.uint32))
+    for a, b in ((-1, 2), (2, 1), (0, N + 1)):
+        with pytest.raises(ndf_mod.NdfError) as ei:
+            ndf_mod.ndf_field_sorted_columns(ctx, fid, a, b, out)
+        assert ei.value.status == ndf_mod.NDF_ERR_ARG
+    ndf_mod.ndf_free_ensemble(ctx, fid)
+
+
+def test_sorted_columns_absent_above_4096_members(ndf_mod, ctx):
+    f = rand_field((4097, 1, 1, 8), 5)
+    fid = load(ndf_mod, ctx, f)
+    out = np.empty((4097, 8), dtype=np.float32)
+    with pytest.raises(ndf_mod.NdfError) as ei:
+        ndf_mod.ndf_field_sorted_columns(ctx, fid, 0, 8, out)
+    assert ei.value.status == ndf_mod.NDF_ERR_STATE
+    ndf_mod.ndf_free_ensemble(ctx, fid)
+
+
+@pytest.mark.parametrize("M,offset", [(1000, 0), (1000, 1), (1100, 0)])
+def test_device_source_load_matches_host_load(ndf_mod, ctx, M, offset):
+    """A device-resident field is read in place: up to 1024 members the sort kernel
+    writes the copy as it reads (16-byte quads from an aligned source, single floats
+    from one shifted by a float), above that a contiguous copy comes first.  The
+    statistics, sorted columns and both volumes equal those of the same field loaded
+    from host memory, bit for bit, for ndf_load_ensemble and ndf_load_and_compute."""
+    Z, Y, X = 1, 3, 100  # N = 300: 18 whole 16-vertex tiles and a ragged one
+    N, ref = Z * Y * X, 17
+    f = rand_field((M, Z, Y, X), 21)
+    fh = load(ndf_mod, ctx, f)
+    buf = torch.empty(M * N + offset, dtype=torch.float32, device="cuda")
+    buf[offset:] = torch.from_numpy(f.reshape(-1)).cuda()
+    src = buf[offset:]
+
+    def state(fid):
+        mean, inv = np.empty(N), np.empty(N)
+        ndf_mod.ndf_field_stats(ctx, fid, mean, inv)
+        cols = np.empty((M, N), dtype=np.float32)
+        ndf_mod.ndf_field_sorted_columns(ctx, fid, 0, N, cols)
+        r, mi = np.empty(N, dtype=np.float32), np.empty(N, dtype=np.float32)
+        ndf_mod.ndf_pearson(ctx, fid, fid, ref, r)
+        ndf_mod.ndf_mi_ksg(ctx, fid, fid, ref, 4, mi)
+        return [mean.view(np.uint64), inv.view(np.uint64), cols.view(np.uint32),
+                r.view(np.uint32), mi.view(np.uint32)]
+
+    want = state(fh)
+    fd = ndf_mod.ndf_load_ensemble(ctx, src, M, Z, Y, X)
+    for a, b in zip(state(fd), want):
+        assert np.array_equal(a, b)
+    r, mi = np.empty(N, dtype=np.float32), np.empty(N, dtype=np.float32)
+    fc = ndf_mod.ndf_load_and_compute(ctx, src, M, Z, Y, X, ref, 4, r, mi)
+    assert np.array_equal(r.view(np.uint32), want[3]) and np.array_equal(mi.view(np.uint32), want[4])
+    for a, b in zip(state(fc), want):
+        assert np.array_equal(a, b)
+    for fid in (fh, fd, fc):
+        ndf_mod.ndf_free_ensemble(ctx, fid)
+
+
 def test_reload_reuses_buffers_without_stale_data(ndf_mod, ctx, tiny_field, tiny_ref):
     """A freed field's buffers are reused by the next load of the same size; the
     new field's statistics, sorted columns and volumes must be its own."""
@@ -385,11 +461,15 @@ def test_argument_errors(ndf_mod, ctx, tiny_field, tiny_ref):
     with pytest.raises(ndf.NdfError) as ei:
         ndf.ndf_pearson(ctx, fid, other, 0, out)
     assert ei.value.status == ndf.NDF_ERR_ARG
-    bad = tiny_field.copy()
-    bad[3, 0, 0, 0] = np.nan
-    with pytest.raises(ndf.NdfError) as ei:
-        load(ndf, ctx, bad)
-    assert ei.value.status == ndf.NDF_ERR_ARG
+    for value, where in ((np.nan, (3, 0, 0, 0)), (np.inf, (0, 0, 1, 5)), (-np.inf, (7, 0, 0, 15))):
+        bad = tiny_field.copy()
+        bad[where] = value
+        with pytest.raises(ndf.NdfError) as ei:
+            load(ndf, ctx, bad)
+        assert ei.value.status == ndf.NDF_ERR_ARG
+        with pytest.raises(ndf.NdfError) as ei:  # read in place from device memory
+            ndf.ndf_load_ensemble(ctx, torch.from_numpy(bad).cuda(), *bad.shape)
+        assert ei.value.status == ndf.NDF_ERR_ARG
     with pytest.raises(ndf.NdfError) as ei:
         ndf.ndf_load_ensemble(ctx, tiny_field, 1, 4, 16, 16)
     assert ei.value.status == ndf.NDF_ERR_ARG
