@@ -899,7 +899,7 @@ def run_reference(args, recipe):
     return 0
 
 
-CASES = ("hash-decode", "dense-decode", "pearson-gemm", "ksg", "train-step")
+CASES = ("hash-decode", "dense-decode", "pearson-gemm", "ksg", "train-step", "load-device")
 
 
 def run_case(args, recipe):
@@ -916,6 +916,8 @@ def run_case(args, recipe):
                     (--precision tf32|bf16x3|fp32)
       ksg           one KSG volume (k = 8) of the loaded workload, --ksg-search
       train-step    dense-NDF Adam steps at batch --case-batch (seeded pairs)
+      load-device   ndf_load_ensemble of the workload's field from device memory (the
+                    copy, statistics and sorted columns), then ndf_free_ensemble
     """
     import torch
 
@@ -935,6 +937,9 @@ def run_case(args, recipe):
         field = synth.generate(recipe)
         fid = ndf.ndf_load_ensemble(ctx, field, recipe.M, Z, Y, X)
         del field
+    elif args.case == "load-device":
+        synth.build()
+        field_dev = torch.from_numpy(synth.generate(recipe)).cuda()
     out = torch.empty((R, N), dtype=torch.float32, device="cuda")
     info = {}
     free = []
@@ -985,6 +990,12 @@ def run_case(args, recipe):
 
         def call():
             ndf.ndf_mi_ksg(ctx, fid, fid, int(rng.integers(0, N)), K_NN, out[0])
+    elif args.case == "load-device":
+        info["field_bytes"] = 4 * recipe.M * N
+        R = 1
+
+        def call():
+            ndf.ndf_free_ensemble(ctx, ndf.ndf_load_ensemble(ctx, field_dev, recipe.M, Z, Y, X))
     else:  # train-step
         res = [int(v) for v in args.ndf_res.split(",")]
         m = ndf.ndf_model_create(ctx, res, ndf.NDF_MEASURE_PEARSON, 1, X, Y, Z)
