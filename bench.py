@@ -1302,27 +1302,34 @@ def main():
         ndf.ndf_mi_ksg(ctx, fid2, fid2, ref, K_NN, host_mi)
         ndf.ndf_free_ensemble(ctx, fid2)
 
-    def time_e2e(fn):
-        fn(refs[0])  # warm-up: first-touch of the second field's device pages
-        barrier()
-        t0 = time.perf_counter()
-        for i in range(e2e_steps):
-            fn(refs[args.warmup + i])
-        barrier()
-        ms = max_over_ranks([(time.perf_counter() - t0) * 1e3], world, "cuda")[0]
-        return job_ms_per_volume(ms, e2e_steps, world)
-
-    e2e_per_volume = time_e2e(e2e_volume)
-    e2e_sequential = time_e2e(e2e_volume_sequential)
-    # the host link the end-to-end number depends on: one plain copy of the pinned field
+    # the host link the end-to-end number depends on, sampled by one plain copy of the
+    # pinned field just before each timed call (it is shared with the machine's other
+    # GPUs, and its rate changes within seconds)
     h2d_dev = torch.empty(field_t.shape, dtype=torch.float32, device="cuda")
-    h2d_gbs = []
-    for _ in range(2):
+
+    def link_gbs():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h2d_dev.copy_(field_t, non_blocking=True)
         torch.cuda.synchronize()
-        h2d_gbs.append(field.nbytes / (time.perf_counter() - t0) / 1e9)
+        return field.nbytes / (time.perf_counter() - t0) / 1e9
+
+    def time_e2e(fn):
+        fn(refs[0])  # warm-up: first-touch of the second field's device pages
+        calls_ms, links = [], []
+        for i in range(e2e_steps):
+            links.append(link_gbs())
+            barrier()
+            t0 = time.perf_counter()
+            fn(refs[args.warmup + i])
+            barrier()
+            calls_ms.append((time.perf_counter() - t0) * 1e3)
+        ms = max_over_ranks([sum(calls_ms)], world, "cuda")[0]
+        return job_ms_per_volume(ms, e2e_steps, world), calls_ms, links
+
+    e2e_per_volume, e2e_calls_ms, e2e_links = time_e2e(e2e_volume)
+    e2e_sequential, _, _ = time_e2e(e2e_volume_sequential)
+    h2d_gbs = [link_gbs() for _ in range(2)]
     del h2d_dev
 
     # ---- roofline of the dominant kernel (KSG: ALU-bound distance evaluations)
@@ -1382,8 +1389,10 @@ def main():
             "ksg_batch64": ksg_batch,
             "e2e": {"value": e2e_per_volume, "unit": "ms", "call": "ndf_load_and_compute",
                     "sequential_calls_ms": e2e_sequential,
-                    "host_link_gbs": max(h2d_gbs),
-                    "host_link_note": "one pinned-host to device copy of the field, this box",
+                    "per_call_ms": e2e_calls_ms,
+                    "host_link_gbs_before_call": e2e_links,
+                    "host_link_gbs": max(h2d_gbs + e2e_links),
+                    "host_link_note": "one pinned-host to device copy of the field, this box: before each timed call and twice after",
                     "h2d_bytes_per_step": int(field.nbytes),
                     "d2h_bytes_per_step": int(2 * N * 4)},
             "gpu_launches": int(launches),
