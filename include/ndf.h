@@ -93,8 +93,8 @@ int64_t ndf_index(int64_t x, int64_t y, int64_t z, int64_t X, int64_t Y, int64_t
  * A host field is copied in vertex ranges on an internal stream, the statistics
  * and sorts of each range following on the context's stream; a device field is
  * read in place by one kernel that writes the copy, the statistics and the sorted
- * columns (M <= 1024; a contiguous copy first above that).  The call returns when
- * all is done.  Requires M >= 2 and finite values (NDF_ERR_ARG otherwise; the check
+ * columns (M <= 1024; a contiguous copy first above that); its writes on other
+ * streams must be complete before the call.  The call returns when all is done.  Requires M >= 2 and finite values (NDF_ERR_ARG otherwise; the check
  * reads the copied field).  Writes the new field's id. */
 ndf_status ndf_load_ensemble(ndf_ctx* ctx, const float* field, int64_t M, int64_t Z, int64_t Y,
                              int64_t X, int* field_id_out);

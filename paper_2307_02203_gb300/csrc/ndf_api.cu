@@ -436,7 +436,10 @@ ndf_status ndf_load_and_compute(ndf_ctx* ctx, const float* field, int64_t M, int
     Field f;
     f.M = M; f.Z = Z; f.Y = Y; f.X = X; f.N = N;
     const size_t bytes = sizeof(float) * (size_t)M * (size_t)N, vol = sizeof(float) * (size_t)N;
-    const bool want_sorted = mi_out && M <= kKsgMaxM;  // the KSG searches read it
+    // sorted as ndf_load_ensemble sorts (the KSG searches read the copy, and up to 1024
+    // members the sort kernel writes the statistics), so the field left loaded, and the
+    // Pearson volume from its statistics, are the same bits as after ndf_load_ensemble
+    const bool want_sorted = M <= kKsgMaxM;
     cudaError_t e = ctx_alloc(ctx, (void**)&f.data, bytes);
     if (e == cudaSuccess) e = ctx_alloc(ctx, (void**)&f.mean, sizeof(double) * (size_t)N);
     if (e == cudaSuccess) e = ctx_alloc(ctx, (void**)&f.inv_norm, sizeof(double) * (size_t)N);

@@ -151,7 +151,12 @@ def test_device_source_load_matches_host_load(ndf_mod, ctx, M, offset):
     assert np.array_equal(r.view(np.uint32), want[3]) and np.array_equal(mi.view(np.uint32), want[4])
     for a, b in zip(state(fc), want):
         assert np.array_equal(a, b)
-    for fid in (fh, fd, fc):
+    r2 = np.empty(N, dtype=np.float32)  # Pearson only, from host memory
+    fp = ndf_mod.ndf_load_and_compute(ctx, f, M, Z, Y, X, ref, 4, r2, None)
+    assert np.array_equal(r2.view(np.uint32), want[3])
+    for a, b in zip(state(fp), want):
+        assert np.array_equal(a, b)
+    for fid in (fh, fd, fc, fp):
         ndf_mod.ndf_free_ensemble(ctx, fid)
 
 
