@@ -899,7 +899,8 @@ def run_reference(args, recipe):
     return 0
 
 
-CASES = ("hash-decode", "dense-decode", "pearson-gemm", "ksg", "train-step", "load-device")
+CASES = ("hash-decode", "dense-decode", "pearson-gemm", "ksg", "train-step", "load-device",
+         "hash-train-step")
 
 
 def run_case(args, recipe):
@@ -918,6 +919,8 @@ def run_case(args, recipe):
       train-step    dense-NDF Adam steps at batch --case-batch (seeded pairs)
       load-device   ndf_load_ensemble of the workload's field from device memory (the
                     copy, statistics and sorted columns), then ndf_free_ensemble
+      hash-train-step  Adam steps of the paper's network (default architecture, Pearson)
+                    at batch --case-batch (seeded continuous positions and targets)
     """
     import torch
 
@@ -990,6 +993,20 @@ def run_case(args, recipe):
 
         def call():
             ndf.ndf_mi_ksg(ctx, fid, fid, int(rng.integers(0, N)), K_NN, out[0])
+    elif args.case == "hash-train-step":
+        m = ndf.ndf_hash_model_create(ctx, ndf.ndf_hash_arch_default(), ndf.NDF_MEASURE_PEARSON,
+                                      False, 1, X, Y, Z)
+        free.append(lambda: ndf.ndf_hash_model_free(m))
+        B = args.case_batch
+        g = torch.Generator(device="cuda").manual_seed(1)
+        pr = torch.rand((B, 3), device="cuda", generator=g) * 2 - 1
+        pq = torch.rand((B, 3), device="cuda", generator=g) * 2 - 1
+        tgt = torch.rand(B, device="cuda", generator=g) * 2 - 1
+        info["batch"] = B
+        R = 1
+
+        def call():
+            ndf.ndf_hash_model_step(m, pr, pq, tgt, 1e-3, True)
     elif args.case == "load-device":
         info["field_bytes"] = 4 * recipe.M * N
         R = 1

@@ -6,7 +6,8 @@
 //
 // One kernel, C[M][N] = sum_k A(m, k) B(k, n), with A and B read row-major either
 // way round (TA: A stored [K][M]; TB: B stored [N][K]).  A CTA of 256 threads
-// computes a 64 x 64 tile in 16-deep slices staged through shared memory; thread
+// computes a 64 x 64 tile in 16-deep slices staged through shared memory (each
+// slice read into registers while the previous one is multiplied); thread
 // (ty, tx) owns rows ty + 16 i and columns tx + 16 j (i, j < 4), so a warp's
 // shared-memory reads are broadcasts (A) or 16 consecutive words (B).  With a
 // split over K (blockIdx.z) each slice of K writes its own partial tile, and a
@@ -31,8 +32,10 @@ __global__ void __launch_bounds__(256)
     const int64_t k_begin = (int64_t)blockIdx.z * k_chunk;
     const int64_t k_end = k_begin + k_chunk < K ? k_begin + k_chunk : K;
     float acc[4][4] = {};
-    for (int64_t k0 = k_begin; k0 < k_end; k0 += kBK) {
-        // stage A(m0.., k0..) and B(k0.., n0..): 1024 elements each, 4 per thread
+    // slice k0 of A(m0.., k..) and B(k.., n0..): 1024 elements each, 4 per thread, read
+    // into registers one slice ahead of the products, so the loads' latency overlaps them
+    float va[4], vb[4];
+    auto load_slice = [&](int64_t k0) {
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const int e = threadIdx.x + 256 * r;
@@ -45,9 +48,7 @@ __global__ void __launch_bounds__(256)
                 mm = e >> 4;
             }
             const int64_t gm = m0 + mm, gk = k0 + kk;
-            float v = 0.0f;
-            if (gm < M && gk < k_end) v = TA ? A[gk * lda + gm] : A[gm * lda + gk];
-            As[kk][mm] = v;
+            va[r] = (gm < M && gk < k_end) ? (TA ? A[gk * lda + gm] : A[gm * lda + gk]) : 0.0f;
             int nn;
             if (TB) {  // consecutive threads along k (contiguous in [N][K])
                 kk = e & (kBK - 1);
@@ -57,11 +58,24 @@ __global__ void __launch_bounds__(256)
                 kk = e >> 6;
             }
             const int64_t gn = n0 + nn, gk2 = k0 + kk;
-            float w = 0.0f;
-            if (gn < N && gk2 < k_end) w = TB ? B[gn * ldb + gk2] : B[gk2 * ldb + gn];
-            Bs[kk][nn] = w;
+            vb[r] = (gn < N && gk2 < k_end) ? (TB ? B[gn * ldb + gk2] : B[gk2 * ldb + gn]) : 0.0f;
         }
+    };
+    auto store_slice = [&]() {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int e = threadIdx.x + 256 * r;
+            if (TA) As[e >> 6][e & (kBM - 1)] = va[r];
+            else As[e & (kBK - 1)][e >> 4] = va[r];
+            if (TB) Bs[e & (kBK - 1)][e >> 4] = vb[r];
+            else Bs[e >> 6][e & (kBN - 1)] = vb[r];
+        }
+    };
+    if (k_begin < k_end) load_slice(k_begin);
+    for (int64_t k0 = k_begin; k0 < k_end; k0 += kBK) {
+        store_slice();
         __syncthreads();
+        if (k0 + kBK < k_end) load_slice(k0 + kBK);
         // each 16-deep slice is summed on its own and then added to the running sums
         // (blocked summation: rounding grows with 16 + K / 16 terms instead of K)
         float part[4][4] = {};
