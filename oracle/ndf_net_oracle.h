@@ -3,7 +3,7 @@
  * INFRASTRUCTURE ONLY (tests, smoke check, benchmark baseline).  Plain loops,
  * no blocking, shares no code with the CUDA library.
  *
- * Network (Sec. 4.1-4.3, in the dense-grid / ReLU form of this build):
+ * Network (Sec. 4.1-4.3, in the dense-grid / ReLU form the library trains):
  *   f(p)  = concat over levels l of the trilinear interpolation of a dense
  *           feature grid with res[l] points per axis, corner-aligned on
  *           [-1,1]^3, `feat` features per point                (Sec. 4.2)
